@@ -1,0 +1,257 @@
+"""FP64 CPU oracle for plane-wave beamforming, envelope, log compression and metrics.
+
+TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference leg are the only importers.  The product
+package never imports it, and it imports nothing from the product package.
+
+* ``beamform`` / ``delayed_samples`` wrap ``bf_oracle.c`` (double precision,
+  plain loops over pixels, angles and channels; see that file's header for
+  the exact definition it follows, Eq. (1) and Sec. II-B of the paper).
+* ``envelope`` is the analytic-signal magnitude along depth computed with a
+  library FFT in float64 (one-sided spectrum, scipy.signal.hilbert
+  convention); the DMAS image additionally keeps only the band [f0, 3 f0]
+  around its second harmonic.
+* ``log_compress`` maps the envelope to decibels against the frame maximum
+  and clips at the -70 dB dynamic range the paper's images use (Fig. 3).
+* ``fwhm``, ``contrast`` implement the resolution and contrast metrics of
+  Sec. II-D (FWHM at -6 dB, CR, CNR).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bf_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+DAS, DMAS, CF = "das", "dmas", "cf"
+
+
+def build(force: bool = False) -> str:
+    """Compile bf_oracle.c into liboracle.so next to it (gcc, OpenMP, no FMA contraction)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+           "-shared", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _bind(lib):
+    d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
+    p = ctypes.c_void_p
+    lib.oracle_beamform.argtypes = [p, i32, i32, i32, p, p, i32, i32, d, d, d, d, d, d, d,
+                                    p, i64, p, p, p, p, i32]
+    lib.oracle_beamform.restype = ctypes.c_int
+    lib.oracle_delayed_samples.argtypes = [p, i32, i32, i32, p, p, i32, i32, d, d, d, d,
+                                           i32, i32, d, d, d, p, p, p]
+    lib.oracle_delayed_samples.restype = ctypes.c_int
+    lib.oracle_max_threads.restype = ctypes.c_int32
+    return lib
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = _bind(ctypes.CDLL(build()))
+    return _lib
+
+
+class use_library:
+    """Context manager that routes this module through another build of
+    bf_oracle.c (the mutation tests plant mistakes in a copy of the source)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        _load()
+        self.saved = _lib
+        _lib = _bind(ctypes.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _grid(grid):
+    nx, nz, x0, x1, z0, z1 = grid
+    return int(nx), int(nz), float(x0), float(x1), float(z0), float(z1)
+
+
+def grid_coords(grid):
+    """Pixel coordinates (inclusive linspaces, float64)."""
+    nx, nz, x0, x1, z0, z1 = _grid(grid)
+
+    def ls(lo, hi, n):
+        if n == 1:
+            return np.array([lo])
+        return lo + np.arange(n, dtype=np.float64) * ((hi - lo) / (n - 1))
+
+    return ls(x0, x1, nx), ls(z0, z1, nz)
+
+
+def beamform(rf, x_elem, angles_rad, grid, fs, c, f_number, *, pixels=None, threads=0):
+    """DAS, DMAS and CF-DAS images (float64) plus the active-channel count.
+
+    rf: int16 [A][N][Ns]; grid = (nx, nz, x0, x1, z0, z1) in metres.
+    pixels: optional int64 array of linear indices ix * nz + iz; outputs are
+    then 1-D in that order, otherwise [nx][nz].
+    """
+    rf = np.ascontiguousarray(rf, dtype=np.int16)
+    na, ne, ns = rf.shape
+    x_elem = np.ascontiguousarray(x_elem, dtype=np.float64)
+    th = np.ascontiguousarray(np.atleast_1d(angles_rad), dtype=np.float64)
+    assert x_elem.shape == (ne,) and th.shape == (na,)
+    nx, nz, x0, x1, z0, z1 = _grid(grid)
+    if pixels is None:
+        shape, pix, npix = (nx, nz), None, nx * nz
+    else:
+        pix = np.ascontiguousarray(pixels, dtype=np.int64)
+        shape, npix = pix.shape, pix.size
+    out = {k: np.empty(shape, np.float64) for k in (DAS, DMAS, CF)}
+    m = np.empty(shape, np.int32)
+    rc = _load().oracle_beamform(_ptr(rf), na, ne, ns, _ptr(x_elem), _ptr(th), nx, nz, x0, x1,
+                                 z0, z1, float(fs), float(c), float(f_number), _ptr(pix), npix,
+                                 _ptr(out[DAS]), _ptr(out[DMAS]), _ptr(out[CF]), _ptr(m),
+                                 int(threads))
+    if rc != 0:
+        raise ValueError("oracle_beamform rejected its arguments (rc=%d)" % rc)
+    out["m"] = m
+    return out
+
+
+def delayed_samples(rf, x_elem, angles_rad, grid, ix, iz, fs, c, f_number):
+    """Per (angle, channel) interpolated samples of one pixel and their flags."""
+    rf = np.ascontiguousarray(rf, dtype=np.int16)
+    na, ne, ns = rf.shape
+    x_elem = np.ascontiguousarray(x_elem, dtype=np.float64)
+    th = np.ascontiguousarray(np.atleast_1d(angles_rad), dtype=np.float64)
+    nx, nz, x0, x1, z0, z1 = _grid(grid)
+    v = np.empty((na, ne), np.float64)
+    act = np.empty((na, ne), np.uint8)
+    rec = np.empty((na, ne), np.uint8)
+    rc = _load().oracle_delayed_samples(_ptr(rf), na, ne, ns, _ptr(x_elem), _ptr(th), nx, nz, x0,
+                                        x1, z0, z1, int(ix), int(iz), float(fs), float(c),
+                                        float(f_number), _ptr(v), _ptr(act), _ptr(rec))
+    if rc != 0:
+        raise ValueError("pixel out of the grid")
+    return v, act.astype(bool), rec.astype(bool)
+
+
+def spectral_mask(length, *, bandpass=False, dz=None, c=None, f0=None):
+    """One-sided analytic-signal mask H[k] times the optional band-pass B[k].
+
+    H[0] = 1, H[k] = 2 for 0 < k < L/2, H[L/2] = 1 when L is even, 0 for the
+    negative frequencies.  B[k] = 1 iff f0 <= k c / (2 L dz) <= 3 f0 and
+    B[0] = 0: bin k of a depth axis of spacing dz is the RF frequency
+    k c / (2 L dz) (two-way travel)."""
+    L = int(length)
+    h = np.zeros(L)
+    h[0] = 1.0
+    if L % 2 == 0:
+        h[1:L // 2] = 2.0
+        h[L // 2] = 1.0
+    else:
+        h[1:(L + 1) // 2] = 2.0
+    if bandpass:
+        k = np.arange(L, dtype=np.float64)
+        f = k * c / (2.0 * L * dz) if L > 1 else np.zeros(1)
+        b = ((f >= f0) & (f <= 3.0 * f0)).astype(np.float64)
+        b[0] = 0.0
+        h = h * b
+    return h
+
+
+def envelope(y, *, bandpass=False, dz=None, c=None, f0=None):
+    """|analytic signal| of each column of y [..., nz] along the last axis (float64)."""
+    y = np.asarray(y, dtype=np.float64)
+    L = y.shape[-1]
+    X = np.fft.fft(y, axis=-1)
+    X = X * spectral_mask(L, bandpass=bandpass, dz=dz, c=c, f0=f0)
+    return np.abs(np.fft.ifft(X, axis=-1))
+
+
+def log_compress(env, dynamic_range_db=70.0):
+    """20 log10(env / max env), clipped to [-DR, 0]; a zero envelope maps to -DR."""
+    env = np.asarray(env, dtype=np.float64)
+    peak = env.max() if env.size else 0.0
+    out = np.full(env.shape, -float(dynamic_range_db))
+    if peak > 0.0:
+        with np.errstate(divide="ignore"):
+            db = 20.0 * np.log10(env / peak)
+        out = np.clip(db, -float(dynamic_range_db), 0.0)
+    return out
+
+
+def fwhm(profile, spacing=1.0, drop_db=6.0):
+    """Width at -drop_db below the peak of a sampled profile (linear envelope).
+
+    Crossings are located by linear interpolation between the samples that
+    straddle the threshold, walking outwards from the peak; NaN when the
+    profile never drops below the threshold on one side."""
+    p = np.asarray(profile, dtype=np.float64)
+    m = int(np.argmax(p))
+    thr = p[m] * 10.0 ** (-drop_db / 20.0)
+    j = m
+    while j > 0 and p[j - 1] >= thr:
+        j -= 1
+    if j == 0:
+        return float("nan")
+    left = (j - 1) + (thr - p[j - 1]) / (p[j] - p[j - 1])
+    j = m
+    while j < len(p) - 1 and p[j + 1] >= thr:
+        j += 1
+    if j == len(p) - 1:
+        return float("nan")
+    right = j + (p[j] - thr) / (p[j] - p[j + 1])
+    return float((right - left) * spacing)
+
+
+def cyst_regions(grid, xc, zc, radius, *, inner=0.8, offset=2.5):
+    """Masks [nx][nz]: a disk of inner*radius at the cyst centre and two disks
+    of the same size at the same depth, offset*radius to either side."""
+    xs, zs = grid_coords(grid)
+    X, Z = np.meshgrid(xs, zs, indexing="ij")
+    r2 = (inner * radius) ** 2
+    inside = (X - xc) ** 2 + (Z - zc) ** 2 <= r2
+    outside = (((X - xc - offset * radius) ** 2 + (Z - zc) ** 2 <= r2)
+               | ((X - xc + offset * radius) ** 2 + (Z - zc) ** 2 <= r2))
+    return inside, outside
+
+
+def contrast(env, inside, outside):
+    """CR (dB) and CNR of Sec. II-D from a linear envelope image.
+
+    cnr uses the pooled deviation sqrt((s_in^2 + s_out^2)/2); cnr_printed is
+    the expression exactly as typeset, sqrt(s_in^2 + s_out^2/2)."""
+    a = np.asarray(env, dtype=np.float64)[inside]
+    b = np.asarray(env, dtype=np.float64)[outside]
+    mi, mo = a.mean(), b.mean()
+    si, so = a.std(), b.std()
+    return dict(cr_db=float(20 * np.log10(mi / mo)),
+                cnr=float(abs(mi - mo) / np.sqrt((si * si + so * so) / 2.0)),
+                cnr_printed=float((mi - mo) / np.sqrt(si * si + so * so / 2.0)),
+                mu_in=float(mi), mu_out=float(mo), sigma_in=float(si), sigma_out=float(so))

@@ -1,0 +1,75 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each mutant plants one mistake in a copy of the oracle's C source (a dropped
+term, a wrong sign, a wrong index, a transposed operand, a wrong bound),
+builds it on the CPU, routes the oracle module through it and re-runs the
+pins: at least one pin has to fail for every mutant.
+"""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "bf_oracle.c")
+
+MUTANTS = [
+    ("transmit leg sign", "double tx = xp * st + zp * ct;", "double tx = -xp * st + zp * ct;"),
+    ("transmit leg dropped", "double tx = xp * st + zp * ct;", "double tx = zp * ct;"),
+    ("monostatic delay", "double n = (tx + rx) * kappa;", "double n = (rx + rx) * kappa;"),
+    ("lateral offset transposed", "double dx = xp - xi;", "double dx = xp - zp;"),
+    ("depth term dropped", "sqrt(dx * dx + zp * zp)", "sqrt(dx * dx + zp)"),
+    ("interpolation reads one sample", "alpha * (double)u[kk + 1]", "alpha * (double)u[kk]"),
+    ("interpolation weights swapped",
+     "(1.0 - alpha) * (double)u[kk] + alpha * (double)u[kk + 1]",
+     "alpha * (double)u[kk] + (1.0 - alpha) * (double)u[kk + 1]"),
+    ("aperture uses F instead of 2F", "zp / (2.0 * fnum)", "zp / fnum"),
+    ("aperture exclusive", "fabs(xp - xi) <= zp", "fabs(xp - xi) < zp"),
+    ("record bound off by one", "k <= (double)(ns - 2)", "k <= (double)(ns - 3)"),
+    ("DMAS diagonal sign", "0.5 * (t1 * t1 - t2)", "0.5 * (t1 * t1 + t2)"),
+    ("DMAS without square root", "double s = signed_sqrt(v);", "double s = v;"),
+    ("DMAS sign lost", "return -sqrt(-v);", "return sqrt(-v);"),
+    ("CF without channel count", "(double)m * su2_tot", "su2_tot"),
+    ("angle index frozen", "st[a], ct[a]", "st[0], ct[0]"),
+    ("channel record index", "((size_t)a * ne + i) * (size_t)ns", "((size_t)a * ne) * (size_t)ns"),
+    ("grid spacing", "(hi - lo) / (double)(n - 1)", "(hi - lo) / (double)n"),
+    ("compounding keeps last angle", "s1_tot += s1;", "s1_tot = s1;"),
+]
+
+
+def _pins_pass(golden_dir):
+    checks = [
+        lambda: pins.test_geometry_cases_match_hand_derivations(golden_dir),
+        lambda: pins.test_aperture_counts_match_hand_derivations(golden_dir),
+        lambda: pins.test_constant_record_closed_forms(golden_dir),
+        pins.test_linear_interpolation_exact_on_a_ramp,
+        lambda: pins.test_grid_coordinates_on_a_ramp(golden_dir),
+        pins.test_dmas_identity_against_pairwise_brute_force,
+        pins.test_das_is_linear_and_cf_bounded,
+        lambda: pins.test_point_scatterer_images_within_quarter_wavelength(10.0, "das"),
+    ]
+    for check in checks:
+        try:
+            check()
+        except AssertionError:
+            return False
+    return True
+
+
+def test_unmutated_oracle_passes_pins(golden_dir):
+    assert _pins_pass(golden_dir)
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, golden_dir, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, name
+    mutated = tmp_path / "mutant.c"
+    mutated.write_text(src.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                    str(mutated), "-o", str(lib), "-lm"], check=True)
+    with oracle.use_library(str(lib)):
+        assert not _pins_pass(golden_dir), "mutant '%s' survived every pin" % name
