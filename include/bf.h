@@ -1,0 +1,204 @@
+/*
+ * bf.h -- C ABI of the GB300 plane-wave receive beamformer (libbf.so).
+ *
+ * The library forms B-mode images from plane-wave channel data as the paper
+ * describes (Sec. II-B): for every pixel and receive channel it computes the
+ * transmit + receive time of flight, linearly interpolates the channel's RF,
+ * applies the F-number aperture, and combines the channels by delay-and-sum
+ * (Eq. (1)), by signed-square-root delay-multiply-and-sum, or by
+ * coherence-factor-weighted DAS; results are compounded over plane-wave
+ * angles, then optionally envelope-detected along depth (the DMAS image
+ * through a [f0, 3 f0] band-pass) and log-compressed to the -70 dB dynamic
+ * range the paper's images are shown with (Fig. 3).
+ *
+ * Definitions every entry point follows (all positions in metres):
+ *   element i:  x_i = x_elem_m[i] if given, else (i - (N - 1) / 2) * pitch_m, z_i = 0
+ *   pixel (ix, iz):  x_p = x0 + ix * ((x1 - x0) / (nx - 1))   (x0 when nx == 1),
+ *                    z_p = z0 + iz * ((z1 - z0) / (nz - 1))   (z0 when nz == 1)
+ *   fractional sample index (time zero when the wavefront crosses the array centre):
+ *       n = (x_p sin(theta) + z_p cos(theta) + sqrt((x_p - x_i)^2 + z_p^2)) * (fs / c)
+ *   channel active:  |x_p - x_i| <= z_p / (2 F)               (inclusive boxcar)
+ *   sample:  k = floor(n); v = (1 - (n - k)) u[k] + (n - k) u[k + 1] if 0 <= k <= Ns - 2, else 0
+ *   DAS  = sum_theta sum_active v
+ *   DMAS = sum_theta ((sum s)^2 - sum s^2) / 2,  s = sign(v) sqrt|v|
+ *   CF   = (DAS^2 / (M * sum_theta sum_active v^2)) * DAS, M = active (angle, channel) pairs;
+ *          0 when the denominator is 0
+ * The two discrete decisions (aperture membership and 0 <= k <= Ns - 2) are
+ * taken on the host in double precision with exactly the expressions above,
+ * evaluated left to right without fused multiply-adds; the per-pixel
+ * arithmetic runs on the GPU in FP32.
+ *
+ * Threading: a handle may be used from one thread at a time.  Different
+ * handles may be used concurrently.  All device work of a handle is ordered
+ * on its stream (bf_set_stream; default: a stream the library creates).
+ *
+ * Errors: functions return BF_OK (0), BF_PENDING (1) or a negative BF_E*
+ * code; nothing is thrown across the ABI.  bf_last_error() returns a
+ * thread-local description of the last failure on the calling thread.
+ */
+#ifndef BF_H
+#define BF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define BF_API __attribute__((visibility("default")))
+#else
+#define BF_API
+#endif
+
+/* Linear receive array.  x_elem_m (optional, n_elements entries, strictly
+ * increasing) overrides the uniform centred layout.  f_number > 0. */
+typedef struct bf_geometry {
+    int32_t n_elements;
+    double pitch_m;
+    const double *x_elem_m;
+    double f_number;
+} bf_geometry;
+
+/* Pixel grid: inclusive linspaces, x1 >= x0, z1 >= z0 >= 0, nx, nz in [1, 32767]. */
+typedef struct bf_grid {
+    int32_t nx, nz;
+    double x0_m, x1_m, z0_m, z1_m;
+} bf_grid;
+
+typedef struct bf_handle bf_handle;
+typedef struct bf_batch bf_batch;
+
+/* mode_and_flags: combiner bits (any non-empty subset) ... */
+enum { BF_DAS = 1, BF_DMAS = 2, BF_CF = 4, BF_MODE_MASK = 7 };
+/* ... RF storage precision on the device (bits 4-5; interpolation and sums are always FP32) ... */
+enum { BF_PREC_FP32 = 0, BF_PREC_FP16 = 1 << 4, BF_PREC_BF16 = 2 << 4, BF_PREC_MASK = 3 << 4 };
+/* ... and the output stage (bits 8-9). */
+enum { BF_OUT_RF = 0, BF_OUT_ENV = 1 << 8, BF_OUT_LOGDB = 2 << 8, BF_OUT_MASK = 3 << 8 };
+
+enum {
+    BF_OK = 0,
+    BF_PENDING = 1,      /* bf_poll: result not ready yet */
+    BF_EINVAL = -1,      /* bad argument (message in bf_last_error) */
+    BF_EAGAIN = -2,      /* admission refused: no ring slot / device memory now; retry later */
+    BF_ENOMEM = -3,      /* a device or host allocation failed */
+    BF_ECUDA = -4,       /* a CUDA call failed */
+    BF_ETIMEDOUT = -5,   /* bf_poll deadline passed, or a device-side bounded wait gave up */
+    BF_ENOTFOUND = -6,   /* unknown ticket */
+    BF_ENOSYS = -7       /* feature not available in this build */
+};
+
+/* Create a handle for one geometry and pixel grid.  fs_hz: sampling rate,
+ * f0_hz: transmit centre frequency (sets the DMAS band-pass), c_mps: speed
+ * of sound.  Uploads the geometry tables to the current CUDA device.
+ * *out receives the handle (caller owns it; free with bf_destroy). */
+BF_API int bf_create(const bf_geometry *geometry, const bf_grid *grid, double fs_hz,
+                     double f0_hz, double c_mps, bf_handle **out);
+
+/* Free a handle and its device memory.  BF_EINVAL while tickets are pending. */
+BF_API int bf_destroy(bf_handle *h);
+
+/* Device stream for all of this handle's work (a cudaStream_t; NULL = the
+ * library's own non-blocking stream). */
+BF_API int bf_set_stream(bf_handle *h, void *cuda_stream);
+
+/* Bytes of one output for the given mode_and_flags: popcount(modes) * nx * nz * 4. */
+BF_API size_t bf_output_bytes(const bf_handle *h, uint32_t mode_and_flags);
+
+/* Stream-ordered beamforming of one frame, device-resident data.
+ * rf_dev: device int16 [n_angles][n_elements][n_samples] (read during the call's
+ * stream work), angles_rad: host array of n_angles plane-wave angles in
+ * (-pi/2, pi/2); out_dev: device float [popcount(modes)][nx][nz] (modes in bit
+ * order DAS, DMAS, CF; z fastest) receiving the stage selected by BF_OUT_*.
+ * Returns after enqueueing; the caller synchronises the stream.  Calls on one
+ * handle share its scratch memory and must be ordered on its stream. */
+BF_API int bf_beamform(bf_handle *h, const int16_t *rf_dev, int32_t n_samples,
+                       const double *angles_rad, int32_t n_angles, uint32_t mode_and_flags,
+                       float *out_dev);
+
+/* Asynchronous submission (serving path).  rf: host or device int16
+ * [n_angles][n_elements][n_samples]; it is copied (host -> pinned staging ->
+ * device ring slot) before the call returns, so the caller may reuse it.
+ * *ticket_out identifies the request.  BF_EAGAIN when no slot or device
+ * memory is free right now. */
+BF_API int bf_submit(bf_handle *h, const int16_t *rf, int32_t n_samples,
+                     const double *angles_rad, int32_t n_angles, uint32_t mode_and_flags,
+                     uint64_t *ticket_out);
+
+/* Wait up to timeout_us (0: do not wait; < 0: wait without limit) for a
+ * ticket.  BF_PENDING (timeout_us == 0) or BF_ETIMEDOUT (timeout passed) if
+ * not ready, leaving the ticket valid; BF_OK after copying the result into
+ * out (host or device, out_bytes >= bf_output_bytes; out == NULL discards
+ * it), which releases the ticket; other negative codes release it too.
+ * BF_ENOTFOUND for an unknown or already released ticket. */
+BF_API int bf_poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes,
+                   int64_t timeout_us);
+
+/* Serving-engine introspection: the batch a launched ticket rides in and how
+ * many frames that batch holds (BF_PENDING while still queued). */
+BF_API int bf_ticket_batch(bf_handle *h, uint64_t ticket, int32_t *batch_id,
+                           int32_t *batch_frames);
+
+/* Serving-engine knobs for the current device (values <= 0 keep the current
+ * setting): frames per launched batch (default 64), batches in flight
+ * (default 3), device memory budget of admitted requests in bytes (default
+ * half the device, or BF_MEM_BUDGET_MB from the environment). */
+BF_API int bf_engine_configure(int32_t max_batch, int32_t max_inflight,
+                               uint64_t memory_budget_bytes);
+
+/* Wait for the handle's stream and report device-side failures of its
+ * bf_beamform work (BF_ETIMEDOUT when a bounded wait inside a kernel gave up). */
+BF_API int bf_sync(bf_handle *h);
+
+/* One frame of a batch: its handle (grid, geometry), device RF, host angles,
+ * mode/flags and device output (layout as bf_beamform). */
+typedef struct bf_frame {
+    bf_handle *h;
+    const int16_t *rf_dev;
+    int32_t n_samples;
+    const double *angles_rad;
+    int32_t n_angles;
+    uint32_t mode_and_flags;
+    float *out_dev;
+} bf_frame;
+
+/* Prepare a batch of frames with uneven grids and angle counts: builds the
+ * per-frame tables and one flat work list over all (frame, pixel tile) items
+ * and captures the batch's kernels in a CUDA graph.  The frame descriptors
+ * are copied; the RF and output buffers must stay valid while the batch is
+ * launched. */
+BF_API int bf_batch_create(const bf_frame *frames, int32_t n_frames, bf_batch **out);
+/* Launch a prepared batch on a stream (cudaStream_t; NULL = default stream). */
+BF_API int bf_batch_launch(bf_batch *b, void *cuda_stream);
+/* Synchronise the stream and report device-side failures of the batch's launches. */
+BF_API int bf_batch_status(bf_batch *b, void *cuda_stream);
+/* Device time of the last completed replay, from events captured in the graph:
+ * ms3[0] ingest (+ resets), ms3[1] beamforming launches, ms3[2] envelope + log.
+ * *kernel_launches (optional) receives the number of kernels one replay runs. */
+BF_API int bf_batch_timing(bf_batch *b, float *ms3, int32_t *kernel_launches);
+BF_API int bf_batch_destroy(bf_batch *b);
+
+/* Host-only diagnostic (touches no GPU): the double-precision decision
+ * tables the device path consumes.  valid_rows [n_angles][nx][n_elements][2]
+ * receives the first and last pixel row iz at which channel i's sample
+ * counts for column ix and angle a (inside the aperture and
+ * 0 <= floor(n) <= Ns - 2; first > last when none); aperture_count [nx][nz]
+ * the number of channels inside the aperture of each pixel.  Either output
+ * may be NULL. */
+BF_API int bf_host_tables(const bf_geometry *geometry, const bf_grid *grid, double fs_hz,
+                          double f0_hz, double c_mps, int32_t n_samples,
+                          const double *angles_rad, int32_t n_angles, int32_t *valid_rows,
+                          uint16_t *aperture_count);
+
+/* Thread-local message of the last failure ("" if none). */
+BF_API const char *bf_last_error(void);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+BF_API int bf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BF_H */

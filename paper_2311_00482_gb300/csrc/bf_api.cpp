@@ -1,0 +1,816 @@
+// C ABI of the beamformer: handles, resident tables, scratch, batches and the
+// asynchronous submit / poll path.  See include/bf.h for the contract.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "../../include/bf.h"
+#include "bf_engine.h"
+
+namespace bfi {
+
+// ------------------------------------------------------------------ errors --
+
+static thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? BF_ENOMEM : BF_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------- device mem --
+
+int DevMem::ensure(size_t n)
+{
+    if (n <= bytes && p)
+        return BF_OK;
+    release();
+    if (n == 0)
+        return BF_OK;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        return cuda_fail(e, "cudaMalloc");
+    }
+    bytes = n;
+    return BF_OK;
+}
+
+void DevMem::release()
+{
+    if (p)
+        cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+int DevMem::upload(const void *src, size_t n)
+{
+    int rc = ensure(n);
+    if (rc)
+        return rc;
+    if (n == 0)
+        return BF_OK;
+    cudaError_t e = cudaMemcpy(p, src, n, cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? BF_OK : cuda_fail(e, "cudaMemcpy (tables)");
+}
+
+// ------------------------------------------------------------- tensor map --
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 2-D map over sample pairs: rows = angles * channels, nsp pairs per row.
+static int encode_pairs_map(CUtensorMap *map, void *base, int rows, int nsp, int box, int prec)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc)
+        return fail(BF_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const int pb = pair_bytes(prec);
+    cuuint64_t dims[2] = {(cuuint64_t)nsp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)nsp * (cuuint64_t)pb};
+    cuuint32_t boxd[2] = {(cuuint32_t)box, 1};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, pb == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
+                     2, base, dims, strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(BF_ECUDA, "cuTensorMapEncodeTiled failed (%d): rows %d, pairs %d, box %d", (int)r,
+                    rows, nsp, box);
+    return BF_OK;
+}
+
+// -------------------------------------------------------- envelope tables --
+
+static std::mutex g_env_mu;
+static std::map<std::pair<int, int>, std::shared_ptr<EnvTablesDev>> g_env_cache;  // (device, nz)
+
+static int env_tables(int nz, std::shared_ptr<EnvTablesDev> &out)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_env_mu);
+    auto it = g_env_cache.find({dev, nz});
+    if (it != g_env_cache.end()) {
+        out = it->second;
+        return BF_OK;
+    }
+    EnvHost eh;
+    envelope_tables(nz, eh);
+    auto t = std::make_shared<EnvTablesDev>();
+    t->nz = nz;
+    t->fft_m = eh.fft_m;
+    t->bluestein = eh.bluestein;
+    int rc = t->tw.upload(eh.tw.data(), eh.tw.size() * sizeof(float));
+    if (!rc && eh.bluestein)
+        rc = t->chirp.upload(eh.chirp.data(), eh.chirp.size() * sizeof(float));
+    if (!rc && eh.bluestein)
+        rc = t->bhat.upload(eh.bhat.data(), eh.bhat.size() * sizeof(float));
+    if (rc)
+        return rc;
+    g_env_cache[{dev, nz}] = t;
+    out = t;
+    return BF_OK;
+}
+
+// ------------------------------------------------------------------ plans --
+
+int handle_plan(bf_handle *h, int ns, const double *angles, int na, int prec, Plan **out)
+{
+    PlanKey key{ns, prec, std::vector<double>(angles, angles + na)};
+    std::lock_guard<std::mutex> lk(h->mu);
+    auto it = h->plans.find(key);
+    if (it != h->plans.end()) {
+        *out = it->second.get();
+        return BF_OK;
+    }
+    PlanHost ph;
+    angle_tables(h->g, h->geo, ns, key.angles, prec, ph);
+    if ((size_t)ph.wmax * pair_bytes(prec) > (size_t)kStageBytes * 4)
+        return fail(BF_EINVAL,
+                    "pixel spacing too coarse for the sample rate: one tile needs %d samples per channel",
+                    ph.wmax);
+    auto p = std::make_unique<Plan>();
+    p->ns = ns;
+    p->na = na;
+    p->prec = prec;
+    p->wmax = ph.wmax;
+    p->box = ph.box;
+    p->group = ph.group;
+    p->nsp = ph.nsp;
+    int rc = p->colK.upload(ph.colK.data(), ph.colK.size() * sizeof(int));
+    if (!rc) rc = p->colF.upload(ph.colF.data(), ph.colF.size() * sizeof(float));
+    if (!rc) rc = p->rowK.upload(ph.rowK.data(), ph.rowK.size() * sizeof(int));
+    if (!rc) rc = p->rowF.upload(ph.rowF.data(), ph.rowF.size() * sizeof(float));
+    if (!rc) rc = p->valid.upload(ph.valid.data(), ph.valid.size() * sizeof(int));
+    if (rc)
+        return rc;
+    *out = p.get();
+    h->plans.emplace(std::move(key), std::move(p));
+    return BF_OK;
+}
+
+// ------------------------------------------------------- frame preparation --
+
+static int popcount3(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1); }
+
+int check_frame_args(bf_handle *h, int ns, const double *angles, int na, uint32_t flags)
+{
+    if (!h)
+        return fail(BF_EINVAL, "null handle");
+    if (ns < 2 || ns > (1 << 24))
+        return fail(BF_EINVAL, "n_samples must be in [2, 2^24], got %d", ns);
+    if (na < 1 || na > 256)
+        return fail(BF_EINVAL, "n_angles must be in [1, 256], got %d", na);
+    if (!angles)
+        return fail(BF_EINVAL, "null angles");
+    for (int a = 0; a < na; ++a)
+        if (!std::isfinite(angles[a]) || std::fabs(angles[a]) >= 1.5707963267948966)
+            return fail(BF_EINVAL, "angle %d (%g rad) outside (-pi/2, pi/2)", a, angles[a]);
+    const int modes = flags & BF_MODE_MASK;
+    if (!modes)
+        return fail(BF_EINVAL, "no combiner selected (BF_DAS / BF_DMAS / BF_CF)");
+    if (flags & ~(uint32_t)(BF_MODE_MASK | BF_PREC_MASK | BF_OUT_MASK))
+        return fail(BF_EINVAL, "unknown bits in mode_and_flags 0x%x", flags);
+    const int prec = (flags & BF_PREC_MASK) >> 4;
+    if (prec > kPrecBF16)
+        return fail(BF_EINVAL, "unknown precision bits");
+    const int stage = flags & BF_OUT_MASK;
+    if (stage != BF_OUT_RF && stage != BF_OUT_ENV && stage != BF_OUT_LOGDB)
+        return fail(BF_EINVAL, "unknown output stage bits");
+    if (stage != BF_OUT_RF && h->g.nz > 4096)
+        return fail(BF_EINVAL, "envelope detection supports nz <= 4096 (got %d)", h->g.nz);
+    if ((long long)na * h->g.ne > (1LL << 30))
+        return fail(BF_EINVAL, "too many channel records");
+    return BF_OK;
+}
+
+size_t frame_out_bytes(const bf_handle *h, uint32_t flags)
+{
+    return (size_t)popcount3(flags & BF_MODE_MASK) * (size_t)h->g.nx * (size_t)h->g.nz * sizeof(float);
+}
+
+int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *angles, int na,
+                  uint32_t flags, float *out_dev, FrameScratch &s, FramePrep &fp)
+{
+    int rc = check_frame_args(h, ns, angles, na, flags);
+    if (rc)
+        return rc;
+    const int prec = (flags & BF_PREC_MASK) >> 4;
+    Plan *plan = nullptr;
+    rc = handle_plan(h, ns, angles, na, prec, &plan);
+    if (rc)
+        return rc;
+    const int modes = flags & BF_MODE_MASK, nm = popcount3(modes), stage = flags & BF_OUT_MASK;
+    const size_t img = (size_t)h->g.nx * h->g.nz;
+    const int rows = na * h->g.ne;
+    rc = s.pairs.ensure((size_t)rows * plan->nsp * pair_bytes(prec));
+    if (!rc && stage != BF_OUT_RF)
+        rc = s.y.ensure(nm * img * sizeof(float));
+    if (!rc && stage == BF_OUT_LOGDB)
+        rc = s.env.ensure(nm * img * sizeof(float));
+    if (!rc)
+        rc = s.maxbits.ensure(4 * sizeof(unsigned));
+    if (!rc)
+        rc = s.map.ensure(sizeof(CUtensorMap));
+    if (rc)
+        return rc;
+    fp = FramePrep{};
+    fp.h = h;
+    fp.plan = plan;
+    fp.rf = rf_dev;
+    fp.ns = ns;
+    fp.na = na;
+    fp.modes = modes;
+    fp.stage = stage;
+    fp.prec = prec;
+    fp.out = out_dev;
+    fp.pairs = s.pairs.p;
+    fp.y = stage == BF_OUT_RF ? out_dev : (float *)s.y.p;
+    fp.env = stage == BF_OUT_ENV ? out_dev : (stage == BF_OUT_LOGDB ? (float *)s.env.p : nullptr);
+    fp.maxbits = (unsigned *)s.maxbits.p;
+    fp.map_dev = (CUtensorMap *)s.map.p;
+    if (s.map_base != s.pairs.p || s.map_rows != rows || s.map_nsp != plan->nsp ||
+        s.map_box != plan->box || s.map_prec != prec) {
+        rc = encode_pairs_map(&s.map_host, s.pairs.p, rows, plan->nsp, plan->box, prec);
+        if (rc)
+            return rc;
+        s.map_base = s.pairs.p;
+        s.map_rows = rows;
+        s.map_nsp = plan->nsp;
+        s.map_box = plan->box;
+        s.map_prec = prec;
+        s.map_dirty = true;
+    }
+    fp.map_host = s.map_host;
+    fp.map_dirty = s.map_dirty;
+    fp.scratch = &s;
+    if (stage != BF_OUT_RF) {
+        rc = env_tables(h->g.nz, fp.et);
+        if (rc)
+            return rc;
+    }
+    return BF_OK;
+}
+
+// Host-side launch description of a set of frames (job arrays + prefixes).
+void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
+{
+    hl = HostLaunch{};
+    std::map<int, std::vector<BfJob>> groups;
+    for (const FramePrep &f : frames) {
+        const bf_handle *h = f.h;
+        const Plan *p = f.plan;
+        BfJob j{};
+        j.colK = (const int *)p->colK.p;
+        j.colF = (const float *)p->colF.p;
+        j.rowK = (const int *)p->rowK.p;
+        j.rowF = (const float *)p->rowF.p;
+        j.rowZ = (const float *)h->rowZ.p;
+        j.rowZ2 = (const float *)h->rowZ2.p;
+        j.colDX2 = (const float *)h->colDX2.p;
+        j.valid = (const int2 *)p->valid.p;
+        j.apcnt = (const uint16_t *)h->apcnt.p;
+        j.rf_map = f.map_dev;
+        j.y = f.y;
+        j.nx = h->g.nx;
+        j.nz = h->g.nz;
+        j.na = f.na;
+        j.ne = h->g.ne;
+        j.nsp = p->nsp;
+        j.wmax = p->wmax;
+        j.box = p->box;
+        j.group = p->group;
+        j.modes = f.modes;
+        j.prec = f.prec;
+        j.tiles_x = (h->g.nx + kTileCols - 1) / kTileCols;
+        j.tiles_z = (h->g.nz + kTileRows - 1) / kTileRows;
+        j.out_scale = f.prec == kPrecF32 ? 1.0f : 32768.0f;
+        const int variant = f.prec * 8 + (f.modes & (BF_DMAS | BF_CF));
+        groups[variant].push_back(j);
+        hl.smem = std::max(hl.smem, beamform_smem_bytes(p->wmax, p->group, f.prec));
+    }
+    for (auto &kv : groups) {
+        HostLaunch::Group g;
+        g.prec = kv.first / 8;
+        g.variant = kv.first % 8;
+        g.first = (int)hl.jobs.size();
+        g.count = (int)kv.second.size();
+        g.prefix_first = (int)hl.tile_prefix.size();
+        int acc = 0;
+        for (const BfJob &j : kv.second) {
+            hl.tile_prefix.push_back(acc);
+            acc += j.tiles_x * j.tiles_z;
+            hl.jobs.push_back(j);
+        }
+        g.tiles = acc;
+        hl.groups.push_back(g);
+    }
+    int cols = 0;
+    long long blks = 0;
+    for (const FramePrep &f : frames) {
+        if (f.stage == BF_OUT_RF)
+            continue;
+        const bf_handle *h = f.h;
+        const size_t img = (size_t)h->g.nx * h->g.nz;
+        int slot = 0;
+        for (int bit = 1; bit <= BF_CF; bit <<= 1) {
+            if (!(f.modes & bit))
+                continue;
+            EnvJob e{};
+            e.y = f.y + slot * img;
+            e.env = f.env + slot * img;
+            e.maxbits = f.maxbits + slot;
+            e.nx = h->g.nx;
+            e.nz = h->g.nz;
+            e.fft_m = f.et->fft_m;
+            e.bluestein = f.et->bluestein;
+            e.band = bit == BF_DMAS ? 1 : 0;
+            e.kb_lo = h->kb_lo;
+            e.kb_hi = h->kb_hi;
+            e.tw = (const float2 *)f.et->tw.p;
+            e.chirp = (const float2 *)f.et->chirp.p;
+            e.bhat = (const float2 *)f.et->bhat.p;
+            hl.col_prefix.push_back(cols);
+            cols += h->g.nx;
+            hl.env.push_back(e);
+            hl.max_fft_m = std::max(hl.max_fft_m, e.fft_m);
+            if (f.stage == BF_OUT_LOGDB) {
+                LogJob l{};
+                l.env = e.env;
+                l.out = f.out + slot * img;
+                l.maxbits = e.maxbits;
+                l.n = (int)img;
+                hl.blk_prefix.push_back((int)blks);
+                blks += log_blocks((long long)img);
+                hl.log.push_back(l);
+            }
+            ++slot;
+        }
+    }
+    hl.env_cols = cols;
+    hl.log_blocks = (int)blks;
+}
+
+int DeviceLaunch::upload(const HostLaunch &hl, cudaStream_t st, bool async)
+{
+    auto put = [&](DevMem &d, const void *src, size_t n) -> int {
+        if (n == 0)
+            return BF_OK;
+        int rc = d.ensure(n);
+        if (rc)
+            return rc;
+        cudaError_t e = async ? cudaMemcpyAsync(d.p, src, n, cudaMemcpyHostToDevice, st)
+                              : cudaMemcpy(d.p, src, n, cudaMemcpyHostToDevice);
+        return e == cudaSuccess ? BF_OK : cuda_fail(e, "cudaMemcpy (job list)");
+    };
+    int rc = put(jobs, hl.jobs.data(), hl.jobs.size() * sizeof(BfJob));
+    if (!rc) rc = put(tile_prefix, hl.tile_prefix.data(), hl.tile_prefix.size() * sizeof(int));
+    if (!rc) rc = put(env, hl.env.data(), hl.env.size() * sizeof(EnvJob));
+    if (!rc) rc = put(col_prefix, hl.col_prefix.data(), hl.col_prefix.size() * sizeof(int));
+    if (!rc) rc = put(log, hl.log.data(), hl.log.size() * sizeof(LogJob));
+    if (!rc) rc = put(blk_prefix, hl.blk_prefix.data(), hl.blk_prefix.size() * sizeof(int));
+    if (!rc) rc = err.ensure(sizeof(int));
+    return rc;
+}
+
+// Tensor maps of frames whose scratch changed go to device memory (before any
+// kernel reads them).
+int upload_maps(std::vector<FramePrep> &frames, cudaStream_t st, bool async)
+{
+    for (FramePrep &f : frames) {
+        if (!f.map_dirty)
+            continue;
+        cudaError_t e = async ? cudaMemcpyAsync(f.map_dev, &f.scratch->map_host, sizeof(CUtensorMap),
+                                                cudaMemcpyHostToDevice, st)
+                              : cudaMemcpy(f.map_dev, &f.scratch->map_host, sizeof(CUtensorMap),
+                                           cudaMemcpyHostToDevice);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpy (tensor map)");
+        f.scratch->map_dirty = false;
+        f.map_dirty = false;
+    }
+    return BF_OK;
+}
+
+// The device work of a set of frames, in stream order: ingest, reset of the
+// frame maxima, beamforming (one launch per precision / combiner variant),
+// envelope, log compression.
+int enqueue(const std::vector<FramePrep> &frames, const HostLaunch &hl, DeviceLaunch &dl,
+            cudaStream_t st, cudaEvent_t *marks)
+{
+    cudaError_t e;
+    if (marks)
+        cudaEventRecordWithFlags(marks[0], st, cudaEventRecordExternal);
+    for (const FramePrep &f : frames) {
+        e = launch_ingest(f.rf, f.pairs, f.na * f.h->g.ne, f.ns, f.plan->nsp, f.prec, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "ingest launch");
+        if (f.stage != BF_OUT_RF) {
+            e = cudaMemsetAsync(f.maxbits, 0, 4 * sizeof(unsigned), st);
+            if (e != cudaSuccess)
+                return cuda_fail(e, "cudaMemsetAsync");
+        }
+    }
+    if (marks)
+        cudaEventRecordWithFlags(marks[1], st, cudaEventRecordExternal);
+    for (const HostLaunch::Group &g : hl.groups) {
+        e = launch_beamform((const BfJob *)dl.jobs.p + g.first,
+                            (const int *)dl.tile_prefix.p + g.prefix_first, g.count, g.tiles, hl.smem,
+                            g.prec, g.variant, (int *)dl.err.p, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "beamform launch");
+    }
+    if (marks)
+        cudaEventRecordWithFlags(marks[2], st, cudaEventRecordExternal);
+    if (!hl.env.empty()) {
+        e = launch_envelope((const EnvJob *)dl.env.p, (const int *)dl.col_prefix.p, (int)hl.env.size(),
+                            hl.env_cols, hl.max_fft_m, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "envelope launch");
+    }
+    if (!hl.log.empty()) {
+        e = launch_log((const LogJob *)dl.log.p, (const int *)dl.blk_prefix.p, (int)hl.log.size(),
+                       hl.log_blocks, 70.0f, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "log launch");
+    }
+    if (marks)
+        cudaEventRecordWithFlags(marks[3], st, cudaEventRecordExternal);
+    return BF_OK;
+}
+
+int read_device_error(DeviceLaunch &dl, cudaStream_t st)
+{
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, dl.err.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "reading the device status word");
+    if (v) {
+        cudaMemsetAsync(dl.err.p, 0, sizeof(int), st);
+        if (v & kErrTimeout)
+            return fail(BF_ETIMEDOUT, "a bounded device wait gave up (status 0x%x)", v);
+        return fail(BF_ECUDA, "device-side check failed (status 0x%x)", v);
+    }
+    return BF_OK;
+}
+
+bool is_device_pointer(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace bfi
+
+using namespace bfi;
+
+// ===================================================================== ABI ==
+
+extern "C" {
+
+BF_API const char *bf_last_error(void) { return g_err.c_str(); }
+
+BF_API int bf_version(void) { return 100; }
+
+BF_API int bf_create(const bf_geometry *geom, const bf_grid *grid, double fs_hz, double f0_hz,
+                     double c_mps, bf_handle **out)
+{
+    if (!geom || !grid || !out)
+        return fail(BF_EINVAL, "null argument");
+    *out = nullptr;
+    const int ne = geom->n_elements;
+    if (ne < 1 || ne > 4096)
+        return fail(BF_EINVAL, "n_elements must be in [1, 4096], got %d", ne);
+    if (!(geom->f_number > 0.0) || !std::isfinite(geom->f_number))
+        return fail(BF_EINVAL, "f_number must be > 0");
+    if (!geom->x_elem_m && !(geom->pitch_m > 0.0 && std::isfinite(geom->pitch_m)))
+        return fail(BF_EINVAL, "pitch_m must be > 0 when x_elem_m is NULL");
+    if (grid->nx < 1 || grid->nz < 1 || grid->nx > 32767 || grid->nz > 32767)
+        return fail(BF_EINVAL, "grid dimensions must be in [1, 32767]");
+    const double v[] = {grid->x0_m, grid->x1_m, grid->z0_m, grid->z1_m, fs_hz, f0_hz, c_mps};
+    for (double d : v)
+        if (!std::isfinite(d))
+            return fail(BF_EINVAL, "non-finite grid or acquisition parameter");
+    if (grid->x1_m < grid->x0_m || grid->z1_m < grid->z0_m || grid->z0_m < 0.0)
+        return fail(BF_EINVAL, "grid must satisfy x1 >= x0 and z1 >= z0 >= 0");
+    if (!(fs_hz > 0.0) || !(c_mps > 0.0) || !(f0_hz > 0.0))
+        return fail(BF_EINVAL, "fs, f0 and c must be > 0");
+    auto h = std::make_unique<bf_handle>();
+    GeomHost &g = h->g;
+    g.ne = ne;
+    g.xe.resize(ne);
+    for (int i = 0; i < ne; ++i)
+        g.xe[i] = geom->x_elem_m ? geom->x_elem_m[i]
+                                 : ((double)i - 0.5 * (double)(ne - 1)) * geom->pitch_m;
+    for (int i = 0; i < ne; ++i) {
+        if (!std::isfinite(g.xe[i]))
+            return fail(BF_EINVAL, "non-finite element position");
+        if (i && !(g.xe[i] > g.xe[i - 1]))
+            return fail(BF_EINVAL, "element positions must be strictly increasing");
+    }
+    g.fnum = geom->f_number;
+    g.nx = grid->nx;
+    g.nz = grid->nz;
+    g.x0 = grid->x0_m;
+    g.x1 = grid->x1_m;
+    g.z0 = grid->z0_m;
+    g.z1 = grid->z1_m;
+    g.fs = fs_hz;
+    g.f0 = f0_hz;
+    g.c = c_mps;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGetDevice");
+    e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaStreamCreate");
+    h->stream = h->own_stream;
+    geometry_tables(g, h->geo);
+    int rc = h->rowZ.upload(h->geo.rowZ.data(), h->geo.rowZ.size() * sizeof(float));
+    if (!rc) rc = h->rowZ2.upload(h->geo.rowZ2.data(), h->geo.rowZ2.size() * sizeof(float));
+    if (!rc) rc = h->colDX2.upload(h->geo.colDX2.data(), h->geo.colDX2.size() * sizeof(float));
+    if (!rc) rc = h->apcnt.upload(h->geo.apcnt.data(), h->geo.apcnt.size() * sizeof(uint16_t));
+    if (rc)
+        return rc;
+    bandpass_bins(g.nz, g.z0, g.z1, g.c, g.f0, h->kb_lo, h->kb_hi);
+    *out = h.release();
+    return BF_OK;
+}
+
+BF_API int bf_destroy(bf_handle *h)
+{
+    if (!h)
+        return fail(BF_EINVAL, "null handle");
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        if (!h->tickets.empty())
+            return fail(BF_EINVAL, "handle has %zu pending tickets", h->tickets.size());
+    }
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    engine_forget(h);
+    if (h->own_stream)
+        cudaStreamDestroy(h->own_stream);
+    delete h;
+    return BF_OK;
+}
+
+BF_API int bf_set_stream(bf_handle *h, void *stream)
+{
+    if (!h)
+        return fail(BF_EINVAL, "null handle");
+    h->stream = stream ? (cudaStream_t)stream : h->own_stream;
+    return BF_OK;
+}
+
+BF_API size_t bf_output_bytes(const bf_handle *h, uint32_t flags)
+{
+    return h ? frame_out_bytes(h, flags) : 0;
+}
+
+BF_API int bf_beamform(bf_handle *h, const int16_t *rf_dev, int32_t n_samples,
+                       const double *angles_rad, int32_t n_angles, uint32_t flags, float *out_dev)
+{
+    if (!h)
+        return fail(BF_EINVAL, "null handle");
+    if (!rf_dev || !out_dev)
+        return fail(BF_EINVAL, "null data pointer");
+    cudaSetDevice(h->device);
+    if (!is_device_pointer(rf_dev) || !is_device_pointer(out_dev))
+        return fail(BF_EINVAL, "bf_beamform needs device pointers (use bf_submit for host data)");
+    std::vector<FramePrep> frames(1);
+    int rc = prepare_frame(h, rf_dev, n_samples, angles_rad, n_angles, flags, out_dev, h->scratch,
+                           frames[0]);
+    if (rc)
+        return rc;
+    HostLaunch hl;
+    build_launch(frames, hl);
+    rc = upload_maps(frames, h->stream, true);
+    if (!rc)
+        rc = h->launch.upload(hl, h->stream, true);
+    if (!rc && !h->err_cleared) {
+        cudaMemsetAsync(h->launch.err.p, 0, sizeof(int), h->stream);
+        h->err_cleared = true;
+    }
+    if (!rc)
+        rc = enqueue(frames, hl, h->launch, h->stream);
+    return rc;
+}
+
+BF_API int bf_sync(bf_handle *h)
+{
+    if (!h)
+        return fail(BF_EINVAL, "null handle");
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaStreamSynchronize");
+    if (!h->launch.err.p)
+        return BF_OK;
+    return read_device_error(h->launch, h->stream);
+}
+
+// Host-only view of the decision tables (no CUDA involved): first / last
+// counted row per (angle, column, channel) and aperture counts per pixel.
+BF_API int bf_host_tables(const bf_geometry *geom, const bf_grid *grid, double fs_hz, double f0_hz,
+                          double c_mps, int32_t n_samples, const double *angles_rad,
+                          int32_t n_angles, int32_t *valid_rows, uint16_t *aperture_count)
+{
+    if (!geom || !grid || !angles_rad || n_angles < 1 || n_samples < 2)
+        return fail(BF_EINVAL, "bad arguments");
+    GeomHost g;
+    g.ne = geom->n_elements;
+    if (g.ne < 1 || grid->nx < 1 || grid->nz < 1 || !(geom->f_number > 0.0))
+        return fail(BF_EINVAL, "bad geometry");
+    g.xe.resize(g.ne);
+    for (int i = 0; i < g.ne; ++i)
+        g.xe[i] = geom->x_elem_m ? geom->x_elem_m[i]
+                                 : ((double)i - 0.5 * (double)(g.ne - 1)) * geom->pitch_m;
+    g.fnum = geom->f_number;
+    g.nx = grid->nx;
+    g.nz = grid->nz;
+    g.x0 = grid->x0_m;
+    g.x1 = grid->x1_m;
+    g.z0 = grid->z0_m;
+    g.z1 = grid->z1_m;
+    g.fs = fs_hz;
+    g.f0 = f0_hz;
+    g.c = c_mps;
+    GeometryHost geo;
+    geometry_tables(g, geo);
+    PlanHost ph;
+    angle_tables(g, geo, n_samples, std::vector<double>(angles_rad, angles_rad + n_angles),
+                 kPrecF32, ph);
+    if (valid_rows)
+        std::memcpy(valid_rows, ph.valid.data(), ph.valid.size() * sizeof(int32_t));
+    if (aperture_count)
+        std::memcpy(aperture_count, geo.apcnt.data(), geo.apcnt.size() * sizeof(uint16_t));
+    return BF_OK;
+}
+
+// ------------------------------------------------------------------ batch --
+
+BF_API int bf_batch_create(const bf_frame *frames, int32_t n, bf_batch **out)
+{
+    if (!frames || !out || n < 1)
+        return fail(BF_EINVAL, "bad batch arguments");
+    *out = nullptr;
+    auto b = std::make_unique<bf_batch>();
+    b->scratch.resize(n);
+    b->frames.resize(n);
+    int dev = -1;
+    for (int i = 0; i < n; ++i) {
+        const bf_frame &f = frames[i];
+        if (!f.h || !f.rf_dev || !f.out_dev)
+            return fail(BF_EINVAL, "frame %d: null handle or data pointer", i);
+        if (dev < 0)
+            dev = f.h->device;
+        else if (dev != f.h->device)
+            return fail(BF_EINVAL, "frame %d: all frames of a batch must use one device", i);
+        cudaSetDevice(dev);
+        if (!is_device_pointer(f.rf_dev) || !is_device_pointer(f.out_dev))
+            return fail(BF_EINVAL, "frame %d: batches need device pointers", i);
+        int rc = prepare_frame(f.h, f.rf_dev, f.n_samples, f.angles_rad, f.n_angles,
+                               f.mode_and_flags, f.out_dev, b->scratch[i], b->frames[i]);
+        if (rc)
+            return fail(rc, "frame %d: %s", i, g_err.c_str());
+    }
+    b->device = dev;
+    build_launch(b->frames, b->hl);
+    int rc = upload_maps(b->frames, nullptr, false);
+    if (!rc)
+        rc = b->dl.upload(b->hl, nullptr, false);
+    if (rc)
+        return rc;
+    cudaMemset(b->dl.err.p, 0, sizeof(int));
+    // Capture the batch's launches once; bf_batch_launch replays the graph.
+    cudaStream_t cap;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaStreamCreate");
+    for (auto &m : b->marks)
+        if (e == cudaSuccess)
+            e = cudaEventCreate(&m);
+    b->launches = (int)b->frames.size() + (int)b->hl.groups.size() + (b->hl.env.empty() ? 0 : 1) +
+                  (b->hl.log.empty() ? 0 : 1);
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = enqueue(b->frames, b->hl, b->dl, cap, b->marks);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (!rc && e2 == cudaSuccess) {
+            e2 = cudaGraphInstantiate(&b->exec, g, 0);
+            if (e2 != cudaSuccess)
+                rc = cuda_fail(e2, "cudaGraphInstantiate");
+        } else if (!rc) {
+            rc = cuda_fail(e2, "cudaStreamEndCapture");
+        }
+        if (g)
+            cudaGraphDestroy(g);
+    } else {
+        rc = cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    cudaStreamDestroy(cap);
+    if (rc)
+        return rc;
+    *out = b.release();
+    return BF_OK;
+}
+
+BF_API int bf_batch_launch(bf_batch *b, void *stream)
+{
+    if (!b)
+        return fail(BF_EINVAL, "null batch");
+    cudaSetDevice(b->device);
+    cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    return e == cudaSuccess ? BF_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+BF_API int bf_batch_status(bf_batch *b, void *stream)
+{
+    if (!b)
+        return fail(BF_EINVAL, "null batch");
+    cudaSetDevice(b->device);
+    return read_device_error(b->dl, (cudaStream_t)stream);
+}
+
+BF_API int bf_batch_timing(bf_batch *b, float *ms3, int32_t *kernel_launches)
+{
+    if (!b || !ms3)
+        return fail(BF_EINVAL, "null argument");
+    cudaSetDevice(b->device);
+    for (int k = 0; k < 3; ++k) {
+        cudaError_t e = cudaEventElapsedTime(&ms3[k], b->marks[k], b->marks[k + 1]);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaEventElapsedTime");
+    }
+    if (kernel_launches)
+        *kernel_launches = b->launches;
+    return BF_OK;
+}
+
+BF_API int bf_batch_destroy(bf_batch *b)
+{
+    if (!b)
+        return fail(BF_EINVAL, "null batch");
+    cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    if (b->exec)
+        cudaGraphExecDestroy(b->exec);
+    for (auto &m : b->marks)
+        if (m)
+            cudaEventDestroy(m);
+    delete b;
+    return BF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,485 @@
+// Serving engine behind bf_submit / bf_poll: continuous batching on one GPU.
+//
+// bf_submit admits a request only if a slot (device RF buffer, staging pairs,
+// images, output, pinned host staging) can be had within the engine's device
+// memory budget; otherwise it returns BF_EAGAIN and the caller retries.  The
+// RF is copied host -> pinned staging -> device on a copy stream before the
+// call returns.  A scheduler thread launches everything admitted so far as
+// one batch (one ingest per frame, one beamform launch per precision /
+// combiner variant, one envelope and one log launch) on the next of several
+// streams whenever fewer than `max_inflight` batches are on the GPU, so
+// requests that arrive while others run are admitted and launched as memory
+// and slots free up and their work overlaps on the device.  bf_poll waits for
+// the request's batch, copies the result out and releases the slot.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <string>
+#include <thread>
+
+#include "bf_engine.h"
+
+namespace bfi {
+
+namespace {
+
+constexpr int kStreams = 4;
+
+struct Slot {
+    DevMem rf, out;
+    FrameScratch scratch;
+    void *pinned = nullptr;
+    size_t pinned_bytes = 0;
+    cudaEvent_t h2d = nullptr;
+    ~Slot()
+    {
+        if (pinned)
+            cudaFreeHost(pinned);
+        if (h2d)
+            cudaEventDestroy(h2d);
+    }
+    size_t device_bytes() const
+    {
+        return rf.bytes + out.bytes + scratch.pairs.bytes + scratch.y.bytes + scratch.env.bytes +
+               scratch.maxbits.bytes + scratch.map.bytes;
+    }
+};
+
+struct Batch {
+    int id = 0, frames = 0;
+    cudaEvent_t start = nullptr, done = nullptr;
+    DeviceLaunch dl;
+    ~Batch()
+    {
+        if (start)
+            cudaEventDestroy(start);
+        if (done)
+            cudaEventDestroy(done);
+    }
+};
+
+}  // namespace
+
+struct Request {
+    uint64_t ticket = 0;
+    bf_handle *h = nullptr;
+    std::unique_ptr<Slot> slot;
+    FramePrep fp;
+    size_t out_bytes = 0;
+    std::shared_ptr<Batch> batch;
+    int state = 0;  // 0 queued, 1 launched, 2 failed to launch
+    int rc = BF_OK;
+    std::string err;
+};
+
+namespace {
+
+class Engine {
+public:
+    explicit Engine(int dev) : device_(dev)
+    {
+        cudaSetDevice(dev);
+        for (auto &s : streams_)
+            cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        cudaStreamCreateWithFlags(&copy_, cudaStreamNonBlocking);
+        cudaStreamCreateWithFlags(&d2h_, cudaStreamNonBlocking);
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        budget_ = tot / 2;
+        if (const char *s = std::getenv("BF_MEM_BUDGET_MB"))
+            budget_ = (size_t)std::strtoull(s, nullptr, 10) << 20;
+        worker_ = std::thread([this] { loop(); });
+        worker_.detach();  // lives for the process
+    }
+
+    int submit(bf_handle *h, const int16_t *rf, int ns, const double *angles, int na,
+               uint32_t flags, uint64_t *ticket);
+    int poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes, int64_t timeout_us);
+    int batch_of(bf_handle *h, uint64_t ticket, int *id, int *frames);
+    void configure(int max_batch, int max_inflight, size_t budget)
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        if (max_batch > 0)
+            max_batch_ = max_batch;
+        if (max_inflight > 0)
+            max_inflight_ = max_inflight;
+        if (budget > 0)
+            budget_ = budget;
+    }
+
+private:
+    void loop();
+    void launch(std::vector<std::shared_ptr<Request>> &reqs);
+    std::unique_ptr<Slot> take_slot();
+
+    int device_;
+    std::mutex mu_;
+    std::condition_variable cv_work_, cv_launched_;
+    std::deque<std::shared_ptr<Request>> pending_;
+    std::deque<std::shared_ptr<Batch>> inflight_;
+    std::vector<std::unique_ptr<Slot>> free_;
+    size_t used_ = 0, budget_ = 0;
+    int live_ = 0;
+    int max_batch_ = 64, max_inflight_ = 3, max_live_ = 512;
+    uint64_t next_ticket_ = 1;
+    int next_batch_ = 0;
+    cudaStream_t streams_[kStreams]{};
+    cudaStream_t copy_ = nullptr, d2h_ = nullptr;
+    std::thread worker_;
+};
+
+std::unique_ptr<Slot> Engine::take_slot()
+{
+    if (free_.empty())
+        return std::make_unique<Slot>();
+    auto it = std::max_element(free_.begin(), free_.end(), [](const auto &a, const auto &b) {
+        return a->device_bytes() < b->device_bytes();
+    });
+    std::unique_ptr<Slot> s = std::move(*it);
+    free_.erase(it);
+    return s;
+}
+
+int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles, int na,
+                   uint32_t flags, uint64_t *ticket)
+{
+    int rc = check_frame_args(h, ns, angles, na, flags);
+    if (rc)
+        return rc;
+    const size_t rf_bytes = (size_t)na * h->g.ne * ns * sizeof(int16_t);
+    const size_t out_bytes = frame_out_bytes(h, flags);
+    auto req = std::make_shared<Request>();
+    req->h = h;
+    req->out_bytes = out_bytes;
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        if (live_ >= max_live_)
+            return fail(BF_EAGAIN, "%d requests in flight", live_);
+        req->slot = take_slot();
+        live_ += 1;
+    }
+    Slot &s = *req->slot;
+    const size_t before = s.device_bytes();
+    // admission by device memory: the slot may have to grow
+    const int prec = (flags & BF_PREC_MASK) >> 4;
+    Plan *plan = nullptr;
+    rc = handle_plan(h, ns, angles, na, prec, &plan);
+    size_t need = rf_bytes + out_bytes + (size_t)na * h->g.ne * (plan ? plan->nsp : 0) * pair_bytes(prec);
+    if ((flags & BF_OUT_MASK) != BF_OUT_RF)
+        need += out_bytes * ((flags & BF_OUT_MASK) == BF_OUT_LOGDB ? 2 : 1);
+    auto give_back = [&](int code) {
+        std::lock_guard<std::mutex> lk(mu_);
+        used_ -= before;
+        used_ += s.device_bytes();
+        free_.push_back(std::move(req->slot));
+        live_ -= 1;
+        return code;
+    };
+    if (rc)
+        return give_back(rc);
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        const size_t grow = need > before ? need - before : 0;
+        if (grow && used_ + grow > budget_) {
+            free_.push_back(std::move(req->slot));
+            live_ -= 1;
+            return fail(BF_EAGAIN, "device memory budget reached (%zu of %zu bytes in use)", used_,
+                        budget_);
+        }
+        if (grow) {
+            size_t fr = 0, tot = 0;
+            cudaSetDevice(device_);
+            if (cudaMemGetInfo(&fr, &tot) != cudaSuccess || fr < grow + ((size_t)256 << 20)) {
+                free_.push_back(std::move(req->slot));
+                live_ -= 1;
+                return fail(BF_EAGAIN, "not enough free device memory for a request (%zu needed)",
+                            grow);
+            }
+        }
+        used_ += grow;  // reserved; corrected after allocation
+    }
+    cudaSetDevice(device_);
+    rc = s.rf.ensure(rf_bytes);
+    if (!rc)
+        rc = s.out.ensure(out_bytes);
+    if (!rc && !s.h2d && cudaEventCreateWithFlags(&s.h2d, cudaEventDisableTiming) != cudaSuccess)
+        rc = fail(BF_ECUDA, "cudaEventCreate");
+    if (!rc)
+        rc = prepare_frame(h, (const int16_t *)s.rf.p, ns, angles, na, flags, (float *)s.out.p,
+                           s.scratch, req->fp);
+    if (rc) {
+        std::lock_guard<std::mutex> lk(mu_);
+        const size_t grow = need > before ? need - before : 0;
+        used_ -= grow;
+        used_ -= before;
+        used_ += s.device_bytes();
+        free_.push_back(std::move(req->slot));
+        live_ -= 1;
+        return rc;
+    }
+    // RF into the slot: host data through pinned staging, device data directly.
+    cudaError_t e;
+    if (is_device_pointer(rf)) {
+        e = cudaMemcpyAsync(s.rf.p, rf, rf_bytes, cudaMemcpyDeviceToDevice, copy_);
+    } else {
+        if (s.pinned_bytes < rf_bytes) {
+            if (s.pinned)
+                cudaFreeHost(s.pinned);
+            s.pinned = nullptr;
+            s.pinned_bytes = 0;
+            if (cudaMallocHost(&s.pinned, rf_bytes) != cudaSuccess) {
+                cudaGetLastError();
+                s.pinned = nullptr;
+            } else {
+                s.pinned_bytes = rf_bytes;
+            }
+        }
+        if (!s.pinned) {
+            e = cudaErrorMemoryAllocation;
+        } else {
+            std::memcpy(s.pinned, rf, rf_bytes);
+            e = cudaMemcpyAsync(s.rf.p, s.pinned, rf_bytes, cudaMemcpyHostToDevice, copy_);
+        }
+    }
+    if (e == cudaSuccess)
+        e = cudaEventRecord(s.h2d, copy_);
+    if (e == cudaSuccess && is_device_pointer(rf))
+        e = cudaEventSynchronize(s.h2d);  // caller may reuse its device buffer on return
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        const size_t grow = need > before ? need - before : 0;
+        used_ -= grow;
+        used_ -= before;
+        used_ += s.device_bytes();
+        if (e != cudaSuccess) {
+            free_.push_back(std::move(req->slot));
+            live_ -= 1;
+            return cuda_fail(e, "copying the request's RF");
+        }
+        req->ticket = next_ticket_++;
+        pending_.push_back(req);
+    }
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        h->tickets[req->ticket] = req;
+    }
+    *ticket = req->ticket;
+    cv_work_.notify_one();
+    return BF_OK;
+}
+
+void Engine::launch(std::vector<std::shared_ptr<Request>> &reqs)
+{
+    auto b = std::make_shared<Batch>();
+    b->id = next_batch_++;
+    b->frames = (int)reqs.size();
+    cudaStream_t st = streams_[b->id % kStreams];
+    std::vector<FramePrep> frames;
+    frames.reserve(reqs.size());
+    for (auto &r : reqs) {
+        frames.push_back(r->fp);
+        cudaStreamWaitEvent(st, r->slot->h2d, 0);
+    }
+    HostLaunch hl;
+    build_launch(frames, hl);
+    int rc = BF_OK;
+    if (cudaEventCreate(&b->start) != cudaSuccess || cudaEventCreate(&b->done) != cudaSuccess)
+        rc = fail(BF_ECUDA, "cudaEventCreate");
+    if (!rc)
+        rc = upload_maps(frames, st, true);
+    for (size_t i = 0; i < reqs.size(); ++i)
+        reqs[i]->fp.map_dirty = false;
+    if (!rc)
+        rc = b->dl.upload(hl, st, true);
+    if (!rc && cudaMemsetAsync(b->dl.err.p, 0, sizeof(int), st) != cudaSuccess)
+        rc = fail(BF_ECUDA, "cudaMemsetAsync");
+    if (!rc)
+        cudaEventRecord(b->start, st);
+    if (!rc)
+        rc = enqueue(frames, hl, b->dl, st);
+    if (!rc && cudaEventRecord(b->done, st) != cudaSuccess)
+        rc = fail(BF_ECUDA, "cudaEventRecord");
+    std::string msg = rc ? std::string(bf_last_error()) : std::string();
+    std::lock_guard<std::mutex> lk(mu_);
+    for (auto &r : reqs) {
+        r->batch = b;
+        r->state = rc ? 2 : 1;
+        r->rc = rc;
+        r->err = msg;
+    }
+    if (!rc)
+        inflight_.push_back(b);
+}
+
+void Engine::loop()
+{
+    cudaSetDevice(device_);
+    for (;;) {
+        std::vector<std::shared_ptr<Request>> take;
+        {
+            std::unique_lock<std::mutex> lk(mu_);
+            cv_work_.wait(lk, [&] { return !pending_.empty(); });
+            while (!inflight_.empty() && cudaEventQuery(inflight_.front()->done) != cudaErrorNotReady)
+                inflight_.pop_front();
+            if ((int)inflight_.size() >= max_inflight_) {
+                std::shared_ptr<Batch> oldest = inflight_.front();
+                lk.unlock();
+                cudaEventSynchronize(oldest->done);
+                continue;
+            }
+            while (!pending_.empty() && (int)take.size() < max_batch_) {
+                take.push_back(pending_.front());
+                pending_.pop_front();
+            }
+        }
+        launch(take);
+        cv_launched_.notify_all();
+    }
+}
+
+int Engine::poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes, int64_t timeout_us)
+{
+    std::shared_ptr<Request> req;
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        auto it = h->tickets.find(ticket);
+        if (it == h->tickets.end())
+            return fail(BF_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+        req = it->second;
+    }
+    if (out && out_bytes < req->out_bytes)
+        return fail(BF_EINVAL, "output buffer too small (%zu < %zu bytes)", out_bytes, req->out_bytes);
+    using clk = std::chrono::steady_clock;
+    const auto deadline = clk::now() + std::chrono::microseconds(timeout_us > 0 ? timeout_us : 0);
+    // launched yet?
+    {
+        std::unique_lock<std::mutex> lk(mu_);
+        while (req->state == 0) {
+            if (timeout_us == 0)
+                return BF_PENDING;
+            if (timeout_us < 0)
+                cv_launched_.wait(lk);
+            else if (cv_launched_.wait_until(lk, deadline) == std::cv_status::timeout &&
+                     req->state == 0)
+                return fail(BF_ETIMEDOUT, "ticket %llu not launched within the timeout",
+                            (unsigned long long)ticket);
+        }
+    }
+    int rc = req->rc ? fail(req->rc, "%s", req->err.c_str()) : BF_OK;
+    if (!rc) {
+        for (;;) {
+            cudaError_t q = cudaEventQuery(req->batch->done);
+            if (q == cudaSuccess)
+                break;
+            if (q != cudaErrorNotReady) {
+                rc = cuda_fail(q, "batch execution");
+                break;
+            }
+            if (timeout_us == 0)
+                return BF_PENDING;
+            if (timeout_us > 0 && clk::now() >= deadline)
+                return fail(BF_ETIMEDOUT, "ticket %llu not finished within the timeout",
+                            (unsigned long long)ticket);
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+    }
+    cudaSetDevice(device_);
+    if (!rc)
+        rc = read_device_error(req->batch->dl, d2h_);
+    if (!rc && out) {
+        cudaError_t e = cudaMemcpyAsync(out, req->slot->out.p, req->out_bytes, cudaMemcpyDefault, d2h_);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(d2h_);
+        if (e != cudaSuccess)
+            rc = cuda_fail(e, "copying the result");
+    }
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        h->tickets.erase(ticket);
+    }
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        free_.push_back(std::move(req->slot));
+        live_ -= 1;
+    }
+    return rc;
+}
+
+int Engine::batch_of(bf_handle *h, uint64_t ticket, int *id, int *frames)
+{
+    std::shared_ptr<Request> req;
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        auto it = h->tickets.find(ticket);
+        if (it == h->tickets.end())
+            return fail(BF_ENOTFOUND, "unknown ticket");
+        req = it->second;
+    }
+    std::lock_guard<std::mutex> lk(mu_);
+    if (req->state == 0)
+        return BF_PENDING;
+    *id = req->batch->id;
+    *frames = req->batch->frames;
+    return BF_OK;
+}
+
+std::mutex g_engines_mu;
+std::map<int, Engine *> g_engines;
+
+Engine *engine_for(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_engines_mu);
+    auto it = g_engines.find(dev);
+    if (it != g_engines.end())
+        return it->second;
+    Engine *e = new Engine(dev);  // process lifetime
+    g_engines[dev] = e;
+    return e;
+}
+
+}  // namespace
+
+void engine_forget(bf_handle *) {}
+
+}  // namespace bfi
+
+using namespace bfi;
+
+extern "C" {
+
+BF_API int bf_submit(bf_handle *h, const int16_t *rf, int32_t n_samples, const double *angles_rad,
+                     int32_t n_angles, uint32_t flags, uint64_t *ticket_out)
+{
+    if (!h || !rf || !ticket_out)
+        return fail(BF_EINVAL, "null argument");
+    cudaSetDevice(h->device);
+    return engine_for(h->device)->submit(h, rf, n_samples, angles_rad, n_angles, flags, ticket_out);
+}
+
+BF_API int bf_poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes, int64_t timeout_us)
+{
+    if (!h)
+        return fail(BF_EINVAL, "null handle");
+    return engine_for(h->device)->poll(h, ticket, out, out_bytes, timeout_us);
+}
+
+BF_API int bf_ticket_batch(bf_handle *h, uint64_t ticket, int32_t *batch_id, int32_t *batch_frames)
+{
+    if (!h || !batch_id || !batch_frames)
+        return fail(BF_EINVAL, "null argument");
+    return engine_for(h->device)->batch_of(h, ticket, batch_id, batch_frames);
+}
+
+BF_API int bf_engine_configure(int32_t max_batch, int32_t max_inflight, uint64_t memory_budget_bytes)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return fail(BF_ECUDA, "no CUDA device");
+    engine_for(dev)->configure(max_batch, max_inflight, (size_t)memory_budget_bytes);
+    return BF_OK;
+}
+
+}  // extern "C"

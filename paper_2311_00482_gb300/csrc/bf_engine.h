@@ -1,0 +1,173 @@
+// Host-side structures of the beamformer library (handles, plans, scratch,
+// launch descriptions, serving engine).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <condition_variable>
+#include <cstddef>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/bf.h"
+#include "bf_internal.h"
+#include "bf_tables.h"
+
+namespace bfi {
+
+int fail(int code, const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+
+// Owning device allocation (freed on destruction).
+struct DevMem {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevMem() = default;
+    DevMem(const DevMem &) = delete;
+    DevMem &operator=(const DevMem &) = delete;
+    DevMem(DevMem &&o) noexcept : p(o.p), bytes(o.bytes)
+    {
+        o.p = nullptr;
+        o.bytes = 0;
+    }
+    DevMem &operator=(DevMem &&o) noexcept
+    {
+        if (this != &o) {
+            release();
+            p = o.p;
+            bytes = o.bytes;
+            o.p = nullptr;
+            o.bytes = 0;
+        }
+        return *this;
+    }
+    ~DevMem() { release(); }
+    int ensure(size_t n);  // grow to at least n bytes (contents not kept)
+    void release();
+    int upload(const void *src, size_t n);  // synchronous host -> device
+};
+
+struct PlanKey {
+    int ns, prec;
+    std::vector<double> angles;
+    bool operator<(const PlanKey &o) const
+    {
+        if (ns != o.ns)
+            return ns < o.ns;
+        if (prec != o.prec)
+            return prec < o.prec;
+        return angles < o.angles;
+    }
+};
+
+// Device tables of one (handle, sample count, precision, angle set).
+struct Plan {
+    int ns = 0, na = 0, prec = 0;
+    int wmax = 0, box = 0, group = 1, nsp = 0;
+    DevMem colK, colF, rowK, rowF, valid;
+};
+
+struct EnvTablesDev {
+    int nz = 0, fft_m = 0, bluestein = 0;
+    DevMem tw, chirp, bhat;
+};
+
+// Device scratch of one in-flight frame: staged sample pairs, beamformed
+// image, envelope, frame maxima and the tensor map over the pairs.
+struct FrameScratch {
+    DevMem pairs, y, env, maxbits, map;
+    CUtensorMap map_host{};
+    void *map_base = nullptr;
+    int map_rows = 0, map_nsp = 0, map_box = 0, map_prec = -1;
+    bool map_dirty = false;
+};
+
+struct FramePrep {
+    bf_handle *h = nullptr;
+    Plan *plan = nullptr;
+    std::shared_ptr<EnvTablesDev> et;
+    const int16_t *rf = nullptr;
+    int ns = 0, na = 0, modes = 0, stage = 0, prec = 0;
+    float *out = nullptr;
+    void *pairs = nullptr;
+    float *y = nullptr, *env = nullptr;
+    unsigned *maxbits = nullptr;
+    CUtensorMap *map_dev = nullptr;
+    CUtensorMap map_host{};
+    bool map_dirty = false;
+    FrameScratch *scratch = nullptr;
+};
+
+struct HostLaunch {
+    struct Group {
+        int prec, variant, first, count, prefix_first, tiles;
+    };
+    std::vector<BfJob> jobs;
+    std::vector<int> tile_prefix;
+    std::vector<Group> groups;
+    size_t smem = 0;
+    std::vector<EnvJob> env;
+    std::vector<int> col_prefix;
+    int env_cols = 0, max_fft_m = 0;
+    std::vector<LogJob> log;
+    std::vector<int> blk_prefix;
+    int log_blocks = 0;
+};
+
+struct DeviceLaunch {
+    DevMem jobs, tile_prefix, env, col_prefix, log, blk_prefix, err;
+    int upload(const HostLaunch &hl, cudaStream_t st, bool async);
+};
+
+struct Request;
+
+}  // namespace bfi
+
+struct bf_handle {
+    int device = 0;
+    bfi::GeomHost g;
+    bfi::GeometryHost geo;
+    cudaStream_t stream = nullptr, own_stream = nullptr;
+    bfi::DevMem rowZ, rowZ2, colDX2, apcnt;
+    int kb_lo = 1, kb_hi = 0;
+    std::mutex mu;  // plans, tickets, slot pool
+    std::map<bfi::PlanKey, std::unique_ptr<bfi::Plan>> plans;
+    bfi::FrameScratch scratch;     // bf_beamform
+    bfi::DeviceLaunch launch;      // bf_beamform
+    bool err_cleared = false;
+    std::map<uint64_t, std::shared_ptr<bfi::Request>> tickets;
+};
+
+struct bf_batch {
+    int device = 0;
+    std::vector<bfi::FrameScratch> scratch;
+    std::vector<bfi::FramePrep> frames;
+    bfi::HostLaunch hl;
+    bfi::DeviceLaunch dl;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t marks[4] = {nullptr, nullptr, nullptr, nullptr};
+    int launches = 0;  // kernels one replay launches
+};
+
+namespace bfi {
+
+int handle_plan(bf_handle *h, int ns, const double *angles, int na, int prec, Plan **out);
+int check_frame_args(bf_handle *h, int ns, const double *angles, int na, uint32_t flags);
+size_t frame_out_bytes(const bf_handle *h, uint32_t flags);
+int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *angles, int na,
+                  uint32_t flags, float *out_dev, FrameScratch &s, FramePrep &fp);
+void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl);
+int upload_maps(std::vector<FramePrep> &frames, cudaStream_t st, bool async);
+// marks (optional, 4 events): recorded before the ingest, before and after the
+// beamforming launches, and after the last launch.
+int enqueue(const std::vector<FramePrep> &frames, const HostLaunch &hl, DeviceLaunch &dl,
+            cudaStream_t st, cudaEvent_t *marks = nullptr);
+int read_device_error(DeviceLaunch &dl, cudaStream_t st);
+bool is_device_pointer(const void *p);
+void engine_forget(bf_handle *h);
+
+}  // namespace bfi

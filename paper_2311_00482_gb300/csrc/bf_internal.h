@@ -1,0 +1,95 @@
+// Internal declarations shared by the host engine (C++) and the kernels (CUDA).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bfi {
+
+// RF sample pairs are stored per channel with this many zero samples in front,
+// so that pair j holds samples k = j - kPadL and k + 1.  Samples before 0 and
+// from Ns on read as zero, which makes the interpolation continuous across the
+// record ends (the host tables decide which samples count).
+constexpr int kPadL = 2;
+// Pixel tile of one CTA: 8 columns (one per warp) x 64 rows (2 per lane).
+constexpr int kTileCols = 8;
+constexpr int kRowsPerLane = 2;
+constexpr int kTileRows = 32 * kRowsPerLane;
+constexpr int kThreads = 32 * kTileCols;
+constexpr int kMaxGroup = 16;         // channels staged per pipeline stage (upper bound)
+constexpr int kStageBytes = 16 << 10; // target bytes of one stage's RF windows
+constexpr int kMaxBox = 256;          // TMA box extent limit per dimension
+
+enum Prec : int { kPrecF32 = 0, kPrecF16 = 1, kPrecBF16 = 2 };
+
+// Device-side error bits (written with atomicOr into a per-launch word).
+enum DevErr : int { kErrTimeout = 1, kErrWindow = 2, kErrConfig = 4 };
+
+// Everything one frame needs inside the beamforming kernel.  All pointers are
+// device pointers owned by the handle / batch that built the job.
+struct BfJob {
+    const int *colK;      // [na][nx]  nearest integer of kappa * x_p * sin(theta)
+    const float *colF;    // [na][nx]  remainder
+    const int *rowK;      // [na][nz]  nearest integer of kappa * z_p * (1 + cos(theta))
+    const float *rowF;    // [na][nz]  remainder
+    const float *rowZ;    // [nz]      kappa * z_p
+    const float *rowZ2;   // [nz]      (kappa * z_p)^2
+    const float *colDX2;  // [nx][ne]  (kappa * (x_p - x_i))^2
+    const int2 *valid;    // [na][nx][ne] first / last row whose sample counts
+    const uint16_t *apcnt;// [nx][nz]  channels inside the aperture (CF denominator)
+    const CUtensorMap *rf_map;  // 2-D map over the sample pairs [na * ne][nsp]
+    float *y;             // [nmodes][nx][nz] beamformed output
+    int nx, nz, na, ne;
+    int nsp;              // pairs per channel row
+    int wmax;             // window length (pairs) staged per channel and tile
+    int box;              // TMA box width (pairs); wmax is a multiple of it
+    int group;            // channels per stage
+    int modes;            // BF_DAS | BF_DMAS | BF_CF
+    int prec;             // Prec
+    int tiles_x, tiles_z;
+    float out_scale;      // 1 (FP32 pairs) or 32768 (FP16 / BF16 data scaled by 2^-15)
+};
+
+// One (frame, mode) image through the analytic-signal envelope along z.
+struct EnvJob {
+    const float *y;       // [nx][nz] beamformed image
+    float *env;           // [nx][nz] envelope output
+    unsigned *maxbits;    // frame maximum of env (float bits), reset to 0 before
+    int nx, nz;
+    int fft_m;            // transform size (nz itself when nz is a power of two)
+    int bluestein;        // 1 when nz is not a power of two
+    int band;             // 1: keep only bins [kb_lo, kb_hi] (DMAS second-harmonic band-pass)
+    int kb_lo, kb_hi;
+    const float2 *tw;     // [fft_m / 2] exp(-2 pi i k / fft_m)
+    const float2 *chirp;  // [nz] exp(i pi n^2 / nz)              (Bluestein only)
+    const float2 *bhat;   // [fft_m] DFT of the chirp convolution kernel (Bluestein only)
+};
+
+// One (frame, mode) envelope image to decibels against its frame maximum.
+struct LogJob {
+    const float *env;
+    float *out;
+    const unsigned *maxbits;
+    int n;                // pixels
+};
+
+// Kernel launchers (bf_kernels.cu).  All enqueue on `stream` and return the
+// launch status.  `variant` holds the BF_DMAS / BF_CF bits the launch computes
+// (all its jobs must share them and the precision).
+cudaError_t launch_ingest(const int16_t *rf, void *pairs, int rows, int ns, int nsp, int prec,
+                          cudaStream_t stream);
+cudaError_t launch_beamform(const BfJob *jobs_dev, const int *tile_prefix_dev, int njobs,
+                            int total_tiles, size_t smem_bytes, int prec, int variant,
+                            int *err_dev, cudaStream_t stream);
+cudaError_t launch_envelope(const EnvJob *jobs_dev, const int *col_prefix_dev, int njobs,
+                            int total_cols, int max_fft_m, cudaStream_t stream);
+cudaError_t launch_log(const LogJob *jobs_dev, const int *blk_prefix_dev, int njobs,
+                       int total_blocks, float dynamic_range_db, cudaStream_t stream);
+size_t beamform_smem_bytes(int wmax, int group, int prec);
+int log_blocks(long long pixels);
+
+// Bytes of one stored sample pair for a precision.
+inline int pair_bytes(int prec) { return prec == kPrecF32 ? 8 : 4; }
+
+}  // namespace bfi

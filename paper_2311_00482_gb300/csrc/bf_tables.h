@@ -1,0 +1,49 @@
+// Host-side table builders (double precision, no fused multiply-adds).
+#pragma once
+
+#include <stdint.h>
+
+#include <vector>
+
+#include "bf_internal.h"
+
+namespace bfi {
+
+struct GeomHost {
+    int ne = 0;
+    std::vector<double> xe;  // element x positions (m)
+    double fnum = 1.0;
+    int nx = 1, nz = 1;
+    double x0 = 0, x1 = 0, z0 = 0, z1 = 0;
+    double fs = 0, f0 = 0, c = 0;
+};
+
+// Angle-independent tables of a handle.
+struct GeometryHost {
+    std::vector<int> ap_first;     // [nx][ne] first row inside the aperture (nz: never)
+    std::vector<uint16_t> apcnt;   // [nx][nz] channels inside the aperture
+    std::vector<float> rowZ, rowZ2;
+    std::vector<float> colDX2;     // [nx][ne]
+};
+
+// Tables of one angle set and sample count.
+struct PlanHost {
+    std::vector<int> colK, rowK;
+    std::vector<float> colF, rowF;
+    std::vector<int> valid;        // [na][nx][ne][2] first / last counted row
+    int wmax = 0, box = 0, group = 1, nsp = 0;
+};
+
+struct EnvHost {
+    int nz = 0, fft_m = 0, bluestein = 0;
+    std::vector<float> tw, chirp, bhat;  // interleaved re / im
+};
+
+double grid_coord(double lo, double hi, int n, int j);
+void geometry_tables(const GeomHost &g, GeometryHost &out);
+void angle_tables(const GeomHost &g, const GeometryHost &geo, int ns,
+                  const std::vector<double> &angles, int prec, PlanHost &out);
+void bandpass_bins(int nz, double z0, double z1, double c, double f0, int &lo, int &hi);
+void envelope_tables(int nz, EnvHost &out);
+
+}  // namespace bfi

@@ -1,0 +1,263 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (relative L2 over the image, plus a per-pixel bound relative to the
+image's peak): FP32 path 1e-5 / 2e-5; FP16 and BF16 storage 2e-3 / 1e-2.
+Envelopes use the same bounds; log-compressed images are compared in dB with
+a max-abs bound of 0.05 dB, which is what a 2e-6-of-peak envelope error
+becomes at the -70 dB floor (8.7 dB per unit relative error at 3.2e-4 of peak).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2311_00482_gb300 as bf
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {bf.BF_PREC_FP32: (1e-5, 2e-5), bf.BF_PREC_FP16: (2e-3, 1e-2), bf.BF_PREC_BF16: (2e-3, 1e-2)}
+MODES = (("das", bf.BF_DAS), ("dmas", bf.BF_DMAS), ("cf", bf.BF_CF))
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+
+    from paper_2311_00482_gb300 import build as bfbuild
+
+    bfbuild.build()
+    bf.load()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    return torch
+
+
+def grid_of(acq):
+    return (acq.nx, acq.nz, acq.x0_m, acq.x1_m, acq.z0_m, acq.z1_m)
+
+
+def make_handle(acq):
+    return bf.bf_create(acq.n_elements, acq.pitch_m, acq.f_number, grid_of(acq), acq.fs_hz,
+                        acq.f0_hz, acq.c_mps)
+
+
+def run_gpu(torch, acq, rf, flags, angles=None, h=None):
+    own = h is None
+    h = make_handle(acq) if own else h
+    try:
+        rf_d = torch.from_numpy(np.ascontiguousarray(rf)).cuda()
+        nm = bf.n_modes(flags)
+        out = torch.full((nm, acq.nx, acq.nz), float("nan"), dtype=torch.float32, device="cuda")
+        bf.bf_beamform(h, rf_d, rf.shape[2], acq.angles_rad if angles is None else angles, flags, out)
+        bf.bf_sync(h)
+        return out.cpu().numpy().astype(np.float64)
+    finally:
+        if own:
+            bf.bf_destroy(h)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def assert_close(got, ref, prec, what):
+    l2, elem = TOL[prec]
+    assert np.all(np.isfinite(got)), what
+    err = rel_l2(got, ref)
+    peak = float(np.max(np.abs(ref)))
+    worst = float(np.max(np.abs(got - ref)))
+    assert err <= l2, "%s: rel-L2 %.3e > %.1e" % (what, err, l2)
+    assert worst <= elem * peak, "%s: max abs err %.3e > %.1e of peak" % (what, worst / peak, elem)
+
+
+def oracle_all(acq, rf):
+    return oracle.beamform(rf, acq.x_elements(), acq.angles_rad, grid_of(acq), acq.fs_hz,
+                           acq.c_mps, acq.f_number)
+
+
+# ------------------------------------------------------------ RF stage --
+
+@pytest.mark.parametrize("prec", [bf.BF_PREC_FP32, bf.BF_PREC_FP16, bf.BF_PREC_BF16])
+def test_ragged_grid_all_combiners(torch, prec):
+    """100 x 77 pixels: 12.5 tiles across, 1.2 tiles deep; record ends inside the field."""
+    acq = synth.SPECKLE_POINTS_128.with_(nx=100, nz=77, angles_deg=(-6.0, 0.0, 6.0))
+    rf, _ = synth.speckle_points_frame(acq)
+    ref = oracle_all(acq, rf)
+    got = run_gpu(torch, acq, rf, bf.BF_DAS | bf.BF_DMAS | bf.BF_CF | prec)
+    for k, (name, _) in enumerate(MODES):
+        assert_close(got[k], ref[name], prec, name)
+
+
+@pytest.mark.parametrize("flags", [bf.BF_DAS, bf.BF_DMAS, bf.BF_CF, bf.BF_DAS | bf.BF_CF,
+                                   bf.BF_DMAS | bf.BF_CF])
+def test_mode_subsets_keep_bit_order(torch, flags):
+    acq = synth.SPECKLE_POINTS_128.with_(nx=24, nz=70)
+    rf, _ = synth.speckle_points_frame(acq)
+    ref = oracle_all(acq, rf)
+    got = run_gpu(torch, acq, rf, flags)
+    names = [n for n, b in MODES if flags & b]
+    assert got.shape[0] == len(names)
+    for k, name in enumerate(names):
+        assert_close(got[k], ref[name], bf.BF_PREC_FP32, name)
+
+
+def test_full_size_512_das_dmas(torch):
+    """The 512 x 512, 2048-sample cyst + wire frame, every pixel."""
+    acq = synth.CYST_WIRES_512
+    rf, _ = synth.cyst_wires_frame(acq)
+    ref = oracle_all(acq, rf)
+    got = run_gpu(torch, acq, rf, bf.BF_DAS | bf.BF_DMAS)
+    assert_close(got[0], ref["das"], bf.BF_PREC_FP32, "das")
+    assert_close(got[1], ref["dmas"], bf.BF_PREC_FP32, "dmas")
+
+
+def test_degenerate_grids_and_geometry(torch):
+    rng = np.random.default_rng(5)
+    cases = [
+        synth.Acquisition(nx=1, nz=50, x0_m=1e-3, x1_m=1e-3),              # one column
+        synth.Acquisition(nx=33, nz=1, z0_m=20e-3, z1_m=20e-3),            # one row
+        synth.Acquisition(nx=1, nz=1, x0_m=0.0, x1_m=0.0, z0_m=15e-3, z1_m=15e-3),
+        synth.Acquisition(n_elements=1, nx=9, nz=65),                      # single element
+        synth.Acquisition(nx=17, nz=66, z0_m=0.0, z1_m=3e-3),              # empty apertures at z=0
+        synth.Acquisition(nx=20, nz=90, n_samples=300),                    # most samples off-record
+        synth.Acquisition(nx=20, nz=64, angles_deg=(-30.0, 30.0), f_number=0.7),
+    ]
+    for acq in cases:
+        rf = rng.integers(-32768, 32767, (len(acq.angles_deg), acq.n_elements, acq.n_samples)).astype(np.int16)
+        ref = oracle_all(acq, rf)
+        got = run_gpu(torch, acq, rf, bf.BF_DAS | bf.BF_DMAS | bf.BF_CF)
+        # Bound every value by 1e-6 of the magnitude of the terms it sums: all FP32 errors
+        # (delay, interpolation, summation order) are relative errors of individual terms,
+        # and white-noise records make single sums cancel (a single element's DMAS is 0 in
+        # exact arithmetic and a rounding residual in FP32).  S = sum |v| bounds DAS and,
+        # tripled, CF-DAS = S1^3 / (M Q); DMAS sums M^2/2 products, bounded by M S.
+        mag = oracle_all(acq, np.abs(rf.astype(np.int32)).clip(0, 32767).astype(np.int16))
+        scale = {"das": mag["das"], "cf": 3 * mag["das"], "dmas": mag["m"] * mag["das"]}
+        for k, (name, _) in enumerate(MODES):
+            assert np.all(np.abs(got[k] - ref[name]) <= 1e-6 * scale[name] + 1e-30), (acq, name)
+            if acq.nx * acq.nz >= 64 and np.max(np.abs(ref[name])) > 0:
+                assert_close(got[k], ref[name], bf.BF_PREC_FP32, "%s %s" % (acq, name))
+
+
+# ------------------------------------------------------ envelope / log --
+
+@pytest.mark.parametrize("nz", [128, 150])
+def test_envelope_and_log_stages(torch, nz):
+    """Power-of-two depth (radix-2) and 150 rows (Bluestein), fine axial sampling."""
+    acq = synth.CYST_WIRES_512.with_(nx=40, nz=nz, z0_m=18e-3, z1_m=18e-3 + (nz - 1) * 20e-6)
+    rf, _ = synth.cyst_wires_frame(acq)
+    ref = oracle_all(acq, rf)
+    dz = (acq.z1_m - acq.z0_m) / (acq.nz - 1)
+    flags = bf.BF_DAS | bf.BF_DMAS | bf.BF_CF
+    env = run_gpu(torch, acq, rf, flags | bf.BF_OUT_ENV)
+    db = run_gpu(torch, acq, rf, flags | bf.BF_OUT_LOGDB)
+    for k, (name, _) in enumerate(MODES):
+        e_ref = oracle.envelope(ref[name], bandpass=(name == "dmas"), dz=dz, c=acq.c_mps,
+                                f0=acq.f0_hz)
+        assert_close(env[k], e_ref, bf.BF_PREC_FP32, "env " + name)
+        d_ref = oracle.log_compress(e_ref)
+        assert np.max(np.abs(db[k] - d_ref)) <= 0.05, name
+
+
+# -------------------------------------------------------------- batch --
+
+def test_batch_of_uneven_frames_matches_single_frames(torch):
+    specs = [(64, 96, 1, bf.BF_DAS), (100, 64, 3, bf.BF_DMAS), (37, 150, 5, bf.BF_DAS | bf.BF_CF),
+             (80, 80, 2, bf.BF_DAS | bf.BF_DMAS | bf.BF_OUT_LOGDB), (70, 65, 4, bf.BF_DAS | bf.BF_PREC_FP16)]
+    rng = np.random.default_rng(9)
+    frames, handles, refs, outs, keep = [], [], [], [], []
+    try:
+        for nx, nz, na, flags in specs:
+            acq = synth.CYST_WIRES_512.with_(nx=nx, nz=nz, angles_deg=synth.angles_linspace(na))
+            rf = rng.integers(-20000, 20000, (na, 64, acq.n_samples)).astype(np.int16)
+            h = make_handle(acq)
+            handles.append(h)
+            rf_d = torch.from_numpy(rf).cuda()
+            out = torch.zeros((bf.n_modes(flags), nx, nz), dtype=torch.float32, device="cuda")
+            keep += [rf_d, out]
+            frames.append((h, rf_d, acq.n_samples, acq.angles_rad, flags, out))
+            refs.append(run_gpu(torch, acq, rf, flags))
+            outs.append(out)
+        batch = bf.Batch(frames)
+        for _ in range(2):  # replaying the graph gives the same result
+            batch.launch()
+            batch.status()
+            for got, ref in zip(outs, refs):
+                np.testing.assert_array_equal(got.cpu().numpy(), ref.astype(np.float32))
+        batch.close()
+    finally:
+        for h in handles:
+            bf.bf_destroy(h)
+
+
+# ------------------------------------------------------------ serving --
+
+def test_submit_poll_results_equal_solo_and_batches_overlap(torch):
+    """Continuous batching: while a large frame occupies the GPU, small requests
+    are admitted, queue up and ride together in the next launch; every result
+    equals the same frame beamformed alone."""
+    rng = np.random.default_rng(21)
+    big = synth.PRECISION_1024.with_(n_elements=64, x0_m=-9.6e-3, x1_m=9.6e-3, n_samples=2048)
+    big_rf = rng.integers(-20000, 20000, (7, 64, big.n_samples)).astype(np.int16)
+    acqs, rfs, flagss, handles = [], [], [], []
+    for k in range(16):
+        n = int(rng.integers(64, 200))
+        na = int(rng.integers(1, 5))
+        acq = synth.CYST_WIRES_512.with_(nx=n, nz=n, angles_deg=synth.angles_linspace(na))
+        acqs.append(acq)
+        rfs.append(rng.integers(-20000, 20000, (na, 64, acq.n_samples)).astype(np.int16))
+        flagss.append([bf.BF_DAS, bf.BF_DMAS][k % 2] | bf.BF_OUT_LOGDB)
+        handles.append(make_handle(acq))
+    hb = make_handle(big)
+    try:
+        solo = [run_gpu(torch, a, r, f, h=h) for a, r, f, h in zip(acqs, rfs, flagss, handles)]
+        bf.bf_engine_configure(64, 1, 0)
+        # warm the slots so that admission below does not allocate
+        for a, r, f, h in zip(acqs, rfs, flagss, handles):
+            t = bf.bf_submit(h, r, a.n_samples, a.angles_rad, f)
+            assert bf.bf_poll(h, t, None, timeout_us=10_000_000) == bf.BF_OK
+        tb = bf.bf_submit(hb, big_rf, big.n_samples, big.angles_rad, bf.BF_DAS | bf.BF_DMAS)
+        tickets = [bf.bf_submit(h, r, a.n_samples, a.angles_rad, f)
+                   for a, r, f, h in zip(acqs, rfs, flagss, handles)]
+        batches = []
+        for h, t in zip(handles, tickets):
+            info = None
+            for _ in range(100000):
+                info = bf.bf_ticket_batch(h, t)
+                if info is not None:
+                    break
+            batches.append(info)
+        for a, f, h, t, ref in zip(acqs, flagss, handles, tickets, solo):
+            out = np.empty((bf.n_modes(f), a.nx, a.nz), np.float32)
+            assert bf.bf_poll(h, t, out, timeout_us=10_000_000) == bf.BF_OK
+            np.testing.assert_allclose(out, ref, atol=1e-4)
+        assert bf.bf_poll(hb, tb, None, timeout_us=10_000_000) == bf.BF_OK
+        launched = [b for b in batches if b is not None]
+        assert launched and max(n for _, n in launched) > 1, launched
+        with pytest.raises(bf.BFError) as ei:
+            bf.bf_poll(handles[0], tickets[0], None, 0)
+        assert ei.value.code == bf.BF_ENOTFOUND
+    finally:
+        bf.bf_engine_configure(64, 3, 0)
+        for h in handles + [hb]:
+            bf.bf_destroy(h)
+
+
+def test_device_pointer_contract(torch):
+    acq = synth.Acquisition(nx=8, nz=8)
+    h = make_handle(acq)
+    try:
+        rf = np.zeros((1, 64, acq.n_samples), np.int16)
+        out = torch.zeros((1, 8, 8), device="cuda")
+        with pytest.raises(bf.BFError) as ei:
+            bf.bf_beamform(h, rf, acq.n_samples, [0.0], bf.BF_DAS, out)
+        assert ei.value.code == bf.BF_EINVAL
+        rf_d = torch.from_numpy(rf).cuda()
+        with pytest.raises(bf.BFError) as ei:
+            bf.bf_beamform(h, rf_d, acq.n_samples, [2.0], bf.BF_DAS, out)
+        assert ei.value.code == bf.BF_EINVAL
+        with pytest.raises(bf.BFError) as ei:
+            bf.bf_beamform(h, rf_d, acq.n_samples, [0.0], 0, out)
+        assert ei.value.code == bf.BF_EINVAL
+    finally:
+        bf.bf_destroy(h)
