@@ -183,13 +183,25 @@ BF_API int bf_batch_destroy(bf_batch *b);
  * tables the device path consumes.  valid_rows [n_angles][nx][n_elements][2]
  * receives the first and last pixel row iz at which channel i's sample
  * counts for column ix and angle a (inside the aperture and
- * 0 <= floor(n) <= Ns - 2; first > last when none); aperture_count [nx][nz]
+ * 0 <= floor(n) <= Ns - 2; (-1, -1) when none); aperture_count [nx][nz]
  * the number of channels inside the aperture of each pixel.  Either output
  * may be NULL. */
 BF_API int bf_host_tables(const bf_geometry *geometry, const bf_grid *grid, double fs_hz,
                           double f0_hz, double c_mps, int32_t n_samples,
                           const double *angles_rad, int32_t n_angles, int32_t *valid_rows,
                           uint16_t *aperture_count);
+
+/* Plan introspection (builds the plan if needed): info8 receives
+ * {window pairs staged per channel, TMA box width, channels per stage, rows
+ * per thread, tiles across, tiles down, pairs per channel record, entries of
+ * the window table}; wtab (optional, wtab_entries >= info8[7]) the first
+ * staged pair of every (angle, tile, channel) window, INT32_MIN when no pixel
+ * of the tile counts that channel.  Pair j of a record holds samples j - 2
+ * and j - 1.  Tiles are 32 columns wide and 8 * rows deep, numbered across
+ * first. */
+BF_API int bf_plan_info(bf_handle *h, int32_t n_samples, const double *angles_rad,
+                        int32_t n_angles, uint32_t mode_and_flags, int32_t *info8, int32_t *wtab,
+                        size_t wtab_entries);
 
 /* Thread-local message of the last failure ("" if none). */
 BF_API const char *bf_last_error(void);

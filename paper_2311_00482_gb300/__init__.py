@@ -33,7 +33,7 @@ EXPORTED = ("bf_create", "bf_destroy", "bf_set_stream", "bf_output_bytes", "bf_b
             "bf_submit", "bf_poll", "bf_ticket_batch", "bf_engine_configure", "bf_sync",
             "bf_batch_create", "bf_batch_launch", "bf_batch_status", "bf_batch_timing",
             "bf_batch_destroy",
-            "bf_host_tables", "bf_last_error", "bf_version")
+            "bf_host_tables", "bf_plan_info", "bf_last_error", "bf_version")
 
 
 class BFError(RuntimeError):
@@ -95,6 +95,7 @@ def load(path: str | None = None):
         "bf_batch_timing": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32)], ctypes.c_int),
         "bf_host_tables": ([ctypes.POINTER(bf_geometry), ctypes.POINTER(bf_grid), ctypes.c_double,
                             ctypes.c_double, ctypes.c_double, i32, dp, i32, vp, vp], ctypes.c_int),
+        "bf_plan_info": ([vp, i32, dp, i32, u32, vp, vp, ctypes.c_size_t], ctypes.c_int),
         "bf_last_error": ([], ctypes.c_char_p),
         "bf_version": ([], ctypes.c_int),
     }
@@ -188,6 +189,21 @@ def bf_beamform(h, rf_dev, n_samples, angles_rad, flags, out_dev):
     a, ap = _angles(angles_rad)
     return _check(load().bf_beamform(h, _ptr(rf_dev), int(n_samples), ap, len(a), int(flags),
                                      _ptr(out_dev)))
+
+
+def bf_plan_info(h, n_samples, angles_rad, flags, with_windows=False):
+    """Plan description dict; with_windows adds the [A][tiles][N] window table."""
+    a, ap = _angles(angles_rad)
+    info = np.zeros(8, np.int32)
+    _check(load().bf_plan_info(h, int(n_samples), ap, len(a), int(flags), info.ctypes.data, None, 0))
+    keys = ("wmax", "box", "group", "rows", "tiles_x", "tiles_z", "nsp", "entries")
+    d = {k: int(v) for k, v in zip(keys, info)}
+    if with_windows:
+        w = np.zeros(d["entries"], np.int32)
+        _check(load().bf_plan_info(h, int(n_samples), ap, len(a), int(flags), info.ctypes.data,
+                                   w.ctypes.data, w.size))
+        d["windows"] = w.reshape(len(a), d["tiles_x"] * d["tiles_z"], -1)
+    return d
 
 
 def bf_sync(h):

@@ -100,25 +100,32 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// 2-D map over sample pairs: rows = angles * channels, nsp pairs per row.
-static int encode_pairs_map(CUtensorMap *map, void *base, int rows, int nsp, int box, int prec)
+// 2-D tensor map over a row-major table of `rows` rows of `cols` elements of
+// `elem` bytes (4 or 8), read in boxes of box_cols x box_rows; out-of-range
+// elements read as zero.
+static int encode_map(CUtensorMap *map, void *base, int rows, int cols, int elem, int box_cols,
+                      int box_rows)
 {
     auto enc = tensor_map_encoder();
     if (!enc)
         return fail(BF_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    const int pb = pair_bytes(prec);
-    cuuint64_t dims[2] = {(cuuint64_t)nsp, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)nsp * (cuuint64_t)pb};
-    cuuint32_t boxd[2] = {(cuuint32_t)box, 1};
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * (cuuint64_t)elem};
+    cuuint32_t boxd[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(map, pb == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
+    CUresult r = enc(map, elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
                      2, base, dims, strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
-        return fail(BF_ECUDA, "cuTensorMapEncodeTiled failed (%d): rows %d, pairs %d, box %d", (int)r,
-                    rows, nsp, box);
+        return fail(BF_ECUDA, "cuTensorMapEncodeTiled failed (%d): %d x %d of %d bytes, box %d x %d",
+                    (int)r, rows, cols, elem, box_cols, box_rows);
     return BF_OK;
+}
+
+static int encode_pairs_map(CUtensorMap *map, void *base, int rows, int nsp, int box, int prec)
+{
+    return encode_map(map, base, rows, nsp, pair_bytes(prec), box, 1);
 }
 
 // -------------------------------------------------------- envelope tables --
@@ -156,6 +163,15 @@ static int env_tables(int nz, std::shared_ptr<EnvTablesDev> &out)
 
 // ------------------------------------------------------------------ plans --
 
+// Rows per thread of the beamforming tile: 8 (64-row tiles) unless that
+// leaves fewer than two CTAs per SM for one frame.
+static int choose_rows(const GeomHost &g)
+{
+    const long long cols = (g.nx + kTileCols - 1) / kTileCols;
+    const long long tiles8 = cols * ((g.nz + tile_rows(8) - 1) / tile_rows(8));
+    return tiles8 >= 2 * 152 ? 8 : 4;
+}
+
 int handle_plan(bf_handle *h, int ns, const double *angles, int na, int prec, Plan **out)
 {
     PlanKey key{ns, prec, std::vector<double>(angles, angles + na)};
@@ -166,7 +182,7 @@ int handle_plan(bf_handle *h, int ns, const double *angles, int na, int prec, Pl
         return BF_OK;
     }
     PlanHost ph;
-    angle_tables(h->g, h->geo, ns, key.angles, prec, ph);
+    angle_tables(h->g, h->geo, ns, key.angles, prec, choose_rows(h->g), ph);
     if ((size_t)ph.wmax * pair_bytes(prec) > (size_t)kStageBytes * 4)
         return fail(BF_EINVAL,
                     "pixel spacing too coarse for the sample rate: one tile needs %d samples per channel",
@@ -179,13 +195,67 @@ int handle_plan(bf_handle *h, int ns, const double *angles, int na, int prec, Pl
     p->box = ph.box;
     p->group = ph.group;
     p->nsp = ph.nsp;
+    p->rows = ph.rows;
+    p->tiles_x = (h->g.nx + kTileCols - 1) / kTileCols;
+    p->tiles_z = (h->g.nz + tile_rows(ph.rows) - 1) / tile_rows(ph.rows);
+    const int nxp = pad_cols(h->g.nx), ne = h->g.ne;
     int rc = p->colK.upload(ph.colK.data(), ph.colK.size() * sizeof(int));
     if (!rc) rc = p->colF.upload(ph.colF.data(), ph.colF.size() * sizeof(float));
     if (!rc) rc = p->rowK.upload(ph.rowK.data(), ph.rowK.size() * sizeof(int));
     if (!rc) rc = p->rowF.upload(ph.rowF.data(), ph.rowF.size() * sizeof(float));
     if (!rc) rc = p->valid.upload(ph.valid.data(), ph.valid.size() * sizeof(int));
+    if (!rc) rc = p->wtab.ensure((size_t)na * p->tiles_x * p->tiles_z * ne * sizeof(int));
     if (rc)
         return rc;
+    CUtensorMap maps[2];
+    rc = encode_map(&maps[0], p->valid.p, na * ne, nxp, 8, kTileCols, p->group);
+    if (!rc)
+        rc = encode_map(&maps[1], h->dx2.p, ne, nxp, 4, kTileCols, p->group);
+    if (!rc)
+        rc = p->maps.upload(maps, sizeof maps);
+    if (rc)
+        return rc;
+    // window starts of every (angle, tile, channel), once per plan
+    PlanJob pj{};
+    pj.colK = (const int *)p->colK.p;
+    pj.colF = (const float *)p->colF.p;
+    pj.rowK = (const int *)p->rowK.p;
+    pj.rowF = (const float *)p->rowF.p;
+    pj.rowZ = (const float *)h->rowZ.p;
+    pj.valid = (const int2 *)p->valid.p;
+    pj.dx2 = (const float *)h->dx2.p;
+    pj.wtab = (int *)p->wtab.p;
+    pj.nx = h->g.nx;
+    pj.nxp = nxp;
+    pj.nz = h->g.nz;
+    pj.na = na;
+    pj.ne = ne;
+    pj.rows = p->rows;
+    pj.tiles_x = p->tiles_x;
+    pj.tiles_z = p->tiles_z;
+    pj.wmax = p->wmax;
+    pj.align = ph.align;
+    DevMem errw;
+    rc = errw.ensure(sizeof(int));
+    if (rc)
+        return rc;
+    cudaStream_t st;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaStreamCreate");
+    int herr = 0;
+    e = cudaMemsetAsync(errw.p, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = launch_plan(pj, (int *)errw.p, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&herr, errw.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "window planner");
+    if (herr)
+        return fail(BF_ECUDA, "window planner: a tile's delays span more than %d samples", p->wmax);
     *out = p.get();
     h->plans.emplace(std::move(key), std::move(p));
     return BF_OK;
@@ -308,32 +378,32 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
         j.rowK = (const int *)p->rowK.p;
         j.rowF = (const float *)p->rowF.p;
         j.rowZ = (const float *)h->rowZ.p;
-        j.rowZ2 = (const float *)h->rowZ2.p;
-        j.colDX2 = (const float *)h->colDX2.p;
-        j.valid = (const int2 *)p->valid.p;
+        j.wtab = (const int *)p->wtab.p;
         j.apcnt = (const uint16_t *)h->apcnt.p;
         j.rf_map = f.map_dev;
+        j.valid_map = (const CUtensorMap *)p->maps.p;
+        j.dx2_map = (const CUtensorMap *)p->maps.p + 1;
         j.y = f.y;
         j.nx = h->g.nx;
         j.nz = h->g.nz;
         j.na = f.na;
         j.ne = h->g.ne;
-        j.nsp = p->nsp;
         j.wmax = p->wmax;
         j.box = p->box;
         j.group = p->group;
+        j.rows = p->rows;
         j.modes = f.modes;
-        j.prec = f.prec;
-        j.tiles_x = (h->g.nx + kTileCols - 1) / kTileCols;
-        j.tiles_z = (h->g.nz + kTileRows - 1) / kTileRows;
+        j.tiles_x = p->tiles_x;
+        j.tiles_z = p->tiles_z;
         j.out_scale = f.prec == kPrecF32 ? 1.0f : 32768.0f;
-        const int variant = f.prec * 8 + (f.modes & (BF_DMAS | BF_CF));
+        const int variant = (p->rows * 4 + f.prec) * 8 + (f.modes & (BF_DMAS | BF_CF));
         groups[variant].push_back(j);
         hl.smem = std::max(hl.smem, beamform_smem_bytes(p->wmax, p->group, f.prec));
     }
     for (auto &kv : groups) {
         HostLaunch::Group g;
-        g.prec = kv.first / 8;
+        g.rows = kv.first / 32;
+        g.prec = (kv.first / 8) % 4;
         g.variant = kv.first % 8;
         g.first = (int)hl.jobs.size();
         g.count = (int)kv.second.size();
@@ -346,6 +416,24 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
         }
         g.tiles = acc;
         hl.groups.push_back(g);
+    }
+    std::map<int, std::vector<IngestJob>> ig;
+    for (const FramePrep &f : frames)
+        ig[f.prec].push_back(IngestJob{f.rf, f.pairs, f.na * f.h->g.ne, f.ns, f.plan->nsp});
+    for (auto &kv : ig) {
+        HostLaunch::IGroup g;
+        g.prec = kv.first;
+        g.first = (int)hl.ingest.size();
+        g.count = (int)kv.second.size();
+        g.prefix_first = (int)hl.ingest_prefix.size();
+        int acc = 0;
+        for (const IngestJob &j : kv.second) {
+            hl.ingest_prefix.push_back(acc);
+            acc += j.rows;
+            hl.ingest.push_back(j);
+        }
+        g.rows = acc;
+        hl.igroups.push_back(g);
     }
     int cols = 0;
     long long blks = 0;
@@ -372,10 +460,12 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
             e.tw = (const float2 *)f.et->tw.p;
             e.chirp = (const float2 *)f.et->chirp.p;
             e.bhat = (const float2 *)f.et->bhat.p;
-            hl.col_prefix.push_back(cols);
-            cols += h->g.nx;
+            e.cols_per_block = e.bluestein ? 1 : envelope_cols_per_block(e.fft_m);
+            hl.env_prefix.push_back(cols);
+            cols += (h->g.nx + e.cols_per_block - 1) / e.cols_per_block;
             hl.env.push_back(e);
-            hl.max_fft_m = std::max(hl.max_fft_m, e.fft_m);
+            hl.env_smem = std::max(hl.env_smem, (2u * (size_t)e.cols_per_block * e.fft_m +
+                                                 (size_t)std::max(1, e.fft_m / 2)) * sizeof(float2));
             if (f.stage == BF_OUT_LOGDB) {
                 LogJob l{};
                 l.env = e.env;
@@ -389,7 +479,7 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
             ++slot;
         }
     }
-    hl.env_cols = cols;
+    hl.env_blocks = cols;
     hl.log_blocks = (int)blks;
 }
 
@@ -407,8 +497,10 @@ int DeviceLaunch::upload(const HostLaunch &hl, cudaStream_t st, bool async)
     };
     int rc = put(jobs, hl.jobs.data(), hl.jobs.size() * sizeof(BfJob));
     if (!rc) rc = put(tile_prefix, hl.tile_prefix.data(), hl.tile_prefix.size() * sizeof(int));
+    if (!rc) rc = put(ingest, hl.ingest.data(), hl.ingest.size() * sizeof(IngestJob));
+    if (!rc) rc = put(ingest_prefix, hl.ingest_prefix.data(), hl.ingest_prefix.size() * sizeof(int));
     if (!rc) rc = put(env, hl.env.data(), hl.env.size() * sizeof(EnvJob));
-    if (!rc) rc = put(col_prefix, hl.col_prefix.data(), hl.col_prefix.size() * sizeof(int));
+    if (!rc) rc = put(env_prefix, hl.env_prefix.data(), hl.env_prefix.size() * sizeof(int));
     if (!rc) rc = put(log, hl.log.data(), hl.log.size() * sizeof(LogJob));
     if (!rc) rc = put(blk_prefix, hl.blk_prefix.data(), hl.blk_prefix.size() * sizeof(int));
     if (!rc) rc = err.ensure(sizeof(int));
@@ -443,10 +535,14 @@ int enqueue(const std::vector<FramePrep> &frames, const HostLaunch &hl, DeviceLa
     cudaError_t e;
     if (marks)
         cudaEventRecordWithFlags(marks[0], st, cudaEventRecordExternal);
-    for (const FramePrep &f : frames) {
-        e = launch_ingest(f.rf, f.pairs, f.na * f.h->g.ne, f.ns, f.plan->nsp, f.prec, st);
+    for (const HostLaunch::IGroup &g : hl.igroups) {
+        e = launch_ingest((const IngestJob *)dl.ingest.p + g.first,
+                          (const int *)dl.ingest_prefix.p + g.prefix_first, g.count, g.rows, g.prec,
+                          st);
         if (e != cudaSuccess)
             return cuda_fail(e, "ingest launch");
+    }
+    for (const FramePrep &f : frames) {
         if (f.stage != BF_OUT_RF) {
             e = cudaMemsetAsync(f.maxbits, 0, 4 * sizeof(unsigned), st);
             if (e != cudaSuccess)
@@ -458,15 +554,15 @@ int enqueue(const std::vector<FramePrep> &frames, const HostLaunch &hl, DeviceLa
     for (const HostLaunch::Group &g : hl.groups) {
         e = launch_beamform((const BfJob *)dl.jobs.p + g.first,
                             (const int *)dl.tile_prefix.p + g.prefix_first, g.count, g.tiles, hl.smem,
-                            g.prec, g.variant, (int *)dl.err.p, st);
+                            g.prec, g.variant, g.rows, (int *)dl.err.p, st);
         if (e != cudaSuccess)
             return cuda_fail(e, "beamform launch");
     }
     if (marks)
         cudaEventRecordWithFlags(marks[2], st, cudaEventRecordExternal);
     if (!hl.env.empty()) {
-        e = launch_envelope((const EnvJob *)dl.env.p, (const int *)dl.col_prefix.p, (int)hl.env.size(),
-                            hl.env_cols, hl.max_fft_m, st);
+        e = launch_envelope((const EnvJob *)dl.env.p, (const int *)dl.env_prefix.p, (int)hl.env.size(),
+                            hl.env_blocks, hl.env_smem, st);
         if (e != cudaSuccess)
             return cuda_fail(e, "envelope launch");
     }
@@ -575,8 +671,7 @@ BF_API int bf_create(const bf_geometry *geom, const bf_grid *grid, double fs_hz,
     h->stream = h->own_stream;
     geometry_tables(g, h->geo);
     int rc = h->rowZ.upload(h->geo.rowZ.data(), h->geo.rowZ.size() * sizeof(float));
-    if (!rc) rc = h->rowZ2.upload(h->geo.rowZ2.data(), h->geo.rowZ2.size() * sizeof(float));
-    if (!rc) rc = h->colDX2.upload(h->geo.colDX2.data(), h->geo.colDX2.size() * sizeof(float));
+    if (!rc) rc = h->dx2.upload(h->geo.dx2.data(), h->geo.dx2.size() * sizeof(float));
     if (!rc) rc = h->apcnt.upload(h->geo.apcnt.data(), h->geo.apcnt.size() * sizeof(uint16_t));
     if (rc)
         return rc;
@@ -688,11 +783,47 @@ BF_API int bf_host_tables(const bf_geometry *geom, const bf_grid *grid, double f
     geometry_tables(g, geo);
     PlanHost ph;
     angle_tables(g, geo, n_samples, std::vector<double>(angles_rad, angles_rad + n_angles),
-                 kPrecF32, ph);
-    if (valid_rows)
-        std::memcpy(valid_rows, ph.valid.data(), ph.valid.size() * sizeof(int32_t));
+                 kPrecF32, 8, ph);
+    const int nxp = pad_cols(g.nx);
+    if (valid_rows)  // [na][ne][nxp][2] -> [na][nx][ne][2]
+        for (int a = 0; a < n_angles; ++a)
+            for (int ix = 0; ix < g.nx; ++ix)
+                for (int i = 0; i < g.ne; ++i)
+                    for (int q = 0; q < 2; ++q)
+                        valid_rows[(((size_t)a * g.nx + ix) * g.ne + i) * 2 + q] =
+                            ph.valid[(((size_t)a * g.ne + i) * nxp + ix) * 2 + q];
     if (aperture_count)
         std::memcpy(aperture_count, geo.apcnt.data(), geo.apcnt.size() * sizeof(uint16_t));
+    return BF_OK;
+}
+
+// Plan introspection: tile shape and window sizes of the plan a frame with
+// these arguments uses (built if needed), and optionally its window table.
+BF_API int bf_plan_info(bf_handle *h, int32_t n_samples, const double *angles_rad,
+                        int32_t n_angles, uint32_t flags, int32_t *info8, int32_t *wtab,
+                        size_t wtab_entries)
+{
+    int rc = check_frame_args(h, n_samples, angles_rad, n_angles, flags);
+    if (rc)
+        return rc;
+    if (!info8)
+        return fail(BF_EINVAL, "null info");
+    cudaSetDevice(h->device);
+    Plan *p = nullptr;
+    rc = handle_plan(h, n_samples, angles_rad, n_angles, (flags & BF_PREC_MASK) >> 4, &p);
+    if (rc)
+        return rc;
+    const size_t n = (size_t)n_angles * p->tiles_x * p->tiles_z * h->g.ne;
+    const int32_t v[8] = {p->wmax, p->box, p->group, p->rows, p->tiles_x, p->tiles_z, p->nsp,
+                          (int32_t)n};
+    std::memcpy(info8, v, sizeof v);
+    if (wtab) {
+        if (wtab_entries < n)
+            return fail(BF_EINVAL, "window table needs %zu entries", n);
+        cudaError_t e = cudaMemcpy(wtab, p->wtab.p, n * sizeof(int32_t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpy (window table)");
+    }
     return BF_OK;
 }
 
@@ -739,7 +870,7 @@ BF_API int bf_batch_create(const bf_frame *frames, int32_t n, bf_batch **out)
     for (auto &m : b->marks)
         if (e == cudaSuccess)
             e = cudaEventCreate(&m);
-    b->launches = (int)b->frames.size() + (int)b->hl.groups.size() + (b->hl.env.empty() ? 0 : 1) +
+    b->launches = (int)b->hl.igroups.size() + (int)b->hl.groups.size() + (b->hl.env.empty() ? 0 : 1) +
                   (b->hl.log.empty() ? 0 : 1);
     if (e == cudaSuccess)
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);

@@ -64,11 +64,14 @@ struct PlanKey {
     }
 };
 
-// Device tables of one (handle, sample count, precision, angle set).
+// Device tables of one (handle, sample count, precision, angle set): the
+// transmit tables, the counted-row intervals, the per-tile window starts and
+// the tensor maps through which the beamformer stages its per-tile tables.
 struct Plan {
     int ns = 0, na = 0, prec = 0;
-    int wmax = 0, box = 0, group = 1, nsp = 0;
-    DevMem colK, colF, rowK, rowF, valid;
+    int wmax = 0, box = 0, group = 1, nsp = 0, rows = 8, tiles_x = 0, tiles_z = 0;
+    DevMem colK, colF, rowK, rowF, valid, wtab;
+    DevMem maps;  // CUtensorMap[2]: valid rows, dx^2
 };
 
 struct EnvTablesDev {
@@ -103,23 +106,30 @@ struct FramePrep {
 };
 
 struct HostLaunch {
-    struct Group {
-        int prec, variant, first, count, prefix_first, tiles;
+    struct Group {  // one beamforming launch
+        int prec, variant, rows, first, count, prefix_first, tiles;
+    };
+    struct IGroup {  // one ingest launch
+        int prec, first, count, prefix_first, rows;
     };
     std::vector<BfJob> jobs;
     std::vector<int> tile_prefix;
     std::vector<Group> groups;
     size_t smem = 0;
+    std::vector<IngestJob> ingest;
+    std::vector<int> ingest_prefix;
+    std::vector<IGroup> igroups;
     std::vector<EnvJob> env;
-    std::vector<int> col_prefix;
-    int env_cols = 0, max_fft_m = 0;
+    std::vector<int> env_prefix;
+    int env_blocks = 0;
+    size_t env_smem = 0;
     std::vector<LogJob> log;
     std::vector<int> blk_prefix;
     int log_blocks = 0;
 };
 
 struct DeviceLaunch {
-    DevMem jobs, tile_prefix, env, col_prefix, log, blk_prefix, err;
+    DevMem jobs, tile_prefix, ingest, ingest_prefix, env, env_prefix, log, blk_prefix, err;
     int upload(const HostLaunch &hl, cudaStream_t st, bool async);
 };
 
@@ -132,7 +142,7 @@ struct bf_handle {
     bfi::GeomHost g;
     bfi::GeometryHost geo;
     cudaStream_t stream = nullptr, own_stream = nullptr;
-    bfi::DevMem rowZ, rowZ2, colDX2, apcnt;
+    bfi::DevMem rowZ, dx2, apcnt;
     int kb_lo = 1, kb_hi = 0;
     std::mutex mu;  // plans, tickets, slot pool
     std::map<bfi::PlanKey, std::unique_ptr<bfi::Plan>> plans;

@@ -12,14 +12,19 @@ namespace bfi {
 // from Ns on read as zero, which makes the interpolation continuous across the
 // record ends (the host tables decide which samples count).
 constexpr int kPadL = 2;
-// Pixel tile of one CTA: 8 columns (one per warp) x 64 rows (2 per lane).
-constexpr int kTileCols = 8;
-constexpr int kRowsPerLane = 2;
-constexpr int kTileRows = 32 * kRowsPerLane;
-constexpr int kThreads = 32 * kTileCols;
+// Pixel tile of one CTA: 32 columns (one per lane) x kWarps * rows-per-thread
+// rows (each warp a contiguous band of rows).
+constexpr int kTileCols = 32;
+constexpr int kWarps = 8;
+constexpr int kThreads = 32 * kWarps;
 constexpr int kMaxGroup = 16;         // channels staged per pipeline stage (upper bound)
-constexpr int kStageBytes = 16 << 10; // target bytes of one stage's RF windows
+constexpr int kStageBytes = 24 << 10; // target bytes of one stage's RF windows
 constexpr int kMaxBox = 256;          // TMA box extent limit per dimension
+constexpr int kNoWindow = (int)0x80000000;  // window table: no sample of this channel counts
+// Columns of the per-(channel, column) tables are padded to a multiple of 4
+// so that every table row starts 16-byte aligned (a tensor-map requirement).
+inline int pad_cols(int nx) { return (nx + 3) / 4 * 4; }
+inline int tile_rows(int rows_per_thread) { return kWarps * rows_per_thread; }
 
 enum Prec : int { kPrecF32 = 0, kPrecF16 = 1, kPrecBF16 = 2 };
 
@@ -34,21 +39,40 @@ struct BfJob {
     const int *rowK;      // [na][nz]  nearest integer of kappa * z_p * (1 + cos(theta))
     const float *rowF;    // [na][nz]  remainder
     const float *rowZ;    // [nz]      kappa * z_p
-    const float *rowZ2;   // [nz]      (kappa * z_p)^2
-    const float *colDX2;  // [nx][ne]  (kappa * (x_p - x_i))^2
-    const int2 *valid;    // [na][nx][ne] first / last row whose sample counts
+    const int *wtab;      // [na][tiles][ne] first staged pair of each tile's channel window
     const uint16_t *apcnt;// [nx][nz]  channels inside the aperture (CF denominator)
-    const CUtensorMap *rf_map;  // 2-D map over the sample pairs [na * ne][nsp]
+    const CUtensorMap *rf_map;     // sample pairs [na * ne][nsp]
+    const CUtensorMap *valid_map;  // int2 [na * ne][nxp]: first / last counted row, (-1, -1) if none
+    const CUtensorMap *dx2_map;    // float [ne][nxp]: max((kappa * (x_p - x_i))^2, 1e-30)
     float *y;             // [nmodes][nx][nz] beamformed output
     int nx, nz, na, ne;
-    int nsp;              // pairs per channel row
     int wmax;             // window length (pairs) staged per channel and tile
     int box;              // TMA box width (pairs); wmax is a multiple of it
     int group;            // channels per stage
+    int rows;             // rows per thread (tile height = kWarps * rows)
     int modes;            // BF_DAS | BF_DMAS | BF_CF
-    int prec;             // Prec
     int tiles_x, tiles_z;
     float out_scale;      // 1 (FP32 pairs) or 32768 (FP16 / BF16 data scaled by 2^-15)
+};
+
+// Inputs of the per-plan window planner (one job per plan).
+struct PlanJob {
+    const int *colK;
+    const float *colF;
+    const int *rowK;
+    const float *rowF;
+    const float *rowZ;
+    const int2 *valid;    // [na][ne][nxp]
+    const float *dx2;     // [ne][nxp]
+    int *wtab;            // [na][tiles][ne]
+    int nx, nxp, nz, na, ne, rows, tiles_x, tiles_z, wmax, align;
+};
+
+// One frame's int16 records to staged sample pairs.
+struct IngestJob {
+    const int16_t *rf;    // [rows][ns]
+    void *pairs;          // [rows][nsp]
+    int rows, ns, nsp;
 };
 
 // One (frame, mode) image through the analytic-signal envelope along z.
@@ -61,6 +85,7 @@ struct EnvJob {
     int bluestein;        // 1 when nz is not a power of two
     int band;             // 1: keep only bins [kb_lo, kb_hi] (DMAS second-harmonic band-pass)
     int kb_lo, kb_hi;
+    int cols_per_block;   // columns transformed together by one CTA
     const float2 *tw;     // [fft_m / 2] exp(-2 pi i k / fft_m)
     const float2 *chirp;  // [nz] exp(i pi n^2 / nz)              (Bluestein only)
     const float2 *bhat;   // [fft_m] DFT of the chirp convolution kernel (Bluestein only)
@@ -76,18 +101,21 @@ struct LogJob {
 
 // Kernel launchers (bf_kernels.cu).  All enqueue on `stream` and return the
 // launch status.  `variant` holds the BF_DMAS / BF_CF bits the launch computes
-// (all its jobs must share them and the precision).
-cudaError_t launch_ingest(const int16_t *rf, void *pairs, int rows, int ns, int nsp, int prec,
-                          cudaStream_t stream);
+// (all its jobs must share them, the precision and the rows per thread).
+cudaError_t launch_plan(const PlanJob &job, int *err_dev, cudaStream_t stream);
+cudaError_t launch_ingest(const IngestJob *jobs_dev, const int *row_prefix_dev, int njobs,
+                          int total_rows, int prec, cudaStream_t stream);
 cudaError_t launch_beamform(const BfJob *jobs_dev, const int *tile_prefix_dev, int njobs,
-                            int total_tiles, size_t smem_bytes, int prec, int variant,
+                            int total_tiles, size_t smem_bytes, int prec, int variant, int rows,
                             int *err_dev, cudaStream_t stream);
-cudaError_t launch_envelope(const EnvJob *jobs_dev, const int *col_prefix_dev, int njobs,
-                            int total_cols, int max_fft_m, cudaStream_t stream);
+cudaError_t launch_envelope(const EnvJob *jobs_dev, const int *blk_prefix_dev, int njobs,
+                            int total_blocks, size_t smem_bytes, cudaStream_t stream);
 cudaError_t launch_log(const LogJob *jobs_dev, const int *blk_prefix_dev, int njobs,
                        int total_blocks, float dynamic_range_db, cudaStream_t stream);
 size_t beamform_smem_bytes(int wmax, int group, int prec);
 int log_blocks(long long pixels);
+int envelope_cols_per_block(int fft_m);
+size_t envelope_smem_bytes(int fft_m);
 
 // Bytes of one stored sample pair for a precision.
 inline int pair_bytes(int prec) { return prec == kPrecF32 ? 8 : 4; }

@@ -79,21 +79,18 @@ void geometry_tables(const GeomHost &g, GeometryHost &out)
     const double kappa = g.fs / g.c;
     out.ap_first.assign((size_t)g.nx * g.ne, g.nz);
     out.apcnt.assign((size_t)g.nx * g.nz, 0);
+    const int nxp = pad_cols(g.nx);
     out.rowZ.resize(g.nz);
-    out.rowZ2.resize(g.nz);
-    out.colDX2.resize((size_t)g.nx * g.ne);
-    for (int iz = 0; iz < g.nz; ++iz) {
-        double z = kappa * grid_coord(g.z0, g.z1, g.nz, iz);
-        out.rowZ[iz] = (float)z;
-        out.rowZ2[iz] = (float)(z * z);
-    }
+    out.dx2.assign((size_t)g.ne * nxp, 0.0f);
+    for (int iz = 0; iz < g.nz; ++iz)
+        out.rowZ[iz] = (float)(kappa * grid_coord(g.z0, g.z1, g.nz, iz));
     parallel_for(g.nx, [&](int ix) {
         const double xp = grid_coord(g.x0, g.x1, g.nx, ix);
         std::vector<int> hist(g.nz + 1, 0);
         for (int i = 0; i < g.ne; ++i) {
             const double xi = g.xe[i];
             double d = kappa * (xp - xi);
-            out.colDX2[(size_t)ix * g.ne + i] = (float)(d * d);
+            out.dx2[(size_t)i * nxp + ix] = std::max((float)(d * d), 1e-30f);  // keeps sqrt off 0
             int t = first_true(0, g.nz - 1, [&](int iz) {
                 return in_aperture(xp, grid_coord(g.z0, g.z1, g.nz, iz), xi, g.fnum);
             });
@@ -109,15 +106,18 @@ void geometry_tables(const GeomHost &g, GeometryHost &out)
 }
 
 void angle_tables(const GeomHost &g, const GeometryHost &geo, int ns,
-                  const std::vector<double> &angles, int prec, PlanHost &out)
+                  const std::vector<double> &angles, int prec, int rows_per_thread, PlanHost &out)
 {
     const double kappa = g.fs / g.c;
     const int na = (int)angles.size();
+    const int nxp = pad_cols(g.nx);
     out.colK.resize((size_t)na * g.nx);
     out.colF.resize((size_t)na * g.nx);
     out.rowK.resize((size_t)na * g.nz);
     out.rowF.resize((size_t)na * g.nz);
-    out.valid.resize((size_t)na * g.nx * g.ne * 2);
+    // An empty row range is (-1, -1): row -1 never exists, and the kernel's
+    // test (row - first) <= (last - first) in unsigned arithmetic stays exact.
+    out.valid.assign((size_t)na * g.ne * nxp * 2, -1);
     double smax = 0.0;
     for (int a = 0; a < na; ++a) {
         const double st = std::sin(angles[a]), ct = std::cos(angles[a]);
@@ -155,10 +155,10 @@ void angle_tables(const GeomHost &g, const GeometryHost &geo, int ns,
             if (lo <= hi && !(std::floor(n_at(hi, xi)) <= kmax))
                 hi = first_true(lo, hi, [&](int iz) { return !(std::floor(n_at(iz, xi)) <= kmax); }) - 1;
             if (lo > hi) {
-                lo = 1;
-                hi = 0;
+                lo = -1;
+                hi = -1;
             }
-            size_t o = (((size_t)a * g.nx + ix) * g.ne + i) * 2;
+            size_t o = (((size_t)a * g.ne + i) * nxp + ix) * 2;
             out.valid[o] = lo;
             out.valid[o + 1] = hi;
         }
@@ -168,7 +168,8 @@ void angle_tables(const GeomHost &g, const GeometryHost &geo, int ns,
     const int align = 16 / pair_bytes(prec);
     const double dz = g.nz > 1 ? (g.z1 - g.z0) / (double)(g.nz - 1) : 0.0;
     const double dx = g.nx > 1 ? (g.x1 - g.x0) / (double)(g.nx - 1) : 0.0;
-    const int rows = std::min(kTileRows, g.nz) - 1, cols = std::min(kTileCols, g.nx) - 1;
+    const int rows = std::min(tile_rows(rows_per_thread), g.nz) - 1;
+    const int cols = std::min(kTileCols, g.nx) - 1;
     double spread = 2.0 * kappa * dz * rows + (1.0 + smax) * kappa * dx * cols;
     int span = (int)std::ceil(spread) + 1 + 4 + align;
     // Box widths are whole multiples of 128 bytes, so every shared-memory
@@ -180,7 +181,9 @@ void angle_tables(const GeomHost &g, const GeometryHost &geo, int ns,
     box = (box + box_align - 1) / box_align * box_align;
     out.box = box;
     out.wmax = nb * box;
-    out.nsp = (ns + kPadL + 3) / 4 * 4;
+    out.nsp = (ns + kPadL + 7) / 8 * 8;
+    out.rows = rows_per_thread;
+    out.align = align;
     int grp = kStageBytes / (out.wmax * pair_bytes(prec));
     out.group = std::max(1, std::min(kMaxGroup, std::min(grp, g.ne)));
 }

@@ -22,16 +22,16 @@ struct GeomHost {
 struct GeometryHost {
     std::vector<int> ap_first;     // [nx][ne] first row inside the aperture (nz: never)
     std::vector<uint16_t> apcnt;   // [nx][nz] channels inside the aperture
-    std::vector<float> rowZ, rowZ2;
-    std::vector<float> colDX2;     // [nx][ne]
+    std::vector<float> rowZ;
+    std::vector<float> dx2;        // [ne][nxp] (kappa (x_p - x_i))^2, columns padded
 };
 
 // Tables of one angle set and sample count.
 struct PlanHost {
     std::vector<int> colK, rowK;
     std::vector<float> colF, rowF;
-    std::vector<int> valid;        // [na][nx][ne][2] first / last counted row
-    int wmax = 0, box = 0, group = 1, nsp = 0;
+    std::vector<int> valid;        // [na][ne][nxp][2] first / last counted row (padding: none)
+    int wmax = 0, box = 0, group = 1, nsp = 0, rows = 8, align = 2;
 };
 
 struct EnvHost {
@@ -41,8 +41,9 @@ struct EnvHost {
 
 double grid_coord(double lo, double hi, int n, int j);
 void geometry_tables(const GeomHost &g, GeometryHost &out);
+// rows: rows per thread of the beamforming tile (tile height kWarps * rows)
 void angle_tables(const GeomHost &g, const GeometryHost &geo, int ns,
-                  const std::vector<double> &angles, int prec, PlanHost &out);
+                  const std::vector<double> &angles, int prec, int rows, PlanHost &out);
 void bandpass_bins(int nz, double z0, double z1, double c, double f0, int &lo, int &hi);
 void envelope_tables(int nz, EnvHost &out);
 

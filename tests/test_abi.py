@@ -64,6 +64,10 @@ def _compare_tables_with_oracle(acq, angles_rad, ns, x_elem=None):
     xe = acq.x_elements() if x_elem is None else np.asarray(x_elem)
     valid, cnt = bf.bf_host_tables(len(xe), acq.pitch_m, acq.f_number, grid, acq.fs_hz, acq.f0_hz,
                                    acq.c_mps, ns, angles_rad, x_elem_m=xe if x_elem is not None else None)
+    empty = valid[..., 0] > valid[..., 1]
+    assert not np.any(empty), "an empty row range is encoded as (-1, -1), never first > last"
+    none = valid[..., 1] < 0
+    assert np.all(valid[none] == -1)
     rf = np.zeros((len(angles_rad), len(xe), ns), np.int16)
     iz = np.arange(acq.nz)
     for ix in range(acq.nx):
