@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -163,13 +164,16 @@ static int env_tables(int nz, std::shared_ptr<EnvTablesDev> &out)
 
 // ------------------------------------------------------------------ plans --
 
-// Rows per thread of the beamforming tile: 8 (64-row tiles) unless that
-// leaves fewer than two CTAs per SM for one frame.
+// Rows per thread of the beamforming tile: 8 (64-row tiles) for deep grids,
+// where the per-channel work of a warp is spread over more pixels; 4 otherwise.
 static int choose_rows(const GeomHost &g)
 {
-    const long long cols = (g.nx + kTileCols - 1) / kTileCols;
-    const long long tiles8 = cols * ((g.nz + tile_rows(8) - 1) / tile_rows(8));
-    return tiles8 >= 2 * 152 ? 8 : 4;
+    if (const char *e = std::getenv("BF_TILE_ROWS")) {
+        const int r = std::atoi(e);
+        if (r == 4 || r == 8)
+            return r;
+    }
+    return g.nz >= 256 ? 8 : 4;
 }
 
 int handle_plan(bf_handle *h, int ns, const double *angles, int na, int prec, Plan **out)
@@ -464,8 +468,7 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
             hl.env_prefix.push_back(cols);
             cols += (h->g.nx + e.cols_per_block - 1) / e.cols_per_block;
             hl.env.push_back(e);
-            hl.env_smem = std::max(hl.env_smem, (2u * (size_t)e.cols_per_block * e.fft_m +
-                                                 (size_t)std::max(1, e.fft_m / 2)) * sizeof(float2));
+            hl.env_smem = std::max(hl.env_smem, envelope_smem_bytes(e.fft_m, e.bluestein));
             if (f.stage == BF_OUT_LOGDB) {
                 LogJob l{};
                 l.env = e.env;

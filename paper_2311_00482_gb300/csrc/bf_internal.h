@@ -13,11 +13,13 @@ namespace bfi {
 // record ends (the host tables decide which samples count).
 constexpr int kPadL = 2;
 // Pixel tile of one CTA: 32 columns (one per lane) x kWarps * rows-per-thread
-// rows (each warp a contiguous band of rows).
+// rows (each consumer warp a contiguous band of rows); one more warp issues
+// the tensor-memory-accelerator copies.
 constexpr int kTileCols = 32;
 constexpr int kWarps = 8;
 constexpr int kThreads = 32 * kWarps;
 constexpr int kMaxGroup = 16;         // channels staged per pipeline stage (upper bound)
+constexpr int kStages = 3;            // pipeline stages in shared memory
 constexpr int kStageBytes = 24 << 10; // target bytes of one stage's RF windows
 constexpr int kMaxBox = 256;          // TMA box extent limit per dimension
 constexpr int kNoWindow = (int)0x80000000;  // window table: no sample of this channel counts
@@ -85,8 +87,8 @@ struct EnvJob {
     int bluestein;        // 1 when nz is not a power of two
     int band;             // 1: keep only bins [kb_lo, kb_hi] (DMAS second-harmonic band-pass)
     int kb_lo, kb_hi;
-    int cols_per_block;   // columns transformed together by one CTA
-    const float2 *tw;     // [fft_m / 2] exp(-2 pi i k / fft_m)
+    int cols_per_block;   // image columns transformed together by one CTA
+    const float2 *tw;     // [fft_m] exp(-2 pi i k / fft_m)
     const float2 *chirp;  // [nz] exp(i pi n^2 / nz)              (Bluestein only)
     const float2 *bhat;   // [fft_m] DFT of the chirp convolution kernel (Bluestein only)
 };
@@ -115,7 +117,7 @@ cudaError_t launch_log(const LogJob *jobs_dev, const int *blk_prefix_dev, int nj
 size_t beamform_smem_bytes(int wmax, int group, int prec);
 int log_blocks(long long pixels);
 int envelope_cols_per_block(int fft_m);
-size_t envelope_smem_bytes(int fft_m);
+size_t envelope_smem_bytes(int fft_m, int bluestein);
 
 // Bytes of one stored sample pair for a precision.
 inline int pair_bytes(int prec) { return prec == kPrecF32 ? 8 : 4; }

@@ -242,17 +242,16 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestJob *__restrict
 
 // ------------------------------------------------------------- beamform --
 
-// Shared memory of one CTA: barriers + window starts, then per stage the
-// tile's per-(channel, column) tables and the channels' record windows.
+// Shared memory of one CTA: the mbarrier ring and window starts, then
+// kStages stages, each holding the tile's per-(channel, column) tables of one
+// channel group and the channels' record windows.
 struct SmemHeader {
-    uint64_t full[2];
-    int w0[2][kMaxGroup];
+    uint64_t full[kStages];   // producer -> consumers: the stage's copies have landed
+    uint64_t empty[kStages];  // consumers -> producer: every consumer warp is done with it
+    int w0[kStages][kMaxGroup];
 };
-constexpr int kHeaderBytes = 256;
+constexpr int kHeaderBytes = 512;
 static_assert(sizeof(SmemHeader) <= kHeaderBytes, "header");
-constexpr int kVrBytes = kMaxGroup * kTileCols * 8;  // int2 valid rows, one stage
-constexpr int kD2Bytes = kMaxGroup * kTileCols * 4;  // float dx^2, one stage
-constexpr int kDataOffset = kHeaderBytes + 2 * kVrBytes + 2 * kD2Bytes;
 
 template <int PREC>
 struct PairIO;
@@ -289,112 +288,158 @@ struct PairIO<kPrecBF16> {
     }
 };
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bytes of one pipeline stage: tables (int2 rows + float dx^2) and windows.
+__host__ __device__ __forceinline__ int stage_bytes(int group, int wmax, int pb)
+{
+    return group * (kTileCols * 12 + wmax * pb);
+}
+
+// Accumulate one channel into the ROWS pixels of this thread.  CHECK: test
+// every pixel's row against the channel's counted rows (otherwise the whole
+// row band of the warp counts it).
+template <int PREC, bool DMAS, bool CF, int ROWS, bool CHECK>
+__device__ __forceinline__ void accumulate(const unsigned char *win, int wmax, int w0, float d2,
+                                           int2 vr, int r_first, const float *Z, const float *fp,
+                                           const int *Kc, float *S1, float *T1, float *T2,
+                                           float *Su2)
+{
+    const unsigned span = (unsigned)(vr.y - vr.x);
+#pragma unroll
+    for (int j = 0; j < ROWS; ++j) {
+        const float x = rx_excess(d2, Z[j]) + fp[j];
+        const float m = x + kRoundMagic;
+        const float al = x - (m - kRoundMagic);  // in [-1/2, 1/2]
+        const unsigned idx = min((unsigned)(__float_as_int(m) + Kc[j] - w0), (unsigned)(wmax - 1));
+        const float v = PairIO<PREC>::interp(win, idx, al);
+        if (!CHECK || (unsigned)(r_first + j - vr.x) <= span) {
+            S1[j] += v;
+            if (DMAS) {
+                const float av = fabsf(v);
+                T1[j] += copysignf(sqrt_approx(av), v);
+                T2[j] += av;
+            }
+            if (CF)
+                Su2[j] = fmaf(v, v, Su2[j]);
+        }
+    }
+}
+
 template <int PREC, bool DMAS, bool CF, int ROWS>
-__global__ void __launch_bounds__(kThreads, 2) beamform_kernel(const BfJob *__restrict__ jobs,
-                                                               const int *__restrict__ tile_prefix,
-                                                               int njobs, int *__restrict__ err)
+__global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_kernel(const BfJob *__restrict__ jobs,
+                                                                    const int *__restrict__ tile_prefix,
+                                                                    int njobs, int *__restrict__ err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     SmemHeader &sh = *reinterpret_cast<SmemHeader *>(smem);
-    int2 *vr_s = reinterpret_cast<int2 *>(smem + kHeaderBytes);                 // [2][G][32]
-    float *d2_s = reinterpret_cast<float *>(smem + kHeaderBytes + 2 * kVrBytes);  // [2][G][32]
-    unsigned char *data = smem + kDataOffset;
     constexpr int PB = PairIO<PREC>::kBytes;
 
     // ---- which frame and tile
     const int jb = find_job(tile_prefix, njobs, blockIdx.x);
     const BfJob *J = jobs + jb;
     const int nx = J->nx, nz = J->nz, na = J->na, ne = J->ne;
-    const int wmax = J->wmax, box = J->box, G = J->group;
-    const int *__restrict__ colK = J->colK;
-    const float *__restrict__ colF = J->colF;
-    const int *__restrict__ rowK = J->rowK;
-    const float *__restrict__ rowF = J->rowF;
-    const int *__restrict__ wtab = J->wtab;
-    const CUtensorMap *rf_map = J->rf_map;
-    const CUtensorMap *valid_map = J->valid_map;
-    const CUtensorMap *dx2_map = J->dx2_map;
-
+    const int wmax = J->wmax, G = J->group;
     const int tile = blockIdx.x - __ldg(tile_prefix + jb);
-    const int ntiles = J->tiles_x * J->tiles_z;
     const int tx = tile % J->tiles_x, tz = tile / J->tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ix = tx * kTileCols + lane;
-    const bool col_ok = ix < nx;
-    const int ixc = min(ix, nx - 1);
-    const int r_first = tz * kWarps * ROWS + warp * ROWS;  // this warp's rows
-    const int r_last = r_first + ROWS - 1;
+    const int ngroups = (ne + G - 1) / G;
+    const int steps = na * ngroups;
+    const int sbytes = stage_bytes(G, wmax, PB);
+    // stage layout: int2 rows [G][32], float dx^2 [G][32], windows [G][wmax]
+    auto stage_base = [&](int st) { return smem + kHeaderBytes + (size_t)st * sbytes; };
 
     if (threadIdx.x == 0) {
-        mbar_init(&sh.full[0], 1);
-        mbar_init(&sh.full[1], 1);
+        for (int st = 0; st < kStages; ++st) {
+            mbar_init(&sh.full[st], 1);
+            mbar_init(&sh.empty[st], kWarps);
+        }
         mbar_fence_init();
     }
     __syncthreads();
     const unsigned long long deadline = global_ns() + kWaitNs;
 
-    const int ngroups = (ne + G - 1) / G;
-    const int steps = na * ngroups;
-    const unsigned meta_bytes = (unsigned)G * kTileCols * (8 + 4);
-
-    // Producer (warp 0): window start of this lane's channel for a step.
-    auto window_of = [&](int s) -> int {
-        const int a = s / ngroups, g = s - a * ngroups;
-        const int c = g * G + lane;
-        if (s >= steps || lane >= G || c >= ne)
-            return kNoWindow;
-        return __ldg(wtab + ((size_t)a * ntiles + tile) * ne + c);
-    };
-    auto issue = [&](int s, int w0) {
-        const int a = s / ngroups, g = s - a * ngroups, buf = s & 1;
-        const int i0 = g * G;
-        const bool mine = lane < G && i0 + lane < ne;
-        if (mine)
-            sh.w0[buf][lane] = w0;
-        const unsigned bytes = (mine && w0 != kNoWindow) ? (unsigned)(wmax * PB) : 0u;
-        unsigned total = bytes;
+    if (warp == kWarps) {
+        // ================= producer warp: TMA copies of every step's stage
+        const int *__restrict__ wtab = J->wtab;
+        const CUtensorMap *rf_map = J->rf_map;
+        const CUtensorMap *valid_map = J->valid_map;
+        const CUtensorMap *dx2_map = J->dx2_map;
+        const int box = J->box;
+        const int ntiles = J->tiles_x * J->tiles_z;
+        const unsigned meta_bytes = (unsigned)G * kTileCols * 12;
+        auto window_of = [&](int s) -> int {
+            const int a = s / ngroups, g = s - a * ngroups;
+            const int c = g * G + lane;
+            if (s >= steps || lane >= G || c >= ne)
+                return kNoWindow;
+            return __ldg(wtab + ((size_t)a * ntiles + tile) * ne + c);
+        };
+        int w0 = window_of(0);
+        for (int s = 0; s < steps; ++s) {
+            const int st = s % kStages, use = s / kStages;
+            const int w0_next = window_of(s + 1);  // in flight while we wait
+            if (use > 0 && !mbar_wait(&sh.empty[st], (unsigned)((use - 1) & 1), deadline, err))
+                break;
+            const int a = s / ngroups, g = s - a * ngroups, i0 = g * G;
+            const bool mine = lane < G && i0 + lane < ne;
+            if (mine)
+                sh.w0[st][lane] = w0;
+            const unsigned bytes = (mine && w0 != kNoWindow) ? (unsigned)(wmax * PB) : 0u;
+            unsigned total = bytes;
 #pragma unroll
-        for (int off = 16; off; off >>= 1)
-            total += __shfl_xor_sync(0xffffffffu, total, off);
-        if (lane == 0) {
-            mbar_arrive_expect_tx(&sh.full[buf], total + meta_bytes);
-            tma_2d(vr_s + (size_t)buf * G * kTileCols, valid_map, tx * kTileCols, a * ne + i0,
-                   &sh.full[buf]);
-            tma_2d(d2_s + (size_t)buf * G * kTileCols, dx2_map, tx * kTileCols, i0, &sh.full[buf]);
+            for (int off = 16; off; off >>= 1)
+                total += __shfl_xor_sync(0xffffffffu, total, off);
+            unsigned char *base = stage_base(st);
+            // the window starts are read by the consumers after the full barrier
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&sh.full[st], total + meta_bytes);
+                tma_2d(base, valid_map, tx * kTileCols, a * ne + i0, &sh.full[st]);
+                tma_2d(base + (size_t)G * kTileCols * 8, dx2_map, tx * kTileCols, i0, &sh.full[st]);
+            }
+            __syncwarp();
+            if (bytes) {
+                unsigned char *dst = base + (size_t)G * kTileCols * 12 + (size_t)lane * wmax * PB;
+                const int row = a * ne + i0 + lane;
+                for (int off = 0; off < wmax; off += box)
+                    tma_2d(dst + (size_t)off * PB, rf_map, w0 + off, row, &sh.full[st]);
+            }
+            w0 = w0_next;
         }
-        __syncwarp();
-        if (bytes) {
-            unsigned char *dst = data + ((size_t)buf * G + lane) * wmax * PB;
-            const int row = a * ne + i0 + lane;
-            for (int off = 0; off < wmax; off += box)
-                tma_2d(dst + (size_t)off * PB, rf_map, w0 + off, row, &sh.full[buf]);
-        }
-    };
+        return;
+    }
 
-    // ---- per-pixel state: ROWS contiguous rows per thread, one column per lane
+    // ================= consumer warps: one column per lane, ROWS rows per thread
+    const int ix = tx * kTileCols + lane;
+    const bool col_ok = ix < nx;
+    const int ixc = min(ix, nx - 1);
+    const int r_first = tz * kWarps * ROWS + warp * ROWS;
+    const int r_last = r_first + ROWS - 1;
+    const int *__restrict__ colK = J->colK;
+    const float *__restrict__ colF = J->colF;
+    const int *__restrict__ rowK = J->rowK;
+    const float *__restrict__ rowF = J->rowF;
+
     int Kc[ROWS];
     float Z[ROWS], fp[ROWS];
     float S1[ROWS], T1[ROWS], T2[ROWS], Yd[ROWS], Su2[ROWS];
 #pragma unroll
     for (int j = 0; j < ROWS; ++j) {
-        const int izc = min(r_first + j, nz - 1);
-        Z[j] = __ldg(J->rowZ + izc);
+        Z[j] = __ldg(J->rowZ + min(r_first + j, nz - 1));
         S1[j] = T1[j] = T2[j] = Yd[j] = Su2[j] = 0.f;
         Kc[j] = 0;
         fp[j] = 0.f;
     }
 
     bool ok = true;
-    int w0_next = 0;
-    if (warp == 0) {
-        const int w0_first = window_of(0);
-        w0_next = window_of(1);
-        if (steps > 0)
-            issue(0, w0_first);
-    }
 #pragma unroll 1
-    for (int s = 0; s < steps; ++s) {
-        const int a = s / ngroups, g = s - a * ngroups, buf = s & 1;
+    for (int s = 0; s < steps && ok; ++s) {
+        const int a = s / ngroups, g = s - a * ngroups;
+        const int st = s % kStages, use = s / kStages;
         if (g == 0) {
             const int ck = __ldg(colK + a * nx + ixc);
             const float cf = __ldg(colF + a * nx + ixc);
@@ -406,50 +451,35 @@ __global__ void __launch_bounds__(kThreads, 2) beamform_kernel(const BfJob *__re
                 T1[j] = T2[j] = 0.f;
             }
         }
-        __syncthreads();  // every warp is done with step s - 1: its stage is free
-        if (warp == 0 && s + 1 < steps && ok) {
-            issue(s + 1, w0_next);
-            w0_next = window_of(s + 2);
-        }
-        if (ok)
-            ok = mbar_wait(&sh.full[buf], (unsigned)((s >> 1) & 1), deadline, err);
-        if (ok) {
-            const int i0 = g * G, gs = min(G, ne - i0);
-            const int2 *vrb = vr_s + (size_t)buf * G * kTileCols;
-            const float *d2b = d2_s + (size_t)buf * G * kTileCols;
+        ok = mbar_wait(&sh.full[st], (unsigned)(use & 1), deadline, err);
+        if (!ok)
+            break;
+        const unsigned char *base = stage_base(st);
+        const int2 *vrb = reinterpret_cast<const int2 *>(base);
+        const float *d2b = reinterpret_cast<const float *>(base + (size_t)G * kTileCols * 8);
+        const unsigned char *wins = base + (size_t)G * kTileCols * 12;
+        const int gs = min(G, ne - g * G);
 #pragma unroll 1
-            for (int c = 0; c < gs; ++c) {
-                const int w0 = sh.w0[buf][c];
-                if (w0 == kNoWindow)
-                    continue;  // no pixel of the tile counts this channel
-                const int2 vr = vrb[c * kTileCols + lane];  // (-1, -1): no row counts
-                const bool mine = vr.x <= r_last && vr.y >= r_first;
-                if (!__any_sync(0xffffffffu, mine))
-                    continue;
-                const float d2 = d2b[c * kTileCols + lane];
-                const unsigned char *win = data + ((size_t)buf * G + c) * wmax * PB;
-                const unsigned span = (unsigned)(vr.y - vr.x);
-#pragma unroll
-                for (int j = 0; j < ROWS; ++j) {
-                    const float x = rx_excess(d2, Z[j]) + fp[j];
-                    const float m = x + kRoundMagic;
-                    const float al = x - (m - kRoundMagic);  // in [-1/2, 1/2]
-                    const unsigned idx =
-                        min((unsigned)(__float_as_int(m) + Kc[j] - w0), (unsigned)(wmax - 1));
-                    const float v = PairIO<PREC>::interp(win, idx, al);
-                    if ((unsigned)(r_first + j - vr.x) <= span) {
-                        S1[j] += v;
-                        if (DMAS) {
-                            const float av = fabsf(v);
-                            T1[j] += copysignf(sqrt_approx(av), v);
-                            T2[j] += av;
-                        }
-                        if (CF)
-                            Su2[j] = fmaf(v, v, Su2[j]);
-                    }
-                }
-            }
+        for (int c = 0; c < gs; ++c) {
+            const int w0 = sh.w0[st][c];
+            if (w0 == kNoWindow)
+                continue;  // no pixel of the tile counts this channel
+            const int2 vr = vrb[c * kTileCols + lane];  // (-1, -1): no row counts
+            const bool mine = vr.x <= r_last && vr.y >= r_first;
+            if (!__any_sync(0xffffffffu, mine))
+                continue;
+            const float d2 = d2b[c * kTileCols + lane];
+            const unsigned char *win = wins + (size_t)c * wmax * PB;
+            if (__all_sync(0xffffffffu, vr.x <= r_first && vr.y >= r_last))
+                accumulate<PREC, DMAS, CF, ROWS, false>(win, wmax, w0, d2, vr, r_first, Z, fp, Kc,
+                                                        S1, T1, T2, Su2);
+            else
+                accumulate<PREC, DMAS, CF, ROWS, true>(win, wmax, w0, d2, vr, r_first, Z, fp, Kc,
+                                                       S1, T1, T2, Su2);
         }
+        __syncwarp();
+        if (lane == 0)
+            mbar_arrive(&sh.empty[st]);
         if (DMAS && g == ngroups - 1) {
 #pragma unroll
             for (int j = 0; j < ROWS; ++j)
@@ -489,29 +519,65 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// Radix-2 Stockham FFTs of `cols` columns of length m (power of two) stored
-// back to back in x; twiddles exp(-2 pi i k / m) in shared memory.  The result
-// ends in the returned buffer.  inverse: +i exponent, no scaling.
-__device__ float2 *fft_cols(float2 *x, float2 *y, int m, int lgm, int cols, const float2 *tw,
-                            bool inverse)
+// Radix-4 Stockham FFTs (a final radix-2 pass when log2(m) is odd) of `cols`
+// complex columns of length m stored back to back in x; tw[k] = exp(-2 pi i
+// k / m) for k < m.  inverse: +i exponent, no scaling.  Returns the buffer
+// holding the result.
+__device__ float2 *fft_r4(float2 *x, float2 *y, int m, int lgm, int cols, const float2 *tw,
+                          bool inverse)
 {
-    const int half = m >> 1;
-    const int total = cols * half;
-    for (int ns = 1, lg = 0; ns < m; ns <<= 1, ++lg) {
-        const int stride_sh = lgm - 1 - lg;  // log2(m / (2 ns))
-        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int ns = 1, lg = 0;
+    if (m >= 4) {
+        const int q = m >> 2;
+        for (; (ns << 2) <= m; ns <<= 2, lg += 2) {
+            const int sh = lgm - 2 - lg;  // log2(m / (4 ns))
+            const int total = cols * q;
+            for (int t = threadIdx.x; t < total; t += blockDim.x) {
+                const int c = t >> (lgm - 2), j = t & (q - 1);
+                const float2 *xc = x + (size_t)c * m;
+                float2 *yc = y + (size_t)c * m;
+                float2 v0 = xc[j], v1 = xc[j + q], v2 = xc[j + 2 * q], v3 = xc[j + 3 * q];
+                const int r = j & (ns - 1);
+                const int k1 = r << sh;
+                float2 w1 = tw[k1], w2 = tw[2 * k1], w3 = tw[3 * k1];
+                if (inverse) {
+                    w1.y = -w1.y;
+                    w2.y = -w2.y;
+                    w3.y = -w3.y;
+                }
+                v1 = cmul(v1, w1);
+                v2 = cmul(v2, w2);
+                v3 = cmul(v3, w3);
+                const float2 a0 = make_float2(v0.x + v2.x, v0.y + v2.y);
+                const float2 a1 = make_float2(v0.x - v2.x, v0.y - v2.y);
+                const float2 a2 = make_float2(v1.x + v3.x, v1.y + v3.y);
+                const float2 d = make_float2(v1.x - v3.x, v1.y - v3.y);
+                // (v1 - v3) times -i (forward) or +i (inverse)
+                const float2 a3 = inverse ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
+                const int o = ((j - r) << 2) + r;
+                yc[o] = make_float2(a0.x + a2.x, a0.y + a2.y);
+                yc[o + ns] = make_float2(a1.x + a3.x, a1.y + a3.y);
+                yc[o + 2 * ns] = make_float2(a0.x - a2.x, a0.y - a2.y);
+                yc[o + 3 * ns] = make_float2(a1.x - a3.x, a1.y - a3.y);
+            }
+            __syncthreads();
+            float2 *tmp = x;
+            x = y;
+            y = tmp;
+        }
+    }
+    if (ns < m) {  // one radix-2 pass, ns == m / 2
+        const int half = m >> 1;
+        for (int t = threadIdx.x; t < cols * half; t += blockDim.x) {
             const int c = t >> (lgm - 1), j = t & (half - 1);
             const float2 *xc = x + (size_t)c * m;
             float2 *yc = y + (size_t)c * m;
-            const float2 v0 = xc[j], v1 = xc[j + half];
-            const int r = j & (ns - 1);
-            float2 w = tw[r << stride_sh];
+            float2 w = tw[j];
             if (inverse)
                 w.y = -w.y;
-            const float2 t2 = cmul(v1, w);
-            const int d = ((j - r) << 1) + r;
-            yc[d] = make_float2(v0.x + t2.x, v0.y + t2.y);
-            yc[d + ns] = make_float2(v0.x - t2.x, v0.y - t2.y);
+            const float2 v0 = xc[j], t2 = cmul(xc[j + half], w);
+            yc[j] = make_float2(v0.x + t2.x, v0.y + t2.y);
+            yc[j + half] = make_float2(v0.x - t2.x, v0.y - t2.y);
         }
         __syncthreads();
         float2 *tmp = x;
@@ -529,6 +595,15 @@ __device__ __forceinline__ float spectral_weight(int k, int L, int band, int kb_
     return h;
 }
 
+// Analytic-signal envelope of an image's columns.  The one-sided spectrum
+// X * H (H = 1 at 0 and L/2, 2 between, 0 for negative frequencies), times
+// the band-pass B for the DMAS image, has as inverse transform r + i h: r is
+// the column filtered by B mirrored onto negative frequencies (the column
+// itself without band-pass) and h its Hilbert transform, the multiplier
+// -i sgn(k) B(|k|) with sgn(0) = sgn(L/2) = 0.  Both are real and linear in
+// the column, so two columns a, b go through one complex transform of
+// a + i b: the inverse transforms of M(k) (A + iB) give r_a + i r_b and
+// h_a + i h_b.
 __global__ void __launch_bounds__(256) envelope_kernel(const EnvJob *__restrict__ jobs,
                                                        const int *__restrict__ blk_prefix,
                                                        int njobs)
@@ -537,40 +612,85 @@ __global__ void __launch_bounds__(256) envelope_kernel(const EnvJob *__restrict_
     __shared__ float red[32];
     const int jb = find_job(blk_prefix, njobs, blockIdx.x);
     const EnvJob J = jobs[jb];
-    const int C = J.cols_per_block;
-    const int c0 = (blockIdx.x - __ldg(blk_prefix + jb)) * C;
-    const int cols = min(C, J.nx - c0);
     const int nz = J.nz, m = J.fft_m;
     const int lgm = 31 - __clz(m);
-    float2 *A = sbuf, *B = sbuf + (size_t)C * m, *tw = sbuf + (size_t)2 * C * m;
-    for (int k = threadIdx.x; k < (m >> 1); k += blockDim.x)
-        tw[k] = __ldg(J.tw + k);
     float lmax = 0.f;
 
     if (!J.bluestein) {
-        for (int t = threadIdx.x; t < cols * m; t += blockDim.x) {
-            const int c = t / m, n = t - c * m;
-            A[t] = make_float2(__ldg(J.y + (size_t)(c0 + c) * nz + n), 0.f);
-        }
-        __syncthreads();
-        float2 *X = fft_cols(A, B, m, lgm, cols, tw, false);
-        float2 *O = X == A ? B : A;
-        for (int t = threadIdx.x; t < cols * m; t += blockDim.x) {
-            const int k = t & (m - 1);
-            const float h = spectral_weight(k, nz, J.band, J.kb_lo, J.kb_hi);
-            X[t] = make_float2(X[t].x * h, X[t].y * h);
-        }
-        __syncthreads();
-        float2 *R = fft_cols(X, O, m, lgm, cols, tw, true);
-        const float inv = 1.f / (float)m;
-        for (int t = threadIdx.x; t < cols * m; t += blockDim.x) {
+        const int C = J.cols_per_block >> 1;  // complex columns (pairs of image columns)
+        const int c0 = (blockIdx.x - __ldg(blk_prefix + jb)) * J.cols_per_block;
+        float2 *Zb = sbuf, *Pb = sbuf + (size_t)C * m, *Qb = sbuf + (size_t)2 * C * m;
+        float2 *tw = sbuf + (size_t)3 * C * m;
+        for (int k = threadIdx.x; k < m; k += blockDim.x)
+            tw[k] = __ldg(J.tw + k);
+        for (int t = threadIdx.x; t < C * m; t += blockDim.x) {
             const int c = t >> lgm, n = t & (m - 1);
-            const float e = hypotf(R[t].x, R[t].y) * inv;
-            J.env[(size_t)(c0 + c) * nz + n] = e;
-            lmax = fmaxf(lmax, e);
+            const int ca = c0 + 2 * c, cb = ca + 1;
+            const float ya = ca < J.nx ? __ldg(J.y + (size_t)ca * nz + n) : 0.f;
+            const float yb = cb < J.nx ? __ldg(J.y + (size_t)cb * nz + n) : 0.f;
+            Zb[t] = make_float2(ya, yb);
+        }
+        __syncthreads();
+        float2 *S = fft_r4(Zb, Pb, m, lgm, C, tw, false);  // spectrum of a + i b
+        float2 *F1 = S == Zb ? Pb : Zb;                    // free buffer
+        const float inv = 1.f / (float)m;
+        if (!J.band) {
+            for (int t = threadIdx.x; t < C * m; t += blockDim.x) {
+                const int k = t & (m - 1);
+                const float sg = (k == 0 || 2 * k == m) ? 0.f : (2 * k < m ? 1.f : -1.f);
+                F1[t] = make_float2(S[t].y * sg, -S[t].x * sg);  // -i sgn(k) S
+            }
+            __syncthreads();
+            const float2 *Hh = fft_r4(F1, S, m, lgm, C, tw, true);
+            for (int t = threadIdx.x; t < C * m; t += blockDim.x) {
+                const int c = t >> lgm, n = t & (m - 1);
+                const int ca = c0 + 2 * c, cb = ca + 1;
+                if (ca < J.nx) {
+                    const float e = hypotf(__ldg(J.y + (size_t)ca * nz + n), Hh[t].x * inv);
+                    J.env[(size_t)ca * nz + n] = e;
+                    lmax = fmaxf(lmax, e);
+                }
+                if (cb < J.nx) {
+                    const float e = hypotf(__ldg(J.y + (size_t)cb * nz + n), Hh[t].y * inv);
+                    J.env[(size_t)cb * nz + n] = e;
+                    lmax = fmaxf(lmax, e);
+                }
+            }
+        } else {
+            for (int t = threadIdx.x; t < C * m; t += blockDim.x) {
+                const int k = t & (m - 1);
+                const int kk = 2 * k <= m ? k : m - k;  // |k|
+                const float bp = (kk >= J.kb_lo && kk <= J.kb_hi) ? 1.f : 0.f;
+                const float sg = (k == 0 || 2 * k == m) ? 0.f : (2 * k < m ? 1.f : -1.f);
+                const float2 r = make_float2(S[t].x * bp, S[t].y * bp);
+                S[t] = r;
+                Qb[t] = make_float2(r.y * sg, -r.x * sg);
+            }
+            __syncthreads();
+            float2 *R = fft_r4(S, F1, m, lgm, C, tw, true);
+            float2 *F2 = R == S ? F1 : S;
+            const float2 *Hh = fft_r4(Qb, F2, m, lgm, C, tw, true);
+            for (int t = threadIdx.x; t < C * m; t += blockDim.x) {
+                const int c = t >> lgm, n = t & (m - 1);
+                const int ca = c0 + 2 * c, cb = ca + 1;
+                if (ca < J.nx) {
+                    const float e = hypotf(R[t].x, Hh[t].x) * inv;
+                    J.env[(size_t)ca * nz + n] = e;
+                    lmax = fmaxf(lmax, e);
+                }
+                if (cb < J.nx) {
+                    const float e = hypotf(R[t].y, Hh[t].y) * inv;
+                    J.env[(size_t)cb * nz + n] = e;
+                    lmax = fmaxf(lmax, e);
+                }
+            }
         }
     } else {
-        // one column per block (C == 1)
+        // one column per block through Bluestein's chirp transforms
+        const int c0 = blockIdx.x - __ldg(blk_prefix + jb);
+        float2 *A = sbuf, *B = sbuf + m, *tw = sbuf + (size_t)3 * m;
+        for (int k = threadIdx.x; k < m; k += blockDim.x)
+            tw[k] = __ldg(J.tw + k);
         const float *__restrict__ y = J.y + (size_t)c0 * nz;
         const float2 *__restrict__ w = J.chirp;
         const float2 *__restrict__ bh = J.bhat;
@@ -586,12 +706,12 @@ __global__ void __launch_bounds__(256) envelope_kernel(const EnvJob *__restrict_
             A[n] = v;
         }
         __syncthreads();
-        float2 *X = fft_cols(A, B, m, lgm, 1, tw, false);
+        float2 *X = fft_r4(A, B, m, lgm, 1, tw, false);
         for (int k = threadIdx.x; k < m; k += blockDim.x)
             X[k] = cmul(X[k], __ldg(bh + k));
         __syncthreads();
         float2 *O = X == A ? B : A;
-        float2 *Cb = fft_cols(X, O, m, lgm, 1, tw, true);
+        float2 *Cb = fft_r4(X, O, m, lgm, 1, tw, true);
         float2 *D = Cb == A ? B : A;
         // masked spectrum, conjugated and pre-multiplied by conj(w) for the second
         // pass: the inverse DFT of S is conj(DFT(conj S)) / nz
@@ -608,11 +728,11 @@ __global__ void __launch_bounds__(256) envelope_kernel(const EnvJob *__restrict_
             D[k] = v;
         }
         __syncthreads();
-        float2 *E = fft_cols(D, Cb, m, lgm, 1, tw, false);
+        float2 *E = fft_r4(D, Cb, m, lgm, 1, tw, false);
         for (int k = threadIdx.x; k < m; k += blockDim.x)
             E[k] = cmul(E[k], __ldg(bh + k));
         __syncthreads();
-        float2 *F = fft_cols(E, E == A ? B : A, m, lgm, 1, tw, true);
+        float2 *F = fft_r4(E, E == A ? B : A, m, lgm, 1, tw, true);
         const float inv = inv_m / (float)nz;
         float *__restrict__ env = J.env + (size_t)c0 * nz;
         for (int n = threadIdx.x; n < nz; n += blockDim.x) {
@@ -669,11 +789,14 @@ cudaError_t launch_bf_t(const BfJob *jobs, const int *prefix, int njobs, int til
     static size_t configured = 0;
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)  // several CTAs per SM need the largest shared-memory carveout
+            e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess)
             return e;
         configured = smem;
     }
-    k<<<tiles, kThreads, smem, st>>>(jobs, prefix, njobs, err);
+    k<<<tiles, kThreads + 32, smem, st>>>(jobs, prefix, njobs, err);
     return cudaGetLastError();
 }
 
@@ -703,15 +826,18 @@ cudaError_t launch_bf_p(const BfJob *jobs, const int *prefix, int njobs, int til
 
 size_t beamform_smem_bytes(int wmax, int group, int prec)
 {
-    return (size_t)kDataOffset + 2u * (size_t)group * (size_t)wmax * (size_t)pair_bytes(prec);
+    return (size_t)kHeaderBytes + (size_t)kStages * stage_bytes(group, wmax, pair_bytes(prec));
 }
 
-int envelope_cols_per_block(int fft_m) { return fft_m >= 2048 ? 1 : 2048 / fft_m; }
+// Image columns per envelope CTA for a power-of-two transform: two per
+// complex column, up to 2048 complex points per buffer.
+int envelope_cols_per_block(int fft_m) { return 2 * (fft_m >= 2048 ? 1 : 2048 / fft_m); }
 
-size_t envelope_smem_bytes(int fft_m)
+// Shared memory of an envelope CTA: three transform buffers and the twiddles.
+size_t envelope_smem_bytes(int fft_m, int bluestein)
 {
-    const int c = envelope_cols_per_block(fft_m);
-    return (2u * (size_t)c * fft_m + (size_t)(fft_m / 2 > 0 ? fft_m / 2 : 1)) * sizeof(float2);
+    const int c = bluestein ? 1 : envelope_cols_per_block(fft_m) / 2;
+    return (3u * (size_t)c * fft_m + (size_t)fft_m) * sizeof(float2);
 }
 
 cudaError_t launch_plan(const PlanJob &job, int *err_dev, cudaStream_t stream)

@@ -184,7 +184,7 @@ void angle_tables(const GeomHost &g, const GeometryHost &geo, int ns,
     out.nsp = (ns + kPadL + 7) / 8 * 8;
     out.rows = rows_per_thread;
     out.align = align;
-    int grp = kStageBytes / (out.wmax * pair_bytes(prec));
+    int grp = kStageBytes / (out.wmax * pair_bytes(prec) + kTileCols * 12);
     out.group = std::max(1, std::min(kMaxGroup, std::min(grp, g.ne)));
 }
 
@@ -246,8 +246,8 @@ void envelope_tables(int nz, EnvHost &out)
             m <<= 1;
     out.fft_m = m;
     out.bluestein = pow2 ? 0 : 1;
-    out.tw.resize(std::max(1, m / 2) * 2);
-    for (int k = 0; k < std::max(1, m / 2); ++k) {
+    out.tw.resize((size_t)m * 2);
+    for (int k = 0; k < m; ++k) {
         double ang = -2.0 * pi * (double)k / (double)m;
         out.tw[2 * k] = (float)std::cos(ang);
         out.tw[2 * k + 1] = (float)std::sin(ang);

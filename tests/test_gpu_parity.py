@@ -218,11 +218,14 @@ def test_submit_poll_results_equal_solo_and_batches_overlap(torch):
         for a, r, f, h in zip(acqs, rfs, flagss, handles):
             t = bf.bf_submit(h, r, a.n_samples, a.angles_rad, f)
             assert bf.bf_poll(h, t, None, timeout_us=10_000_000) == bf.BF_OK
-        tb = bf.bf_submit(hb, big_rf, big.n_samples, big.angles_rad, bf.BF_DAS | bf.BF_DMAS)
+        # four large frames back to back: with one batch in flight the last three queue
+        # behind the first, and so do the small requests submitted meanwhile
+        tbs = [bf.bf_submit(hb, big_rf, big.n_samples, big.angles_rad, bf.BF_DAS | bf.BF_DMAS)
+               for _ in range(4)]
         tickets = [bf.bf_submit(h, r, a.n_samples, a.angles_rad, f)
                    for a, r, f, h in zip(acqs, rfs, flagss, handles)]
         batches = []
-        for h, t in zip(handles, tickets):
+        for h, t in list(zip(handles, tickets)) + [(hb, t) for t in tbs]:
             info = None
             for _ in range(100000):
                 info = bf.bf_ticket_batch(h, t)
@@ -233,7 +236,8 @@ def test_submit_poll_results_equal_solo_and_batches_overlap(torch):
             out = np.empty((bf.n_modes(f), a.nx, a.nz), np.float32)
             assert bf.bf_poll(h, t, out, timeout_us=10_000_000) == bf.BF_OK
             np.testing.assert_allclose(out, ref, atol=1e-4)
-        assert bf.bf_poll(hb, tb, None, timeout_us=10_000_000) == bf.BF_OK
+        for tb in tbs:
+            assert bf.bf_poll(hb, tb, None, timeout_us=10_000_000) == bf.BF_OK
         launched = [b for b in batches if b is not None]
         assert launched and max(n for _, n in launched) > 1, launched
         with pytest.raises(bf.BFError) as ei:
