@@ -164,8 +164,9 @@ static int env_tables(int nz, std::shared_ptr<EnvTablesDev> &out)
 
 // ------------------------------------------------------------------ plans --
 
-// Rows per thread of the beamforming tile: 8 (64-row tiles) for deep grids,
-// where the per-channel work of a warp is spread over more pixels; 4 otherwise.
+// Rows per thread of the beamforming tile: 4 (32-row tiles, three CTAs per SM)
+// measured faster than 8 (one CTA per SM at ~150 registers) on every grid
+// tried; BF_TILE_ROWS=8 overrides.
 static int choose_rows(const GeomHost &g)
 {
     if (const char *e = std::getenv("BF_TILE_ROWS")) {
@@ -173,7 +174,8 @@ static int choose_rows(const GeomHost &g)
         if (r == 4 || r == 8)
             return r;
     }
-    return g.nz >= 256 ? 8 : 4;
+    (void)g;
+    return 4;
 }
 
 int handle_plan(bf_handle *h, int ns, const double *angles, int na, int prec, Plan **out)
