@@ -203,6 +203,28 @@ BF_API int bf_plan_info(bf_handle *h, int32_t n_samples, const double *angles_ra
                         int32_t n_angles, uint32_t mode_and_flags, int32_t *info8, int32_t *wtab,
                         size_t wtab_entries);
 
+/* Allocation-free envelope + log compression, for callers that cannot
+ * allocate device memory while running (a real-time acquisition loop that
+ * must not enter cudaMalloc, an application whose device memory belongs to
+ * its own allocator).  The paper has no counterpart: it is a deployment
+ * variant of the BF_OUT_LOGDB stage.
+ * y_dev: device float [nx][nz] beamformed image (e.g. one mode of a
+ * bf_beamform BF_OUT_RF output); db_dev: device float [nx][nz] receiving
+ * 20 log10(env / max env) clipped to [-70, 0] dB, env the analytic-signal
+ * magnitude along z, through the [f0, 3 f0] band-pass when bandpass != 0
+ * (the DMAS image); z0_m, z1_m: the grid's depth range (sets the band).
+ * Limits: nz a power of two <= 4096 and nx * nz <= 2^20; BF_EINVAL beyond.
+ * Scratch: a fixed 4 MiB array inside the library (held by every GPU that
+ * loads it until exit); no cudaMalloc, cudaFree or other allocating routine is
+ * called.  Every call shares that array and leaves its contents behind, so
+ * calls that overlap on the GPU (different streams, no ordering) race.  The
+ * first call on a device looks up the array's device address; make that first
+ * call before any stream capture.  Enqueued on cuda_stream (NULL: default
+ * stream); returns after enqueueing. */
+BF_API int bf_logdb_static(const float *y_dev, int32_t nx, int32_t nz, double z0_m, double z1_m,
+                           double f0_hz, double c_mps, int32_t bandpass, float *db_dev,
+                           void *cuda_stream);
+
 /* Thread-local message of the last failure ("" if none). */
 BF_API const char *bf_last_error(void);
 

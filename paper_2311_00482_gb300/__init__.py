@@ -33,7 +33,7 @@ EXPORTED = ("bf_create", "bf_destroy", "bf_set_stream", "bf_output_bytes", "bf_b
             "bf_submit", "bf_poll", "bf_ticket_batch", "bf_engine_configure", "bf_sync",
             "bf_batch_create", "bf_batch_launch", "bf_batch_status", "bf_batch_timing",
             "bf_batch_destroy",
-            "bf_host_tables", "bf_plan_info", "bf_last_error", "bf_version")
+            "bf_host_tables", "bf_plan_info", "bf_logdb_static", "bf_last_error", "bf_version")
 
 
 class BFError(RuntimeError):
@@ -96,6 +96,8 @@ def load(path: str | None = None):
         "bf_host_tables": ([ctypes.POINTER(bf_geometry), ctypes.POINTER(bf_grid), ctypes.c_double,
                             ctypes.c_double, ctypes.c_double, i32, dp, i32, vp, vp], ctypes.c_int),
         "bf_plan_info": ([vp, i32, dp, i32, u32, vp, vp, ctypes.c_size_t], ctypes.c_int),
+        "bf_logdb_static": ([vp, i32, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                             ctypes.c_double, i32, vp, vp], ctypes.c_int),
         "bf_last_error": ([], ctypes.c_char_p),
         "bf_version": ([], ctypes.c_int),
     }
@@ -204,6 +206,14 @@ def bf_plan_info(h, n_samples, angles_rad, flags, with_windows=False):
                                    w.ctypes.data, w.size))
         d["windows"] = w.reshape(len(a), d["tiles_x"] * d["tiles_z"], -1)
     return d
+
+
+def bf_logdb_static(y_dev, nx, nz, z0_m, z1_m, f0_hz, c_mps, bandpass, db_dev, stream=None):
+    """Allocation-free envelope + log compression of one device image (see include/bf.h)."""
+    s = getattr(stream, "cuda_stream", stream)
+    return _check(load().bf_logdb_static(_ptr(y_dev), int(nx), int(nz), float(z0_m), float(z1_m),
+                                         float(f0_hz), float(c_mps), int(bool(bandpass)),
+                                         _ptr(db_dev), s))
 
 
 def bf_sync(h):
