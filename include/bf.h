@@ -140,6 +140,15 @@ BF_API int bf_poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes,
 BF_API int bf_ticket_batch(bf_handle *h, uint64_t ticket, int32_t *batch_id,
                            int32_t *batch_frames);
 
+/* Device time of a ticket's batch once it has finished: when the batch began
+ * and ended executing, in ms since the engine started (BF_PENDING before). */
+BF_API int bf_ticket_times(bf_handle *h, uint64_t ticket, double *start_ms, double *end_ms);
+
+/* Hold (paused != 0) or resume the serving engine's launches on the current
+ * device.  Submissions are still admitted while paused; on resume everything
+ * queued is launched as batches. */
+BF_API int bf_engine_pause(int32_t paused);
+
 /* Serving-engine knobs for the current device (values <= 0 keep the current
  * setting): frames per launched batch (default 64), batches in flight
  * (default 3), device memory budget of admitted requests in bytes (default

@@ -30,7 +30,8 @@ _NAMES = {-1: "BF_EINVAL", -2: "BF_EAGAIN", -3: "BF_ENOMEM", -4: "BF_ECUDA", -5:
           -6: "BF_ENOTFOUND", -7: "BF_ENOSYS"}
 
 EXPORTED = ("bf_create", "bf_destroy", "bf_set_stream", "bf_output_bytes", "bf_beamform",
-            "bf_submit", "bf_poll", "bf_ticket_batch", "bf_engine_configure", "bf_sync",
+            "bf_submit", "bf_poll", "bf_ticket_batch", "bf_ticket_times", "bf_engine_pause",
+            "bf_engine_configure", "bf_sync",
             "bf_batch_create", "bf_batch_launch", "bf_batch_status", "bf_batch_timing",
             "bf_batch_destroy",
             "bf_host_tables", "bf_plan_info", "bf_logdb_static", "bf_last_error", "bf_version")
@@ -87,6 +88,9 @@ def load(path: str | None = None):
         "bf_poll": ([vp, u64, vp, ctypes.c_size_t, i64], ctypes.c_int),
         "bf_ticket_batch": ([vp, u64, ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
         "bf_engine_configure": ([i32, i32, u64], ctypes.c_int),
+        "bf_engine_pause": ([i32], ctypes.c_int),
+        "bf_ticket_times": ([vp, u64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+                            ctypes.c_int),
         "bf_sync": ([vp], ctypes.c_int),
         "bf_batch_create": ([ctypes.POINTER(bf_frame), i32, ctypes.POINTER(vp)], ctypes.c_int),
         "bf_batch_launch": ([vp, vp], ctypes.c_int),
@@ -241,6 +245,18 @@ def bf_ticket_batch(h, ticket):
     rc = _check(load().bf_ticket_batch(h, int(ticket), ctypes.byref(bid), ctypes.byref(n)),
                 allow=(BF_OK, BF_PENDING))
     return None if rc == BF_PENDING else (bid.value, n.value)
+
+
+def bf_ticket_times(h, ticket):
+    """(start_ms, end_ms) of the ticket's batch on the device, or None while pending."""
+    t0, t1 = ctypes.c_double(), ctypes.c_double()
+    rc = _check(load().bf_ticket_times(h, int(ticket), ctypes.byref(t0), ctypes.byref(t1)),
+                allow=(BF_OK, BF_PENDING))
+    return None if rc == BF_PENDING else (t0.value, t1.value)
+
+
+def bf_engine_pause(paused=True):
+    return _check(load().bf_engine_pause(int(bool(paused))))
 
 
 def bf_engine_configure(max_batch=0, max_inflight=0, memory_budget_bytes=0):

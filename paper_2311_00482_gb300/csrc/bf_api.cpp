@@ -211,6 +211,7 @@ int handle_plan(bf_handle *h, int ns, const double *angles, int na, int prec, Pl
     if (!rc) rc = p->rowF.upload(ph.rowF.data(), ph.rowF.size() * sizeof(float));
     if (!rc) rc = p->valid.upload(ph.valid.data(), ph.valid.size() * sizeof(int));
     if (!rc) rc = p->wtab.ensure((size_t)na * p->tiles_x * p->tiles_z * ne * sizeof(int));
+    if (!rc) rc = p->btab.ensure((size_t)na * p->tiles_x * p->tiles_z * ne * sizeof(int));
     if (rc)
         return rc;
     CUtensorMap maps[2];
@@ -231,6 +232,7 @@ int handle_plan(bf_handle *h, int ns, const double *angles, int na, int prec, Pl
     pj.valid = (const int2 *)p->valid.p;
     pj.dx2 = (const float *)h->dx2.p;
     pj.wtab = (int *)p->wtab.p;
+    pj.btab = (int *)p->btab.p;
     pj.nx = h->g.nx;
     pj.nxp = nxp;
     pj.nz = h->g.nz;
@@ -385,6 +387,7 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
         j.rowF = (const float *)p->rowF.p;
         j.rowZ = (const float *)h->rowZ.p;
         j.wtab = (const int *)p->wtab.p;
+        j.btab = (const int *)p->btab.p;
         j.apcnt = (const uint16_t *)h->apcnt.p;
         j.rf_map = f.map_dev;
         j.valid_map = (const CUtensorMap *)p->maps.p;

@@ -91,6 +91,8 @@ public:
         budget_ = tot / 2;
         if (const char *s = std::getenv("BF_MEM_BUDGET_MB"))
             budget_ = (size_t)std::strtoull(s, nullptr, 10) << 20;
+        cudaEventCreate(&epoch_);
+        cudaEventRecord(epoch_, streams_[0]);
         worker_ = std::thread([this] { loop(); });
         worker_.detach();  // lives for the process
     }
@@ -99,6 +101,15 @@ public:
                uint32_t flags, uint64_t *ticket);
     int poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes, int64_t timeout_us);
     int batch_of(bf_handle *h, uint64_t ticket, int *id, int *frames);
+    int times_of(bf_handle *h, uint64_t ticket, double *start_ms, double *end_ms);
+    void pause(bool p)
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            paused_ = p;
+        }
+        cv_work_.notify_one();
+    }
     void configure(int max_batch, int max_inflight, size_t budget)
     {
         std::lock_guard<std::mutex> lk(mu_);
@@ -124,6 +135,8 @@ private:
     size_t used_ = 0, budget_ = 0;
     int live_ = 0;
     int max_batch_ = 64, max_inflight_ = 3, max_live_ = 512;
+    bool paused_ = false;
+    cudaEvent_t epoch_ = nullptr;
     uint64_t next_ticket_ = 1;
     int next_batch_ = 0;
     cudaStream_t streams_[kStreams]{};
@@ -321,7 +334,7 @@ void Engine::loop()
         std::vector<std::shared_ptr<Request>> take;
         {
             std::unique_lock<std::mutex> lk(mu_);
-            cv_work_.wait(lk, [&] { return !pending_.empty(); });
+            cv_work_.wait(lk, [&] { return !pending_.empty() && !paused_; });
             while (!inflight_.empty() && cudaEventQuery(inflight_.front()->done) != cudaErrorNotReady)
                 inflight_.pop_front();
             if ((int)inflight_.size() >= max_inflight_) {
@@ -426,6 +439,37 @@ int Engine::batch_of(bf_handle *h, uint64_t ticket, int *id, int *frames)
     return BF_OK;
 }
 
+int Engine::times_of(bf_handle *h, uint64_t ticket, double *start_ms, double *end_ms)
+{
+    std::shared_ptr<Request> req;
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        auto it = h->tickets.find(ticket);
+        if (it == h->tickets.end())
+            return fail(BF_ENOTFOUND, "unknown ticket");
+        req = it->second;
+    }
+    std::shared_ptr<Batch> b;
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        if (req->state != 1)
+            return BF_PENDING;
+        b = req->batch;
+    }
+    cudaError_t e = cudaEventQuery(b->done);
+    if (e == cudaErrorNotReady)
+        return BF_PENDING;
+    float t0 = 0.f, t1 = 0.f;
+    e = cudaEventElapsedTime(&t0, epoch_, b->start);
+    if (e == cudaSuccess)
+        e = cudaEventElapsedTime(&t1, epoch_, b->done);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaEventElapsedTime");
+    *start_ms = t0;
+    *end_ms = t1;
+    return BF_OK;
+}
+
 std::mutex g_engines_mu;
 std::map<int, Engine *> g_engines;
 
@@ -471,6 +515,23 @@ BF_API int bf_ticket_batch(bf_handle *h, uint64_t ticket, int32_t *batch_id, int
     if (!h || !batch_id || !batch_frames)
         return fail(BF_EINVAL, "null argument");
     return engine_for(h->device)->batch_of(h, ticket, batch_id, batch_frames);
+}
+
+BF_API int bf_ticket_times(bf_handle *h, uint64_t ticket, double *start_ms, double *end_ms)
+{
+    if (!h || !start_ms || !end_ms)
+        return fail(BF_EINVAL, "null argument");
+    cudaSetDevice(h->device);
+    return engine_for(h->device)->times_of(h, ticket, start_ms, end_ms);
+}
+
+BF_API int bf_engine_pause(int32_t paused)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return fail(BF_ECUDA, "no CUDA device");
+    engine_for(dev)->pause(paused != 0);
+    return BF_OK;
 }
 
 BF_API int bf_engine_configure(int32_t max_batch, int32_t max_inflight, uint64_t memory_budget_bytes)

@@ -70,7 +70,7 @@ struct PlanKey {
 struct Plan {
     int ns = 0, na = 0, prec = 0;
     int wmax = 0, box = 0, group = 1, nsp = 0, rows = 8, tiles_x = 0, tiles_z = 0;
-    DevMem colK, colF, rowK, rowF, valid, wtab;
+    DevMem colK, colF, rowK, rowF, valid, wtab, btab;
     DevMem maps;  // CUtensorMap[2]: valid rows, dx^2
 };
 

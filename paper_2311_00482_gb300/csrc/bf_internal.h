@@ -42,6 +42,8 @@ struct BfJob {
     const float *rowF;    // [na][nz]  remainder
     const float *rowZ;    // [nz]      kappa * z_p
     const int *wtab;      // [na][tiles][ne] first staged pair of each tile's channel window
+    const int *btab;      // [na][tiles][ne] per row band b: bit b some pixel counts the
+                          // channel, bit 8 + b every pixel of the band does
     const uint16_t *apcnt;// [nx][nz]  channels inside the aperture (CF denominator)
     const CUtensorMap *rf_map;     // sample pairs [na * ne][nsp]
     const CUtensorMap *valid_map;  // int2 [na * ne][nxp]: first / last counted row, (-1, -1) if none
@@ -67,6 +69,7 @@ struct PlanJob {
     const int2 *valid;    // [na][ne][nxp]
     const float *dx2;     // [ne][nxp]
     int *wtab;            // [na][tiles][ne]
+    int *btab;            // [na][tiles][ne]
     int nx, nxp, nz, na, ne, rows, tiles_x, tiles_z, wmax, align;
 };
 

@@ -163,11 +163,22 @@ __global__ void __launch_bounds__(128) plan_kernel(const PlanJob J, int *__restr
     const int tz0 = tz * th, tz_last = min(tz0 + th - 1, J.nz - 1);
     for (int i = threadIdx.x; i < J.ne; i += blockDim.x) {
         int kmin = INT_MAX, kmax = INT_MIN;
+        unsigned any = 0, full = (1u << kWarps) - 1;
         for (int w = 0; w < kTileCols; ++w) {
             const int ix = tx * kTileCols + w;
             if (ix >= J.nx)
                 break;
             const int2 vr = J.valid[((size_t)a * J.ne + i) * J.nxp + ix];
+            // row bands of the consumer warps: does some / every pixel of this column count?
+            for (int b = 0; b < kWarps; ++b) {
+                const int b0 = tz0 + b * J.rows, b1 = min(b0 + J.rows - 1, J.nz - 1);
+                if (b0 > b1)
+                    continue;  // band below the grid: nothing to store there
+                if (vr.x <= b1 && vr.y >= b0)
+                    any |= 1u << b;
+                if (!(vr.x <= b0 && vr.y >= b1))
+                    full &= ~(1u << b);
+            }
             const int r0 = max(vr.x, tz0), r1 = min(vr.y, tz_last);
             if (r0 > r1)
                 continue;
@@ -190,7 +201,9 @@ __global__ void __launch_bounds__(128) plan_kernel(const PlanJob J, int *__restr
             if (kmax + kPadL + 2 - w0 + 1 > J.wmax)
                 atomicOr(err, kErrWindow);
         }
-        J.wtab[((size_t)a * J.tiles_x * J.tiles_z + t) * J.ne + i] = w0;
+        const size_t o = ((size_t)a * J.tiles_x * J.tiles_z + t) * J.ne + i;
+        J.wtab[o] = w0;
+        J.btab[o] = w0 == kNoWindow ? 0 : (int)(any | ((full & any) << 8));
     }
 }
 
@@ -249,31 +262,34 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestJob *__restrict
 struct SmemHeader {
     uint64_t full[kStages];   // producer -> consumers: the stage's copies have landed
     uint64_t empty[kStages];  // consumers -> producer: every consumer warp is done with it
-    int w0[kStages][kMaxGroup];
+    int2 wf[kStages][kMaxGroup];  // (window start, band flags) per staged channel
 };
 constexpr int kHeaderBytes = 512;
 static_assert(sizeof(SmemHeader) <= kHeaderBytes, "header");
 
+// Sample pairs read from shared memory through 32-bit shared-window addresses.
 template <int PREC>
 struct PairIO;
 
 template <>
 struct PairIO<kPrecF32> {
     static constexpr int kBytes = 8;
-    __device__ static __forceinline__ float interp(const unsigned char *win, unsigned idx, float al)
+    __device__ static __forceinline__ float interp(uint32_t addr, float al)
     {
-        const float2 p = reinterpret_cast<const float2 *>(win)[idx];
-        return fmaf(al, p.y, p.x);
+        float mid, diff;
+        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(mid), "=f"(diff) : "r"(addr));
+        return fmaf(al, diff, mid);
     }
 };
 
 template <>
 struct PairIO<kPrecF16> {
     static constexpr int kBytes = 4;
-    __device__ static __forceinline__ float interp(const unsigned char *win, unsigned idx, float al)
+    __device__ static __forceinline__ float interp(uint32_t addr, float al)
     {
-        const __half2 h = reinterpret_cast<const __half2 *>(win)[idx];
-        const float2 f = __half22float2(h);
+        unsigned w;
+        asm volatile("ld.shared.b32 %0, [%1];" : "=r"(w) : "r"(addr));
+        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w));
         return fmaf(al + 0.5f, f.y - f.x, f.x);
     }
 };
@@ -281,9 +297,10 @@ struct PairIO<kPrecF16> {
 template <>
 struct PairIO<kPrecBF16> {
     static constexpr int kBytes = 4;
-    __device__ static __forceinline__ float interp(const unsigned char *win, unsigned idx, float al)
+    __device__ static __forceinline__ float interp(uint32_t addr, float al)
     {
-        const unsigned w = reinterpret_cast<const unsigned *>(win)[idx];
+        unsigned w;
+        asm volatile("ld.shared.b32 %0, [%1];" : "=r"(w) : "r"(addr));
         const float lo = __uint_as_float(w << 16), hi = __uint_as_float(w & 0xffff0000u);
         return fmaf(al + 0.5f, hi - lo, lo);
     }
@@ -304,11 +321,12 @@ __host__ __device__ __forceinline__ int stage_bytes(int group, int wmax, int pb)
 // every pixel's row against the channel's counted rows (otherwise the whole
 // row band of the warp counts it).
 template <int PREC, bool DMAS, bool CF, int ROWS, bool CHECK>
-__device__ __forceinline__ void accumulate(const unsigned char *win, int wmax, int w0, float d2,
-                                           int2 vr, int r_first, const float *Z, const float *fp,
+__device__ __forceinline__ void accumulate(uint32_t win, int wmax, int w0, float d2, int2 vr,
+                                           int r_first, const float *Z, const float *fp,
                                            const int *Kc, float *S1, float *T1, float *T2,
                                            float *Su2)
 {
+    constexpr int PB = PairIO<PREC>::kBytes;
     const unsigned span = (unsigned)(vr.y - vr.x);
 #pragma unroll
     for (int j = 0; j < ROWS; ++j) {
@@ -316,7 +334,7 @@ __device__ __forceinline__ void accumulate(const unsigned char *win, int wmax, i
         const float m = x + kRoundMagic;
         const float al = x - (m - kRoundMagic);  // in [-1/2, 1/2]
         const unsigned idx = min((unsigned)(__float_as_int(m) + Kc[j] - w0), (unsigned)(wmax - 1));
-        const float v = PairIO<PREC>::interp(win, idx, al);
+        const float v = PairIO<PREC>::interp(win + idx * PB, al);
         if (!CHECK || (unsigned)(r_first + j - vr.x) <= span) {
             S1[j] += v;
             if (DMAS) {
@@ -327,6 +345,37 @@ __device__ __forceinline__ void accumulate(const unsigned char *win, int wmax, i
             if (CF)
                 Su2[j] = fmaf(v, v, Su2[j]);
         }
+    }
+}
+
+// Two channels that every pixel of the band counts, interleaved: twice the
+// independent dependency chains per thread (square roots, reciprocal, shared
+// load) for the scheduler to overlap.
+template <int PREC, bool DMAS, bool CF, int ROWS>
+__device__ __forceinline__ void accumulate2(uint32_t win0, int w00, float d20, uint32_t win1,
+                                            int w01, float d21, int wmax, const float *Z,
+                                            const float *fp, const int *Kc, float *S1, float *T1,
+                                            float *T2, float *Su2)
+{
+    constexpr int PB = PairIO<PREC>::kBytes;
+#pragma unroll
+    for (int j = 0; j < ROWS; ++j) {
+        const float x0 = rx_excess(d20, Z[j]) + fp[j];
+        const float x1 = rx_excess(d21, Z[j]) + fp[j];
+        const float m0 = x0 + kRoundMagic, m1 = x1 + kRoundMagic;
+        const float al0 = x0 - (m0 - kRoundMagic), al1 = x1 - (m1 - kRoundMagic);
+        const unsigned i0 = min((unsigned)(__float_as_int(m0) + Kc[j] - w00), (unsigned)(wmax - 1));
+        const unsigned i1 = min((unsigned)(__float_as_int(m1) + Kc[j] - w01), (unsigned)(wmax - 1));
+        const float v0 = PairIO<PREC>::interp(win0 + i0 * PB, al0);
+        const float v1 = PairIO<PREC>::interp(win1 + i1 * PB, al1);
+        S1[j] += v0 + v1;
+        if (DMAS) {
+            const float a0 = fabsf(v0), a1 = fabsf(v1);
+            T1[j] += copysignf(sqrt_approx(a0), v0) + copysignf(sqrt_approx(a1), v1);
+            T2[j] += a0 + a1;
+        }
+        if (CF)
+            Su2[j] = fmaf(v0, v0, fmaf(v1, v1, Su2[j]));
     }
 }
 
@@ -372,23 +421,26 @@ __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_ker
         const int box = J->box;
         const int ntiles = J->tiles_x * J->tiles_z;
         const unsigned meta_bytes = (unsigned)G * kTileCols * 12;
-        auto window_of = [&](int s) -> int {
+        const int *__restrict__ btab = J->btab;
+        auto window_of = [&](int s) -> int2 {
             const int a = s / ngroups, g = s - a * ngroups;
             const int c = g * G + lane;
             if (s >= steps || lane >= G || c >= ne)
-                return kNoWindow;
-            return __ldg(wtab + ((size_t)a * ntiles + tile) * ne + c);
+                return make_int2(kNoWindow, 0);
+            const size_t o = ((size_t)a * ntiles + tile) * ne + c;
+            return make_int2(__ldg(wtab + o), __ldg(btab + o));
         };
-        int w0 = window_of(0);
+        int2 wf = window_of(0);
         for (int s = 0; s < steps; ++s) {
             const int st = s % kStages, use = s / kStages;
-            const int w0_next = window_of(s + 1);  // in flight while we wait
+            const int2 wf_next = window_of(s + 1);  // in flight while we wait
             if (use > 0 && !mbar_wait(&sh.empty[st], (unsigned)((use - 1) & 1), deadline, err))
                 break;
             const int a = s / ngroups, g = s - a * ngroups, i0 = g * G;
             const bool mine = lane < G && i0 + lane < ne;
             if (mine)
-                sh.w0[st][lane] = w0;
+                sh.wf[st][lane] = wf;
+            const int w0 = wf.x;
             const unsigned bytes = (mine && w0 != kNoWindow) ? (unsigned)(wmax * PB) : 0u;
             unsigned total = bytes;
 #pragma unroll
@@ -409,7 +461,7 @@ __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_ker
                 for (int off = 0; off < wmax; off += box)
                     tma_2d(dst + (size_t)off * PB, rf_map, w0 + off, row, &sh.full[st]);
             }
-            w0 = w0_next;
+            wf = wf_next;
         }
         return;
     }
@@ -419,7 +471,6 @@ __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_ker
     const bool col_ok = ix < nx;
     const int ixc = min(ix, nx - 1);
     const int r_first = tz * kWarps * ROWS + warp * ROWS;
-    const int r_last = r_first + ROWS - 1;
     const int *__restrict__ colK = J->colK;
     const float *__restrict__ colF = J->colF;
     const int *__restrict__ rowK = J->rowK;
@@ -458,25 +509,34 @@ __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_ker
         const unsigned char *base = stage_base(st);
         const int2 *vrb = reinterpret_cast<const int2 *>(base);
         const float *d2b = reinterpret_cast<const float *>(base + (size_t)G * kTileCols * 8);
-        const unsigned char *wins = base + (size_t)G * kTileCols * 12;
+        const uint32_t wins = smem_u32(base) + (uint32_t)G * kTileCols * 12;
         const int gs = min(G, ne - g * G);
 #pragma unroll 1
         for (int c = 0; c < gs; ++c) {
-            const int w0 = sh.w0[st][c];
-            if (w0 == kNoWindow)
-                continue;  // no pixel of the tile counts this channel
-            const int2 vr = vrb[c * kTileCols + lane];  // (-1, -1): no row counts
-            const bool mine = vr.x <= r_last && vr.y >= r_first;
-            if (!__any_sync(0xffffffffu, mine))
-                continue;
+            const int2 wf = sh.wf[st][c];
+            const unsigned bands = (unsigned)wf.y >> warp;
+            if (!(bands & 1u))
+                continue;  // no pixel of this warp's row band counts the channel
             const float d2 = d2b[c * kTileCols + lane];
-            const unsigned char *win = wins + (size_t)c * wmax * PB;
-            if (__all_sync(0xffffffffu, vr.x <= r_first && vr.y >= r_last))
-                accumulate<PREC, DMAS, CF, ROWS, false>(win, wmax, w0, d2, vr, r_first, Z, fp, Kc,
-                                                        S1, T1, T2, Su2);
-            else
-                accumulate<PREC, DMAS, CF, ROWS, true>(win, wmax, w0, d2, vr, r_first, Z, fp, Kc,
+            const uint32_t win = wins + (uint32_t)(c * wmax * PB);
+            if ((bands & 0x100u) && c + 1 < gs) {
+                const int2 wf1 = sh.wf[st][c + 1];
+                if (((unsigned)wf1.y >> warp) & 0x100u) {  // two fully counted channels
+                    accumulate2<PREC, DMAS, CF, ROWS>(win, wf.x, d2, win + (uint32_t)(wmax * PB),
+                                                      wf1.x, d2b[(c + 1) * kTileCols + lane], wmax,
+                                                      Z, fp, Kc, S1, T1, T2, Su2);
+                    ++c;
+                    continue;
+                }
+            }
+            if (bands & 0x100u) {  // every pixel of the band counts it
+                accumulate<PREC, DMAS, CF, ROWS, false>(win, wmax, wf.x, d2, make_int2(0, 0),
+                                                        r_first, Z, fp, Kc, S1, T1, T2, Su2);
+            } else {
+                const int2 vr = vrb[c * kTileCols + lane];  // (-1, -1): no row counts
+                accumulate<PREC, DMAS, CF, ROWS, true>(win, wmax, wf.x, d2, vr, r_first, Z, fp, Kc,
                                                        S1, T1, T2, Su2);
+            }
         }
         __syncwarp();
         if (lane == 0)

@@ -195,12 +195,11 @@ def test_batch_of_uneven_frames_matches_single_frames(torch):
 # ------------------------------------------------------------ serving --
 
 def test_submit_poll_results_equal_solo_and_batches_overlap(torch):
-    """Continuous batching: while a large frame occupies the GPU, small requests
-    are admitted, queue up and ride together in the next launch; every result
-    equals the same frame beamformed alone."""
+    """Continuous batching: requests admitted while launches are held ride
+    together; with several batches in flight on the engine's streams their
+    device execution overlaps; every result equals the same frame beamformed
+    alone."""
     rng = np.random.default_rng(21)
-    big = synth.PRECISION_1024.with_(n_elements=64, x0_m=-9.6e-3, x1_m=9.6e-3, n_samples=2048)
-    big_rf = rng.integers(-20000, 20000, (7, 64, big.n_samples)).astype(np.int16)
     acqs, rfs, flagss, handles = [], [], [], []
     for k in range(16):
         n = int(rng.integers(64, 200))
@@ -210,42 +209,55 @@ def test_submit_poll_results_equal_solo_and_batches_overlap(torch):
         rfs.append(rng.integers(-20000, 20000, (na, 64, acq.n_samples)).astype(np.int16))
         flagss.append([bf.BF_DAS, bf.BF_DMAS][k % 2] | bf.BF_OUT_LOGDB)
         handles.append(make_handle(acq))
-    hb = make_handle(big)
     try:
         solo = [run_gpu(torch, a, r, f, h=h) for a, r, f, h in zip(acqs, rfs, flagss, handles)]
-        bf.bf_engine_configure(64, 1, 0)
-        # warm the slots so that admission below does not allocate
-        for a, r, f, h in zip(acqs, rfs, flagss, handles):
-            t = bf.bf_submit(h, r, a.n_samples, a.angles_rad, f)
-            assert bf.bf_poll(h, t, None, timeout_us=10_000_000) == bf.BF_OK
-        # four large frames back to back: with one batch in flight the last three queue
-        # behind the first, and so do the small requests submitted meanwhile
-        tbs = [bf.bf_submit(hb, big_rf, big.n_samples, big.angles_rad, bf.BF_DAS | bf.BF_DMAS)
-               for _ in range(4)]
-        tickets = [bf.bf_submit(h, r, a.n_samples, a.angles_rad, f)
-                   for a, r, f, h in zip(acqs, rfs, flagss, handles)]
-        batches = []
-        for h, t in list(zip(handles, tickets)) + [(hb, t) for t in tbs]:
-            info = None
-            for _ in range(100000):
-                info = bf.bf_ticket_batch(h, t)
-                if info is not None:
-                    break
-            batches.append(info)
-        for a, f, h, t, ref in zip(acqs, flagss, handles, tickets, solo):
-            out = np.empty((bf.n_modes(f), a.nx, a.nz), np.float32)
-            assert bf.bf_poll(h, t, out, timeout_us=10_000_000) == bf.BF_OK
+
+        def burst(max_batch, max_inflight):
+            bf.bf_engine_configure(max_batch, max_inflight, 0)
+            bf.bf_engine_pause(True)
+            try:
+                tickets = [bf.bf_submit(h, r, a.n_samples, a.angles_rad, f)
+                           for a, r, f, h in zip(acqs, rfs, flagss, handles)]
+            finally:
+                bf.bf_engine_pause(False)
+            outs, info, times = [], [], []
+            for a, f, h, t in zip(acqs, flagss, handles, tickets):
+                got = None
+                for _ in range(1000000):
+                    got = bf.bf_ticket_batch(h, t)
+                    if got is not None:
+                        break
+                info.append(got)
+                for _ in range(1000000):
+                    tt = bf.bf_ticket_times(h, t)
+                    if tt is not None:
+                        break
+                times.append(tt)
+                out = np.empty((bf.n_modes(f), a.nx, a.nz), np.float32)
+                assert bf.bf_poll(h, t, out, timeout_us=10_000_000) == bf.BF_OK
+                outs.append(out)
+            return tickets, outs, info, times
+
+        # all 16 queued while held: launched together (batches of up to 64)
+        tickets, outs, info, _ = burst(64, 1)
+        assert max(n for _, n in info) > 1, info
+        for out, ref in zip(outs, solo):
             np.testing.assert_allclose(out, ref, atol=1e-4)
-        for tb in tbs:
-            assert bf.bf_poll(hb, tb, None, timeout_us=10_000_000) == bf.BF_OK
-        launched = [b for b in batches if b is not None]
-        assert launched and max(n for _, n in launched) > 1, launched
+        # batches of 4, three in flight on different streams: some run at the same time
+        _, outs, info, times = burst(4, 3)
+        for out, ref in zip(outs, solo):
+            np.testing.assert_allclose(out, ref, atol=1e-4)
+        spans = sorted({(bid, t) for (bid, _), t in zip(info, times)})
+        overlap = any(spans[i][1][0] < spans[j][1][1] and spans[j][1][0] < spans[i][1][1]
+                      for i in range(len(spans)) for j in range(i + 1, len(spans)))
+        assert len(spans) >= 2 and overlap, spans
         with pytest.raises(bf.BFError) as ei:
             bf.bf_poll(handles[0], tickets[0], None, 0)
         assert ei.value.code == bf.BF_ENOTFOUND
     finally:
+        bf.bf_engine_pause(False)
         bf.bf_engine_configure(64, 3, 0)
-        for h in handles + [hb]:
+        for h in handles:
             bf.bf_destroy(h)
 
 
