@@ -117,6 +117,14 @@ BF_API int bf_beamform(bf_handle *h, const int16_t *rf_dev, int32_t n_samples,
                        const double *angles_rad, int32_t n_angles, uint32_t mode_and_flags,
                        float *out_dev);
 
+/* The same computation as bf_beamform (FP32 storage only) through the plain
+ * baseline kernel: one frame per launch, one thread per pixel, records read
+ * from global memory without staging.  Kept to measure the batched and served
+ * paths against. */
+BF_API int bf_beamform_plain(bf_handle *h, const int16_t *rf_dev, int32_t n_samples,
+                             const double *angles_rad, int32_t n_angles, uint32_t mode_and_flags,
+                             float *out_dev);
+
 /* Asynchronous submission (serving path).  rf: host or device int16
  * [n_angles][n_elements][n_samples]; it is copied (host -> pinned staging ->
  * device ring slot) before the call returns, so the caller may reuse it.

@@ -748,6 +748,61 @@ BF_API int bf_beamform(bf_handle *h, const int16_t *rf_dev, int32_t n_samples,
     return rc;
 }
 
+BF_API int bf_beamform_plain(bf_handle *h, const int16_t *rf_dev, int32_t n_samples,
+                             const double *angles_rad, int32_t n_angles, uint32_t flags,
+                             float *out_dev)
+{
+    if (!h)
+        return fail(BF_EINVAL, "null handle");
+    if (!rf_dev || !out_dev)
+        return fail(BF_EINVAL, "null data pointer");
+    if (flags & BF_PREC_MASK)
+        return fail(BF_EINVAL, "the plain kernel computes from int16 records in FP32 only");
+    cudaSetDevice(h->device);
+    if (!is_device_pointer(rf_dev) || !is_device_pointer(out_dev))
+        return fail(BF_EINVAL, "bf_beamform_plain needs device pointers");
+    std::vector<FramePrep> frames(1);
+    int rc = prepare_frame(h, rf_dev, n_samples, angles_rad, n_angles, flags, out_dev, h->scratch,
+                           frames[0]);
+    if (rc)
+        return rc;
+    HostLaunch hl;
+    build_launch(frames, hl);
+    const BfJob &job = hl.jobs[0];
+    cudaError_t e = launch_plain(job, rf_dev, (const int2 *)frames[0].plan->valid.p,
+                                 (const float *)h->dx2.p, pad_cols(h->g.nx), n_samples, h->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "plain kernel launch");
+    if (frames[0].stage == BF_OUT_RF)
+        return BF_OK;
+    // envelope / log stages as in bf_beamform
+    hl.jobs.clear();
+    hl.groups.clear();
+    hl.igroups.clear();
+    rc = h->launch.upload(hl, h->stream, true);
+    if (!rc && !h->err_cleared) {
+        cudaMemsetAsync(h->launch.err.p, 0, sizeof(int), h->stream);
+        h->err_cleared = true;
+    }
+    if (!rc)
+        rc = cudaMemsetAsync(frames[0].maxbits, 0, 4 * sizeof(unsigned), h->stream) == cudaSuccess
+                 ? BF_OK
+                 : fail(BF_ECUDA, "cudaMemsetAsync");
+    if (!rc && !hl.env.empty()) {
+        e = launch_envelope((const EnvJob *)h->launch.env.p, (const int *)h->launch.env_prefix.p,
+                            (int)hl.env.size(), hl.env_blocks, hl.env_smem, h->stream);
+        if (e != cudaSuccess)
+            rc = cuda_fail(e, "envelope launch");
+    }
+    if (!rc && !hl.log.empty()) {
+        e = launch_log((const LogJob *)h->launch.log.p, (const int *)h->launch.blk_prefix.p,
+                       (int)hl.log.size(), hl.log_blocks, 70.0f, h->stream);
+        if (e != cudaSuccess)
+            rc = cuda_fail(e, "log launch");
+    }
+    return rc;
+}
+
 BF_API int bf_sync(bf_handle *h)
 {
     if (!h)

@@ -117,6 +117,10 @@ cudaError_t launch_envelope(const EnvJob *jobs_dev, const int *blk_prefix_dev, i
                             int total_blocks, size_t smem_bytes, cudaStream_t stream);
 cudaError_t launch_log(const LogJob *jobs_dev, const int *blk_prefix_dev, int njobs,
                        int total_blocks, float dynamic_range_db, cudaStream_t stream);
+// One frame through the plain baseline kernel (FP32, global loads, one thread
+// per pixel); job.y receives the beamformed modes.
+cudaError_t launch_plain(const BfJob &job, const int16_t *rf, const int2 *valid, const float *dx2,
+                         int nxp, int ns, cudaStream_t stream);
 size_t beamform_smem_bytes(int wmax, int group, int prec);
 int log_blocks(long long pixels);
 int envelope_cols_per_block(int fft_m);

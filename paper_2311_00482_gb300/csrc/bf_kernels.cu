@@ -573,6 +573,65 @@ __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_ker
     }
 }
 
+// ----------------------------------------------------- plain (baseline) --
+
+// One frame per launch, one thread per pixel, FP32, the int16 records read
+// straight from global memory (no staging, no tiles): the straightforward
+// port of the per-pixel loop, kept as the comparison baseline for the batched
+// and served paths.  Same tables and the same split delay as beamform_kernel.
+template <bool DMAS, bool CF>
+__global__ void __launch_bounds__(256) plain_kernel(const BfJob J, const int16_t *__restrict__ rf,
+                                                    const int2 *__restrict__ valid,
+                                                    const float *__restrict__ dx2, int nxp, int ns)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (long long)J.nx * J.nz)
+        return;
+    const int ix = (int)(p / J.nz), iz = (int)(p - (long long)ix * J.nz);
+    const float Z = __ldg(J.rowZ + iz);
+    float S1 = 0.f, Yd = 0.f, Su2 = 0.f;
+    for (int a = 0; a < J.na; ++a) {
+        const int K = __ldg(J.colK + a * J.nx + ix) + __ldg(J.rowK + a * J.nz + iz);
+        const float f = __ldg(J.colF + a * J.nx + ix) + __ldg(J.rowF + a * J.nz + iz) - 0.5f;
+        float T1 = 0.f, T2 = 0.f;
+        for (int i = 0; i < J.ne; ++i) {
+            const int2 vr = __ldg(valid + ((size_t)a * J.ne + i) * nxp + ix);
+            if (iz < vr.x || iz > vr.y)
+                continue;
+            const float x = rx_excess(__ldg(dx2 + (size_t)i * nxp + ix), Z) + f;
+            const float m = x + kRoundMagic;
+            const float al = x - (m - kRoundMagic);
+            // the host decided 0 <= floor(n) <= ns - 2; FP32 rounding may land one sample
+            // off at a record end, so clamp and move the weight with it (continuous)
+            const int kk = __float_as_int(m) - kRoundBits + K;
+            const int k = min(max(kk, 0), ns - 2);
+            const int16_t *u = rf + ((size_t)a * J.ne + i) * ns;
+            const float u0 = (float)__ldg(u + k), u1 = (float)__ldg(u + k + 1);
+            const float v = fmaf(al + 0.5f + (float)(kk - k), u1 - u0, u0);
+            S1 += v;
+            if (DMAS) {
+                const float av = fabsf(v);
+                T1 += copysignf(sqrt_approx(av), v);
+                T2 += av;
+            }
+            if (CF)
+                Su2 = fmaf(v, v, Su2);
+        }
+        if (DMAS)
+            Yd = fmaf(0.5f * T1, T1, fmaf(-0.5f, T2, Yd));
+    }
+    const size_t plane = (size_t)J.nx * J.nz, o = (size_t)ix * J.nz + iz;
+    int slot = 0;
+    if (J.modes & BF_DAS)
+        J.y[(size_t)(slot++) * plane + o] = S1;
+    if (J.modes & BF_DMAS)
+        J.y[(size_t)(slot++) * plane + o] = Yd;
+    if (J.modes & BF_CF) {
+        const float den = (float)J.na * (float)__ldg(J.apcnt + o) * Su2;
+        J.y[(size_t)(slot++) * plane + o] = den > 0.f ? (S1 * S1 / den) * S1 : 0.f;
+    }
+}
+
 // ------------------------------------------------------------- envelope --
 
 __device__ __forceinline__ float spectral_weight(int k, int L, int band, int kb_lo, int kb_hi)
@@ -864,6 +923,23 @@ cudaError_t launch_beamform(const BfJob *jobs_dev, const int *tile_prefix_dev, i
                                      dmas, cf, rows, err_dev, stream);
     return launch_bf_p<kPrecBF16>(jobs_dev, tile_prefix_dev, njobs, total_tiles, smem_bytes, dmas,
                                   cf, rows, err_dev, stream);
+}
+
+cudaError_t launch_plain(const BfJob &job, const int16_t *rf, const int2 *valid, const float *dx2,
+                         int nxp, int ns, cudaStream_t stream)
+{
+    const long long px = (long long)job.nx * job.nz;
+    const int blocks = (int)((px + 255) / 256);
+    const int dmas = (job.modes & BF_DMAS) ? 1 : 0, cf = (job.modes & BF_CF) ? 1 : 0;
+    if (dmas && cf)
+        plain_kernel<true, true><<<blocks, 256, 0, stream>>>(job, rf, valid, dx2, nxp, ns);
+    else if (dmas)
+        plain_kernel<true, false><<<blocks, 256, 0, stream>>>(job, rf, valid, dx2, nxp, ns);
+    else if (cf)
+        plain_kernel<false, true><<<blocks, 256, 0, stream>>>(job, rf, valid, dx2, nxp, ns);
+    else
+        plain_kernel<false, false><<<blocks, 256, 0, stream>>>(job, rf, valid, dx2, nxp, ns);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_envelope(const EnvJob *jobs_dev, const int *blk_prefix_dev, int njobs,
