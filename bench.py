@@ -52,6 +52,10 @@ def parse():
     p.add_argument("--prec", default="fp32", choices=["fp32", "fp16", "bf16"])
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--workload", default="cyst512",
+                   choices=["cyst512", "batch256", "serving", "precision", "sweep"],
+                   help="cyst512: the headline line; the others print informational lines")
+    p.add_argument("--requests", type=int, default=2000, help="serving: requests per rate")
     return p.parse_args()
 
 
@@ -60,6 +64,24 @@ def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x, device):
+    """Largest x over the ranks of the default process group (x itself alone)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world_size, units_per_step, steps, seconds):
+    """Whole-job throughput in giga-units/s: every rank does units_per_step per step
+    (weak scaling), the job takes the slowest rank's time."""
+    return world_size * units_per_step * steps / seconds / 1e9
 
 
 def frames_rf(n_distinct=4):
@@ -240,35 +262,26 @@ def run_ours(args):
     batch.status(stream)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    bf_ms = []
     barrier()
     torch.cuda.synchronize(dev)
+    split = []
     for k in range(args.steps):
         flush.fill_(k & 0xFF)
         ev[k][0].record(stream)
         batch.launch(stream)
         ev[k][1].record(stream)
-        if k == 0 or k == args.steps - 1:
-            pass
+        # the per-kernel marks are events captured in the graph: read them after
+        # each step (the wait sits outside the step's own event pair)
+        ev[k][1].synchronize()
+        split.append(batch.timing()[0])
     torch.cuda.synchronize(dev)
     barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    # per-kernel split of the last replay (events captured inside the graph)
-    (ingest_ms, beam_ms, post_ms), launches = batch.timing()
-    # the beamforming kernel over every timed step: replay once more per step with timing reads
-    for k in range(min(args.steps, 10)):
-        flush.fill_(3)
-        batch.launch(stream)
-        torch.cuda.synchronize(dev)
-        bf_ms.append(batch.timing()[0][1])
+    _, launches = batch.timing()
+    ingest_ms, beam_ms, post_ms = (statistics.median(x[i] for x in split) for i in range(3))
+    bf_ms = [x[1] for x in split]
     batch.status(stream)
-    t_dev = sum(step_ms) / 1e3
-    if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([t_dev], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev = float(t.item())
+    t_dev = max_over_ranks(sum(step_ms) / 1e3, dev)
 
     # ---- end-to-end leg through bf_submit / bf_poll (pinned host RF, host outputs)
     host_rf = [torch.from_numpy(rfs[k % len(rfs)]).pin_memory() for k in range(B)]
@@ -295,16 +308,11 @@ def run_ours(args):
         e2e_step(True)
     t_e2e = time.perf_counter() - t0
     clocks = sampler.stop()
-    if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([t_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = max_over_ranks(t_e2e, dev)
 
     # ---- results (rank 0)
     units_step = B * nominal_units(acq)
-    value = ws * units_step * args.steps / t_dev / 1e9
+    value = job_value(ws, units_step, args.steps, t_dev)
     props = torch.cuda.get_device_properties(dev)
     sm_count = props.multi_processor_count
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -341,7 +349,7 @@ def run_ours(args):
                      "peak_basis": "%d SMs x 16 SFU/clk x %.0f MHz / 2 square roots per triple"
                                    % (sm_count, sm_max),
                      "traffic": None},
-        "e2e": {"value": ws * units_step * e2e_steps / t_e2e / 1e9, "unit": UNIT,
+        "e2e": {"value": job_value(ws, units_step, e2e_steps, t_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": B * rfs[0].nbytes,
                 "d2h_bytes_per_step": B * nm * acq.nx * acq.nz * 4,
                 "frames_per_s": ws * B * e2e_steps / t_e2e},
@@ -360,10 +368,294 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------- informational modes --
+
+def _setup_gpu():
+    import torch
+
+    from paper_2311_00482_gb300 import build as bfbuild
+
+    bfbuild.build()
+    import paper_2311_00482_gb300 as bf
+
+    bf.load()
+    torch.cuda.set_device(0)
+    return torch, bf
+
+
+def _handle(bf, acq):
+    return bf.bf_create(acq.n_elements, acq.pitch_m, acq.f_number, grid_of(acq), acq.fs_hz,
+                        acq.f0_hz, acq.c_mps)
+
+
+def run_batch256(args):
+    """Uneven 256-frame batch (64..1024 pixels per side, 1..11 angles) in one graph."""
+    torch, bf = _setup_gpu()
+    specs = synth.mixed_batch_specs(256)
+    base = synth.cyst_wires_frame(synth.CYST_WIRES_512)[0][0]  # 0 deg record, reused per angle
+    frames, handles, keep, units, active = [], [], [], 0, 0
+    for k, sp in enumerate(specs):
+        na = sp["n_angles"]
+        acq = synth.CYST_WIRES_512.with_(nx=sp["nx"], nz=sp["nz"], angles_deg=synth.angles_linspace(na))
+        h = _handle(bf, acq)
+        handles.append(h)
+        rf = torch.from_numpy(np.ascontiguousarray(np.broadcast_to(base, (na,) + base.shape))).cuda()
+        flags = (bf.BF_DAS if k % 2 == 0 else bf.BF_DMAS) | bf.BF_OUT_LOGDB
+        out = torch.empty((1, acq.nx, acq.nz), dtype=torch.float32, device="cuda")
+        keep += [rf, out]
+        frames.append((h, rf, acq.n_samples, acq.angles_rad, flags, out))
+        units += nominal_units(acq)
+    batch = bf.Batch(frames)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        batch.launch(st)
+    torch.cuda.synchronize()
+    times, beam = [], []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        batch.launch(st)
+        b.record(st)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+        beam.append(batch.timing()[0][1])
+    batch.status(st)
+    t = statistics.median(times) / 1e3
+    print(json.dumps({"workload": "uneven batch: 256 frames, 64..1024 px per side, 1..11 plane waves, "
+                                  "64 ch x 2048 samples, DAS or DMAS, envelope + log, one CUDA graph",
+                      "frames_per_s": 256 / t, "gpixel_ch_per_s": units / t / 1e9,
+                      "ms_per_batch": 1e3 * t, "beamform_ms": statistics.median(beam),
+                      "note": "0 deg cyst record reused for every angle (work is data-independent)"}),
+          flush=True)
+    batch.close()
+    for h in handles:
+        bf.bf_destroy(h)
+
+
+def run_precision(args):
+    """1024x1024, 128 elements, 4096 samples, 7 angles: time per frame and rel-L2 per storage."""
+    import oracle
+
+    torch, bf = _setup_gpu()
+    acq = synth.PRECISION_1024
+    rf, _ = synth.precision_frame(acq)
+    h = _handle(bf, acq)
+    rng = np.random.default_rng(5)
+    pix = rng.integers(0, acq.nx * acq.nz, 20000)
+    ref = oracle.beamform(rf, acq.x_elements(), acq.angles_rad, grid_of(acq), acq.fs_hz, acq.c_mps,
+                          acq.f_number, pixels=pix)
+    rf_d = torch.from_numpy(rf).cuda()
+    res = {}
+    for name, prec in (("fp32", bf.BF_PREC_FP32), ("fp16", bf.BF_PREC_FP16), ("bf16", bf.BF_PREC_BF16)):
+        flags = bf.BF_DAS | bf.BF_DMAS | bf.BF_CF | prec
+        out = torch.empty((3, acq.nx, acq.nz), dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            bf.bf_beamform(h, rf_d, acq.n_samples, acq.angles_rad, flags, out)
+        bf.bf_sync(h)
+        ts = []
+        for _ in range(10):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            bf.bf_beamform(h, rf_d, acq.n_samples, acq.angles_rad, flags, out)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        got = out.cpu().numpy().reshape(3, -1)[:, pix].astype(np.float64)
+        errs = {m: float(np.linalg.norm(got[k] - ref[m]) / np.linalg.norm(ref[m]))
+                for k, m in enumerate(("das", "dmas", "cf"))}
+        res[name] = {"ms_per_frame": statistics.median(ts), "rel_l2": errs,
+                     "gpixel_ch_per_s": nominal_units(acq) / (statistics.median(ts) / 1e3) / 1e9}
+    bf.bf_destroy(h)
+    print(json.dumps({"workload": "1024x1024 px, 128 elements, 4096 samples, 7 plane waves over "
+                                  "+-10 deg, DAS + DMAS + CF, beamformed output (single frames)",
+                      "results": res, "rel_l2_sample": "20000 random pixels vs the FP64 oracle"}),
+          flush=True)
+
+
+def run_sweep(args):
+    """The paper's grid sizes (depth x lateral), 50 MHz, 7.5 MHz probe, 3 cm, RF-DAS."""
+    import oracle
+
+    torch, bf = _setup_gpu()
+    rows = []
+    for nz, nx in synth.PAPER_GRIDS:
+        acq = synth.Acquisition(f0_hz=7.5e6, fs_hz=50e6, n_samples=2048, nx=nx, nz=nz,
+                                x0_m=-9.45e-3, x1_m=9.45e-3, z0_m=1e-3, z1_m=30e-3)
+        rng = np.random.default_rng(7)
+        ph = synth.make_phantom(acq, rng, n_speckle=3000, points=np.array([[0.0, 15e-3]]))
+        rf = synth.synth_rf(acq, ph, rng)
+        h = _handle(bf, acq)
+        rf_d = torch.from_numpy(rf).cuda()
+        out = torch.empty((1, nx, nz), dtype=torch.float32, device="cuda")
+        flags = bf.BF_DAS | bf.BF_OUT_LOGDB
+        for _ in range(5):
+            bf.bf_beamform(h, rf_d, acq.n_samples, acq.angles_rad, flags, out)
+        bf.bf_sync(h)
+        ts = []
+        for _ in range(100):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            bf.bf_beamform(h, rf_d, acq.n_samples, acq.angles_rad, flags, out)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        cts = []
+        for _ in range(5):
+            t0 = time.perf_counter()
+            r = oracle.beamform(rf, acq.x_elements(), acq.angles_rad, grid_of(acq), acq.fs_hz,
+                                acq.c_mps, acq.f_number)
+            oracle.log_compress(oracle.envelope(r["das"]))
+            cts.append(1e3 * (time.perf_counter() - t0))
+        g, c = statistics.median(ts), statistics.median(cts)
+        rows.append({"grid": "%dx%d" % (nz, nx), "gpu_ms": g, "cpu_oracle_ms": c, "speedup": c / g})
+        bf.bf_destroy(h)
+    import oracle as _o
+
+    print(json.dumps({"workload": "grid sweep of Sec. II-D, RF-DAS + envelope + log, one frame per call, "
+                                  "median of 100 (GPU) / 5 (FP64 oracle, %d threads)" % _o.max_threads(),
+                      "rows": rows}), flush=True)
+
+
+def run_serving(args):
+    """Poisson arrivals of mixed requests: continuous-batching engine (FP16 storage)
+    vs the plain FP32 one-frame-per-launch kernel on the same trace."""
+    import threading
+
+    torch, bf = _setup_gpu()
+    sys.setswitchinterval(1e-5)  # the submitting thread spins; let the completion thread in
+    rng = np.random.default_rng(synth.BASE_SEED + 4)
+    base = synth.cyst_wires_frame(synth.CYST_WIRES_512)[0][0]
+    pool = [np.ascontiguousarray(np.broadcast_to(base, (7,) + base.shape)) for _ in range(1)]
+    handles = {}
+
+    def handle(n):
+        if n not in handles:
+            handles[n] = _handle(bf, synth.CYST_WIRES_512.with_(nx=n, nz=n))
+        return handles[n]
+
+    N = args.requests
+    trace = []
+    for k in range(N):
+        n = 64 * int(rng.integers(2, 17))  # 128 .. 1024 pixels per side
+        na = int(rng.integers(1, 8))
+        mode = bf.BF_DAS if rng.random() < 0.5 else bf.BF_DMAS
+        ang = np.deg2rad(synth.angles_linspace(na))
+        trace.append((n, na, mode, ang))
+    for n, na, mode, ang in trace:  # tables resident before the clock starts
+        for prec in (bf.BF_PREC_FP16, bf.BF_PREC_FP32):
+            bf.bf_plan_info(handle(n), 2048, ang, mode | prec)
+    outs = {n: np.empty((1, n, n), np.float32) for n in handles}
+    results = []
+    for rate in (1000, 2000, 5000, 10000, 20000):
+        gaps = rng.exponential(1.0 / rate, N)
+        for engine in ("batched_fp16", "plain_fp32"):
+            lat = [0.0] * N
+            t_sub = [0.0] * N
+            done = threading.Event()
+            if engine == "batched_fp16":
+                tickets = [None] * N
+                ready = threading.Semaphore(0)
+
+                def poller():
+                    for k in range(N):
+                        ready.acquire()
+                        n, na, mode, ang = trace[k]
+                        bf.bf_poll(handle(n), tickets[k], outs[n], timeout_us=60_000_000)
+                        lat[k] = time.perf_counter() - t_sub[k]
+                    done.set()
+
+                th = threading.Thread(target=poller)
+                th.start()
+                t0 = time.perf_counter()
+                t_next = t0
+                for k in range(N):
+                    t_next += gaps[k]
+                    while time.perf_counter() < t_next:
+                        pass
+                    n, na, mode, ang = trace[k]
+                    t_sub[k] = time.perf_counter()
+                    while True:
+                        try:
+                            tickets[k] = bf.bf_submit(handle(n), pool[0][:na], 2048, ang,
+                                                      mode | bf.BF_PREC_FP16 | bf.BF_OUT_LOGDB)
+                            break
+                        except bf.BFError as e:
+                            if e.code != bf.BF_EAGAIN:
+                                raise
+                    ready.release()
+                done.wait()
+                th.join()
+                t_all = time.perf_counter() - t0
+            else:
+                # a queue in front of the plain kernel: one request at a time, copy in,
+                # one launch, copy out
+                q = []
+                lock = threading.Condition()
+                rf_pin = torch.from_numpy(pool[0]).pin_memory()
+                rf_dev = torch.empty_like(rf_pin, device="cuda")
+                out_dev = torch.empty((1, 1024, 1024), dtype=torch.float32, device="cuda")
+                out_pin = torch.empty((1024 * 1024,), dtype=torch.float32).pin_memory()
+
+                def worker():
+                    for k in range(N):
+                        with lock:
+                            while not q:
+                                lock.wait()
+                            q.pop(0)
+                        n, na, mode, ang = trace[k]
+                        h = handle(n)
+                        nb = na * 64 * 2048
+                        rf_dev.view(-1)[:nb].copy_(rf_pin.view(-1)[:nb], non_blocking=True)
+                        bf.bf_set_stream(h, torch.cuda.current_stream().cuda_stream)
+                        bf.bf_beamform_plain(h, rf_dev.view(-1)[:nb], 2048, ang, mode | bf.BF_OUT_LOGDB,
+                                             out_dev.view(-1)[:n * n])
+                        out_pin[:n * n].copy_(out_dev.view(-1)[:n * n], non_blocking=True)
+                        torch.cuda.current_stream().synchronize()
+                        lat[k] = time.perf_counter() - t_sub[k]
+                    done.set()
+
+                th = threading.Thread(target=worker)
+                th.start()
+                t0 = time.perf_counter()
+                t_next = t0
+                for k in range(N):
+                    t_next += gaps[k]
+                    while time.perf_counter() < t_next:
+                        pass
+                    t_sub[k] = time.perf_counter()
+                    with lock:
+                        q.append(k)
+                        lock.notify()
+                done.wait()
+                th.join()
+                t_all = time.perf_counter() - t0
+                for h in handles.values():
+                    bf.bf_set_stream(h, None)
+            results.append({"rate_hz": rate, "engine": engine, "frames_per_s": N / t_all,
+                            "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                            "p99_ms": 1e3 * float(np.percentile(lat, 99))})
+            print(json.dumps(results[-1]), flush=True)
+    print(json.dumps({"workload": "serving: Poisson arrivals, square grids 128..1024 px, 1..7 plane waves, "
+                                  "DAS or DMAS, 64 ch x 2048 samples, host RF in, host dB image out",
+                      "requests_per_rate": N, "results": results}), flush=True)
+    for h in handles.values():
+        bf.bf_destroy(h)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch256":
+        run_batch256(args)
+    elif args.workload == "precision":
+        run_precision(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 
