@@ -99,7 +99,7 @@ def nominal_units(acq):
 
 # ------------------------------------------------------------------ CPU --
 
-def time_oracle(acq, rfs, budget_s, max_frames=64):
+def time_oracle(acq, rfs, budget_s, max_frames=2000):
     """FP64 oracle (beamform + envelope + log for DAS and DMAS) on host cores."""
     import oracle
 
@@ -399,7 +399,7 @@ def run_batch256(args):
         acq = synth.CYST_WIRES_512.with_(nx=sp["nx"], nz=sp["nz"], angles_deg=synth.angles_linspace(na))
         h = _handle(bf, acq)
         handles.append(h)
-        rf = torch.from_numpy(np.ascontiguousarray(np.broadcast_to(base, (na,) + base.shape))).cuda()
+        rf = torch.from_numpy(np.broadcast_to(base, (na,) + base.shape).copy()).cuda()
         flags = (bf.BF_DAS if k % 2 == 0 else bf.BF_DMAS) | bf.BF_OUT_LOGDB
         out = torch.empty((1, acq.nx, acq.nz), dtype=torch.float32, device="cuda")
         keep += [rf, out]
@@ -447,6 +447,7 @@ def run_precision(args):
     ref = oracle.beamform(rf, acq.x_elements(), acq.angles_rad, grid_of(acq), acq.fs_hz, acq.c_mps,
                           acq.f_number, pixels=pix)
     rf_d = torch.from_numpy(rf).cuda()
+    bf.bf_set_stream(h, torch.cuda.current_stream())  # events below time this stream
     res = {}
     for name, prec in (("fp32", bf.BF_PREC_FP32), ("fp16", bf.BF_PREC_FP16), ("bf16", bf.BF_PREC_BF16)):
         flags = bf.BF_DAS | bf.BF_DMAS | bf.BF_CF | prec
@@ -487,6 +488,7 @@ def run_sweep(args):
         ph = synth.make_phantom(acq, rng, n_speckle=3000, points=np.array([[0.0, 15e-3]]))
         rf = synth.synth_rf(acq, ph, rng)
         h = _handle(bf, acq)
+        bf.bf_set_stream(h, torch.cuda.current_stream())  # events below time this stream
         rf_d = torch.from_numpy(rf).cuda()
         out = torch.empty((1, nx, nz), dtype=torch.float32, device="cuda")
         flags = bf.BF_DAS | bf.BF_OUT_LOGDB
@@ -519,15 +521,18 @@ def run_sweep(args):
 
 
 def run_serving(args):
-    """Poisson arrivals of mixed requests: continuous-batching engine (FP16 storage)
-    vs the plain FP32 one-frame-per-launch kernel on the same trace."""
+    """Poisson arrivals of mixed requests, pinned host RF in and host dB images
+    out: the continuous-batching engine (FP16 storage) against a FIFO in front
+    of the plain FP32 one-frame-per-launch kernel, on the same trace."""
+    import queue
     import threading
 
     torch, bf = _setup_gpu()
     sys.setswitchinterval(1e-5)  # the submitting thread spins; let the completion thread in
     rng = np.random.default_rng(synth.BASE_SEED + 4)
     base = synth.cyst_wires_frame(synth.CYST_WIRES_512)[0][0]
-    pool = [np.ascontiguousarray(np.broadcast_to(base, (7,) + base.shape)) for _ in range(1)]
+    rf_host = torch.from_numpy(np.ascontiguousarray(np.broadcast_to(base, (7,) + base.shape)))
+    rf_host = rf_host.pin_memory()
     handles = {}
 
     def handle(n):
@@ -537,108 +542,93 @@ def run_serving(args):
 
     N = args.requests
     trace = []
-    for k in range(N):
+    for _ in range(N):
         n = 64 * int(rng.integers(2, 17))  # 128 .. 1024 pixels per side
         na = int(rng.integers(1, 8))
         mode = bf.BF_DAS if rng.random() < 0.5 else bf.BF_DMAS
-        ang = np.deg2rad(synth.angles_linspace(na))
-        trace.append((n, na, mode, ang))
-    for n, na, mode, ang in trace:  # tables resident before the clock starts
-        for prec in (bf.BF_PREC_FP16, bf.BF_PREC_FP32):
-            bf.bf_plan_info(handle(n), 2048, ang, mode | prec)
-    outs = {n: np.empty((1, n, n), np.float32) for n in handles}
+        trace.append((n, na, mode, np.deg2rad(synth.angles_linspace(na))))
+    outs = {n: torch.empty((1, n, n), dtype=torch.float32).pin_memory() for n, *_ in trace}
+    stream = torch.cuda.Stream()
+    rf_dev = torch.empty_like(rf_host, device="cuda")
+    out_dev = torch.empty((1024 * 1024,), dtype=torch.float32, device="cuda")
+
+    def engine_submit(k):
+        n, na, mode, ang = trace[k]
+        while True:
+            try:
+                return bf.bf_submit(handle(n), rf_host[:na], 2048, ang,
+                                    mode | bf.BF_PREC_FP16 | bf.BF_OUT_LOGDB)
+            except bf.BFError as e:
+                if e.code != bf.BF_EAGAIN:
+                    raise
+
+    def engine_wait(k, ticket):
+        n = trace[k][0]
+        bf.bf_poll(handle(n), ticket, outs[n], timeout_us=60_000_000)
+
+    def plain_run(k):
+        n, na, mode, ang = trace[k]
+        h = handle(n)
+        nb = na * 64 * 2048
+        with torch.cuda.stream(stream):
+            rf_dev.view(-1)[:nb].copy_(rf_host.view(-1)[:nb], non_blocking=True)
+            bf.bf_beamform_plain(h, rf_dev.view(-1)[:nb], 2048, ang, mode | bf.BF_OUT_LOGDB,
+                                 out_dev[:n * n])
+            outs[n].view(-1).copy_(out_dev[:n * n], non_blocking=True)
+        stream.synchronize()
+
+    for h in set(handle(n) for n, *_ in trace):
+        bf.bf_set_stream(h, stream)
+    # untimed pass: every table, slot and scratch buffer exists before the clock starts
+    seen = set()
+    for k in range(N):
+        if (trace[k][0], trace[k][1], trace[k][2]) not in seen:
+            seen.add((trace[k][0], trace[k][1], trace[k][2]))
+            plain_run(k)
+    tickets = [engine_submit(k) for k in range(N)]
+    for k in range(N):
+        engine_wait(k, tickets[k])
+
+    def drive(rate, kind):
+        gaps = rng.exponential(1.0 / rate, N)
+        lat, t_sub = [0.0] * N, [0.0] * N
+        handoff = queue.Queue()
+
+        def completer():
+            for k in range(N):
+                item = handoff.get()
+                if kind == "batched_fp16":
+                    engine_wait(k, item)
+                else:
+                    plain_run(k)
+                lat[k] = time.perf_counter() - t_sub[k]
+
+        th = threading.Thread(target=completer)
+        th.start()
+        t0 = time.perf_counter()
+        t_next = t0
+        for k in range(N):
+            t_next += gaps[k]
+            while time.perf_counter() < t_next:
+                pass
+            t_sub[k] = time.perf_counter()
+            handoff.put(engine_submit(k) if kind == "batched_fp16" else k)
+        th.join()
+        t_all = time.perf_counter() - t0
+        units = sum(n * n * 64 * na for n, na, _, _ in trace)
+        return {"rate_hz": rate, "engine": kind, "frames_per_s": N / t_all,
+                "gpixel_ch_per_s": units / t_all / 1e9,
+                "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99))}
+
     results = []
     for rate in (1000, 2000, 5000, 10000, 20000):
-        gaps = rng.exponential(1.0 / rate, N)
-        for engine in ("batched_fp16", "plain_fp32"):
-            lat = [0.0] * N
-            t_sub = [0.0] * N
-            done = threading.Event()
-            if engine == "batched_fp16":
-                tickets = [None] * N
-                ready = threading.Semaphore(0)
-
-                def poller():
-                    for k in range(N):
-                        ready.acquire()
-                        n, na, mode, ang = trace[k]
-                        bf.bf_poll(handle(n), tickets[k], outs[n], timeout_us=60_000_000)
-                        lat[k] = time.perf_counter() - t_sub[k]
-                    done.set()
-
-                th = threading.Thread(target=poller)
-                th.start()
-                t0 = time.perf_counter()
-                t_next = t0
-                for k in range(N):
-                    t_next += gaps[k]
-                    while time.perf_counter() < t_next:
-                        pass
-                    n, na, mode, ang = trace[k]
-                    t_sub[k] = time.perf_counter()
-                    while True:
-                        try:
-                            tickets[k] = bf.bf_submit(handle(n), pool[0][:na], 2048, ang,
-                                                      mode | bf.BF_PREC_FP16 | bf.BF_OUT_LOGDB)
-                            break
-                        except bf.BFError as e:
-                            if e.code != bf.BF_EAGAIN:
-                                raise
-                    ready.release()
-                done.wait()
-                th.join()
-                t_all = time.perf_counter() - t0
-            else:
-                # a queue in front of the plain kernel: one request at a time, copy in,
-                # one launch, copy out
-                q = []
-                lock = threading.Condition()
-                rf_pin = torch.from_numpy(pool[0]).pin_memory()
-                rf_dev = torch.empty_like(rf_pin, device="cuda")
-                out_dev = torch.empty((1, 1024, 1024), dtype=torch.float32, device="cuda")
-                out_pin = torch.empty((1024 * 1024,), dtype=torch.float32).pin_memory()
-
-                def worker():
-                    for k in range(N):
-                        with lock:
-                            while not q:
-                                lock.wait()
-                            q.pop(0)
-                        n, na, mode, ang = trace[k]
-                        h = handle(n)
-                        nb = na * 64 * 2048
-                        rf_dev.view(-1)[:nb].copy_(rf_pin.view(-1)[:nb], non_blocking=True)
-                        bf.bf_set_stream(h, torch.cuda.current_stream().cuda_stream)
-                        bf.bf_beamform_plain(h, rf_dev.view(-1)[:nb], 2048, ang, mode | bf.BF_OUT_LOGDB,
-                                             out_dev.view(-1)[:n * n])
-                        out_pin[:n * n].copy_(out_dev.view(-1)[:n * n], non_blocking=True)
-                        torch.cuda.current_stream().synchronize()
-                        lat[k] = time.perf_counter() - t_sub[k]
-                    done.set()
-
-                th = threading.Thread(target=worker)
-                th.start()
-                t0 = time.perf_counter()
-                t_next = t0
-                for k in range(N):
-                    t_next += gaps[k]
-                    while time.perf_counter() < t_next:
-                        pass
-                    t_sub[k] = time.perf_counter()
-                    with lock:
-                        q.append(k)
-                        lock.notify()
-                done.wait()
-                th.join()
-                t_all = time.perf_counter() - t0
-                for h in handles.values():
-                    bf.bf_set_stream(h, None)
-            results.append({"rate_hz": rate, "engine": engine, "frames_per_s": N / t_all,
-                            "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                            "p99_ms": 1e3 * float(np.percentile(lat, 99))})
+        for kind in ("batched_fp16", "plain_fp32"):
+            results.append(drive(rate, kind))
             print(json.dumps(results[-1]), flush=True)
     print(json.dumps({"workload": "serving: Poisson arrivals, square grids 128..1024 px, 1..7 plane waves, "
-                                  "DAS or DMAS, 64 ch x 2048 samples, host RF in, host dB image out",
+                                  "DAS or DMAS, 64 ch x 2048 samples, pinned host RF in, pinned host "
+                                  "dB image out; plain_fp32 = FIFO of one-frame launches",
                       "requests_per_rate": N, "results": results}), flush=True)
     for h in handles.values():
         bf.bf_destroy(h)

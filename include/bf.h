@@ -89,7 +89,8 @@ enum {
     BF_ENOSYS = -7       /* feature not available in this build */
 };
 
-/* Create a handle for one geometry and pixel grid.  fs_hz: sampling rate,
+/* Paper: Sec. II-B (array, pixel grid and the time of flight of Eq. (1)).
+ * Create a handle for one geometry and pixel grid.  fs_hz: sampling rate,
  * f0_hz: transmit centre frequency (sets the DMAS band-pass), c_mps: speed
  * of sound.  Uploads the geometry tables to the current CUDA device.
  * *out receives the handle (caller owns it; free with bf_destroy). */
@@ -106,7 +107,9 @@ BF_API int bf_set_stream(bf_handle *h, void *cuda_stream);
 /* Bytes of one output for the given mode_and_flags: popcount(modes) * nx * nz * 4. */
 BF_API size_t bf_output_bytes(const bf_handle *h, uint32_t mode_and_flags);
 
-/* Stream-ordered beamforming of one frame, device-resident data.
+/* Paper: Sec. II-B, Eq. (1) (delay, interpolation, apodization, sum), the
+ * B-mode display of Fig. 3 (envelope, -70 dB), timed as in Sec. III-B.
+ * Stream-ordered beamforming of one frame, device-resident data.
  * rf_dev: device int16 [n_angles][n_elements][n_samples] (read during the call's
  * stream work), angles_rad: host array of n_angles plane-wave angles in
  * (-pi/2, pi/2); out_dev: device float [popcount(modes)][nx][nz] (modes in bit
@@ -117,7 +120,8 @@ BF_API int bf_beamform(bf_handle *h, const int16_t *rf_dev, int32_t n_samples,
                        const double *angles_rad, int32_t n_angles, uint32_t mode_and_flags,
                        float *out_dev);
 
-/* The same computation as bf_beamform (FP32 storage only) through the plain
+/* Paper: Sec. II-B, Eq. (1); the one-frame-per-call GPU execution of Sec. II-A.
+ * The same computation as bf_beamform (FP32 storage only) through the plain
  * baseline kernel: one frame per launch, one thread per pixel, records read
  * from global memory without staging.  Kept to measure the batched and served
  * paths against. */
@@ -125,7 +129,9 @@ BF_API int bf_beamform_plain(bf_handle *h, const int16_t *rf_dev, int32_t n_samp
                              const double *angles_rad, int32_t n_angles, uint32_t mode_and_flags,
                              float *out_dev);
 
-/* Asynchronous submission (serving path).  rf: host or device int16
+/* Paper: the front end streams frames to the host GPU one after another
+ * (Sec. II-A); request queueing and batching have no counterpart there.
+ * Asynchronous submission (serving path).  rf: host or device int16
  * [n_angles][n_elements][n_samples]; it is copied (host -> pinned staging ->
  * device ring slot) before the call returns, so the caller may reuse it.
  * *ticket_out identifies the request.  BF_EAGAIN when no slot or device
@@ -180,7 +186,9 @@ typedef struct bf_frame {
     float *out_dev;
 } bf_frame;
 
-/* Prepare a batch of frames with uneven grids and angle counts: builds the
+/* Paper: no counterpart (the paper beamforms one frame per call); each frame
+ * is computed as bf_beamform computes it (Sec. II-B, Eq. (1)).
+ * Prepare a batch of frames with uneven grids and angle counts: builds the
  * per-frame tables and one flat work list over all (frame, pixel tile) items
  * and captures the batch's kernels in a CUDA graph.  The frame descriptors
  * are copied; the RF and output buffers must stay valid while the batch is
@@ -196,7 +204,8 @@ BF_API int bf_batch_status(bf_batch *b, void *cuda_stream);
 BF_API int bf_batch_timing(bf_batch *b, float *ms3, int32_t *kernel_launches);
 BF_API int bf_batch_destroy(bf_batch *b);
 
-/* Host-only diagnostic (touches no GPU): the double-precision decision
+/* Paper: the F-number aperture and the record bound of Sec. II-B.
+ * Host-only diagnostic (touches no GPU): the double-precision decision
  * tables the device path consumes.  valid_rows [n_angles][nx][n_elements][2]
  * receives the first and last pixel row iz at which channel i's sample
  * counts for column ix and angle a (inside the aperture and
@@ -208,7 +217,8 @@ BF_API int bf_host_tables(const bf_geometry *geometry, const bf_grid *grid, doub
                           const double *angles_rad, int32_t n_angles, int32_t *valid_rows,
                           uint16_t *aperture_count);
 
-/* Plan introspection (builds the plan if needed): info8 receives
+/* Paper: no counterpart (tiling of this implementation).
+ * Plan introspection (builds the plan if needed): info8 receives
  * {window pairs staged per channel, TMA box width, channels per stage, rows
  * per thread, tiles across, tiles down, pairs per channel record, entries of
  * the window table}; wtab (optional, wtab_entries >= info8[7]) the first

@@ -65,6 +65,13 @@ int DevMem::ensure(size_t n)
     return BF_OK;
 }
 
+int DevMem::reserve(size_t n)
+{
+    if (n <= bytes && p)
+        return BF_OK;
+    return ensure(std::max<size_t>({n, bytes + bytes / 2, 4096}));
+}
+
 void DevMem::release()
 {
     if (p)
@@ -496,7 +503,7 @@ int DeviceLaunch::upload(const HostLaunch &hl, cudaStream_t st, bool async)
     auto put = [&](DevMem &d, const void *src, size_t n) -> int {
         if (n == 0)
             return BF_OK;
-        int rc = d.ensure(n);
+        int rc = d.reserve(n);
         if (rc)
             return rc;
         cudaError_t e = async ? cudaMemcpyAsync(d.p, src, n, cudaMemcpyHostToDevice, st)

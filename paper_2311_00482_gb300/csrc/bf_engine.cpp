@@ -11,7 +11,15 @@
 // requests that arrive while others run are admitted and launched as memory
 // and slots free up and their work overlaps on the device.  bf_poll waits for
 // the request's batch, copies the result out and releases the slot.
+//
+// Host data moves by DMA where it can: RF in pinned (page-locked) host
+// memory goes straight to the device slot, results go straight into a pinned
+// or device destination; pageable buffers pass through the slot's pinned
+// staging, copied on the host by a few helper threads at once.  A batch's job
+// lists, status word and events are recycled through a pool, so a launch
+// allocates nothing once the engine is warm.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdlib>
@@ -28,16 +36,150 @@ namespace {
 
 constexpr int kStreams = 4;
 
+// Host memcpy split across helper threads (the caller takes chunks too): one
+// core copies well below the host memory bandwidth, and the RF in and the
+// images out of a serving loop are megabytes per frame.
+class CopyPool {
+public:
+    static CopyPool &get()
+    {
+        static CopyPool *pool = new CopyPool();  // process lifetime, like the engines
+        return *pool;
+    }
+
+    void copy(void *dst, const void *src, size_t n)
+    {
+        if (n < kMinSplit || helpers_ == 0) {
+            std::memcpy(dst, src, n);
+            return;
+        }
+        Job j;
+        j.dst = static_cast<char *>(dst);
+        j.src = static_cast<const char *>(src);
+        j.n = n;
+        j.nchunks = (int)((n + kChunk - 1) / kChunk);
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            q_.push_back(&j);
+        }
+        cv_.notify_all();
+        work(&j);
+        std::unique_lock<std::mutex> lk(mu_);
+        auto it = std::find(q_.begin(), q_.end(), &j);
+        if (it != q_.end())
+            q_.erase(it);
+        // every chunk is claimed; wait for helpers still copying theirs
+        done_.wait(lk, [&] { return j.users == 0; });
+    }
+
+private:
+    static constexpr size_t kChunk = (size_t)256 << 10;
+    static constexpr size_t kMinSplit = (size_t)512 << 10;
+    struct Job {
+        char *dst = nullptr;
+        const char *src = nullptr;
+        size_t n = 0;
+        int nchunks = 0;
+        std::atomic<int> next{0};
+        int users = 0;  // helpers inside work(), guarded by mu_
+    };
+
+    CopyPool()
+    {
+        const unsigned hw = std::thread::hardware_concurrency();
+        helpers_ = (int)std::min<unsigned>(7u, hw > 2 ? hw / 2 : 0u);
+        for (int i = 0; i < helpers_; ++i)
+            std::thread([this] { loop(); }).detach();
+    }
+
+    static void work(Job *j)
+    {
+        for (;;) {
+            const int c = j->next.fetch_add(1, std::memory_order_relaxed);
+            if (c >= j->nchunks)
+                return;
+            const size_t o = (size_t)c * kChunk;
+            std::memcpy(j->dst + o, j->src + o, std::min(kChunk, j->n - o));
+        }
+    }
+
+    void loop()
+    {
+        for (;;) {
+            Job *j = nullptr;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&] { return !q_.empty(); });
+                j = q_.front();
+                if (j->next.load(std::memory_order_relaxed) >= j->nchunks) {
+                    q_.pop_front();
+                    continue;
+                }
+                ++j->users;
+            }
+            work(j);
+            {
+                std::lock_guard<std::mutex> lk(mu_);
+                --j->users;
+            }
+            done_.notify_all();
+        }
+    }
+
+    int helpers_ = 0;
+    std::mutex mu_;
+    std::condition_variable cv_, done_;
+    std::deque<Job *> q_;
+};
+
+enum PtrKind { kPageable = 0, kPinned = 1, kDevice = 2 };
+
+PtrKind pointer_kind(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return kPageable;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+        return kDevice;
+    return a.type == cudaMemoryTypeHost ? kPinned : kPageable;
+}
+
+// Page-locked host buffer that grows on demand (contents not kept).
+struct PinnedBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~PinnedBuf()
+    {
+        if (p)
+            cudaFreeHost(p);
+    }
+    bool ensure(size_t n)
+    {
+        if (n <= bytes && p)
+            return true;
+        if (p)
+            cudaFreeHost(p);
+        p = nullptr;
+        bytes = 0;
+        if (cudaMallocHost(&p, n) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return false;
+        }
+        bytes = n;
+        return true;
+    }
+};
+
 struct Slot {
     DevMem rf, out;
     FrameScratch scratch;
-    void *pinned = nullptr;
-    size_t pinned_bytes = 0;
+    PinnedBuf pin_in, pin_out;
     cudaEvent_t h2d = nullptr;
     ~Slot()
     {
-        if (pinned)
-            cudaFreeHost(pinned);
         if (h2d)
             cudaEventDestroy(h2d);
     }
@@ -48,16 +190,63 @@ struct Slot {
     }
 };
 
-struct Batch {
-    int id = 0, frames = 0;
-    cudaEvent_t start = nullptr, done = nullptr;
+// Device job lists, status word and events of one launched batch.
+struct BatchRes {
     DeviceLaunch dl;
-    ~Batch()
+    cudaEvent_t start = nullptr, done = nullptr;
+    int *err_host = nullptr;  // pinned copy of the status word, written after the last kernel
+    bool clean = true;        // false: the launch failed part-way, do not reuse
+    ~BatchRes()
     {
         if (start)
             cudaEventDestroy(start);
         if (done)
             cudaEventDestroy(done);
+        if (err_host)
+            cudaFreeHost(err_host);
+    }
+    int init()
+    {
+        if (!start && cudaEventCreate(&start) != cudaSuccess)
+            return fail(BF_ECUDA, "cudaEventCreate");
+        if (!done && cudaEventCreate(&done) != cudaSuccess)
+            return fail(BF_ECUDA, "cudaEventCreate");
+        if (!err_host && cudaMallocHost((void **)&err_host, 64) != cudaSuccess)
+            return fail(BF_ENOMEM, "cudaMallocHost (status word)");
+        *err_host = 0;
+        return BF_OK;
+    }
+};
+
+struct ResPool {
+    std::mutex mu;
+    std::vector<std::unique_ptr<BatchRes>> free;
+    std::unique_ptr<BatchRes> take()
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (free.empty())
+            return std::make_unique<BatchRes>();
+        std::unique_ptr<BatchRes> r = std::move(free.back());
+        free.pop_back();
+        return r;
+    }
+    void give(std::unique_ptr<BatchRes> r)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        free.push_back(std::move(r));
+    }
+};
+
+// A launched batch; its resources go back to the pool once the last request
+// riding in it has been released (its kernels have finished by then).
+struct Batch {
+    int id = 0, frames = 0;
+    std::unique_ptr<BatchRes> res;
+    ResPool *pool = nullptr;
+    ~Batch()
+    {
+        if (res && pool && res->clean && cudaEventQuery(res->done) == cudaSuccess)
+            pool->give(std::move(res));
     }
 };
 
@@ -142,6 +331,7 @@ private:
     cudaStream_t streams_[kStreams]{};
     cudaStream_t copy_ = nullptr, d2h_ = nullptr;
     std::thread worker_;
+    ResPool res_pool_;
 };
 
 std::unique_ptr<Slot> Engine::take_slot()
@@ -233,34 +423,23 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
         live_ -= 1;
         return rc;
     }
-    // RF into the slot: host data through pinned staging, device data directly.
+    // RF into the slot: device and pinned host data by DMA straight from the
+    // caller's buffer (waited for: the caller may reuse it on return),
+    // pageable host data through the slot's pinned staging.
     cudaError_t e;
-    if (is_device_pointer(rf)) {
-        e = cudaMemcpyAsync(s.rf.p, rf, rf_bytes, cudaMemcpyDeviceToDevice, copy_);
+    const PtrKind kind = pointer_kind(rf);
+    if (kind != kPageable) {
+        e = cudaMemcpyAsync(s.rf.p, rf, rf_bytes, cudaMemcpyDefault, copy_);
+    } else if (!s.pin_in.ensure(rf_bytes)) {
+        e = cudaErrorMemoryAllocation;
     } else {
-        if (s.pinned_bytes < rf_bytes) {
-            if (s.pinned)
-                cudaFreeHost(s.pinned);
-            s.pinned = nullptr;
-            s.pinned_bytes = 0;
-            if (cudaMallocHost(&s.pinned, rf_bytes) != cudaSuccess) {
-                cudaGetLastError();
-                s.pinned = nullptr;
-            } else {
-                s.pinned_bytes = rf_bytes;
-            }
-        }
-        if (!s.pinned) {
-            e = cudaErrorMemoryAllocation;
-        } else {
-            std::memcpy(s.pinned, rf, rf_bytes);
-            e = cudaMemcpyAsync(s.rf.p, s.pinned, rf_bytes, cudaMemcpyHostToDevice, copy_);
-        }
+        CopyPool::get().copy(s.pin_in.p, rf, rf_bytes);
+        e = cudaMemcpyAsync(s.rf.p, s.pin_in.p, rf_bytes, cudaMemcpyHostToDevice, copy_);
     }
     if (e == cudaSuccess)
         e = cudaEventRecord(s.h2d, copy_);
-    if (e == cudaSuccess && is_device_pointer(rf))
-        e = cudaEventSynchronize(s.h2d);  // caller may reuse its device buffer on return
+    if (e == cudaSuccess && kind != kPageable)
+        e = cudaEventSynchronize(s.h2d);
     {
         std::lock_guard<std::mutex> lk(mu_);
         const size_t grow = need > before ? need - before : 0;
@@ -289,6 +468,9 @@ void Engine::launch(std::vector<std::shared_ptr<Request>> &reqs)
     auto b = std::make_shared<Batch>();
     b->id = next_batch_++;
     b->frames = (int)reqs.size();
+    b->pool = &res_pool_;
+    b->res = res_pool_.take();
+    BatchRes &R = *b->res;
     cudaStream_t st = streams_[b->id % kStreams];
     std::vector<FramePrep> frames;
     frames.reserve(reqs.size());
@@ -298,23 +480,27 @@ void Engine::launch(std::vector<std::shared_ptr<Request>> &reqs)
     }
     HostLaunch hl;
     build_launch(frames, hl);
-    int rc = BF_OK;
-    if (cudaEventCreate(&b->start) != cudaSuccess || cudaEventCreate(&b->done) != cudaSuccess)
-        rc = fail(BF_ECUDA, "cudaEventCreate");
+    int rc = R.init();
     if (!rc)
         rc = upload_maps(frames, st, true);
     for (size_t i = 0; i < reqs.size(); ++i)
         reqs[i]->fp.map_dirty = false;
     if (!rc)
-        rc = b->dl.upload(hl, st, true);
-    if (!rc && cudaMemsetAsync(b->dl.err.p, 0, sizeof(int), st) != cudaSuccess)
+        rc = R.dl.upload(hl, st, true);
+    if (!rc && cudaMemsetAsync(R.dl.err.p, 0, sizeof(int), st) != cudaSuccess)
         rc = fail(BF_ECUDA, "cudaMemsetAsync");
     if (!rc)
-        cudaEventRecord(b->start, st);
+        cudaEventRecord(R.start, st);
     if (!rc)
-        rc = enqueue(frames, hl, b->dl, st);
-    if (!rc && cudaEventRecord(b->done, st) != cudaSuccess)
+        rc = enqueue(frames, hl, R.dl, st);
+    // the status word travels back with the batch: polls read it without a sync
+    if (!rc && cudaMemcpyAsync(R.err_host, R.dl.err.p, sizeof(int), cudaMemcpyDeviceToHost, st) !=
+                   cudaSuccess)
+        rc = fail(BF_ECUDA, "cudaMemcpyAsync (status word)");
+    if (!rc && cudaEventRecord(R.done, st) != cudaSuccess)
         rc = fail(BF_ECUDA, "cudaEventRecord");
+    if (rc)
+        R.clean = false;
     std::string msg = rc ? std::string(bf_last_error()) : std::string();
     std::lock_guard<std::mutex> lk(mu_);
     for (auto &r : reqs) {
@@ -335,12 +521,13 @@ void Engine::loop()
         {
             std::unique_lock<std::mutex> lk(mu_);
             cv_work_.wait(lk, [&] { return !pending_.empty() && !paused_; });
-            while (!inflight_.empty() && cudaEventQuery(inflight_.front()->done) != cudaErrorNotReady)
+            while (!inflight_.empty() &&
+                   cudaEventQuery(inflight_.front()->res->done) != cudaErrorNotReady)
                 inflight_.pop_front();
             if ((int)inflight_.size() >= max_inflight_) {
                 std::shared_ptr<Batch> oldest = inflight_.front();
                 lk.unlock();
-                cudaEventSynchronize(oldest->done);
+                cudaEventSynchronize(oldest->res->done);
                 continue;
             }
             while (!pending_.empty() && (int)take.size() < max_batch_) {
@@ -383,8 +570,10 @@ int Engine::poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes, in
     }
     int rc = req->rc ? fail(req->rc, "%s", req->err.c_str()) : BF_OK;
     if (!rc) {
+        // spin (yielding) for the first half millisecond, then sleep between queries
+        const auto spin_until = clk::now() + std::chrono::microseconds(500);
         for (;;) {
-            cudaError_t q = cudaEventQuery(req->batch->done);
+            cudaError_t q = cudaEventQuery(req->batch->res->done);
             if (q == cudaSuccess)
                 break;
             if (q != cudaErrorNotReady) {
@@ -393,19 +582,40 @@ int Engine::poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes, in
             }
             if (timeout_us == 0)
                 return BF_PENDING;
-            if (timeout_us > 0 && clk::now() >= deadline)
+            const auto now = clk::now();
+            if (timeout_us > 0 && now >= deadline)
                 return fail(BF_ETIMEDOUT, "ticket %llu not finished within the timeout",
                             (unsigned long long)ticket);
-            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            if (now < spin_until)
+                std::this_thread::yield();
+            else
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
         }
     }
     cudaSetDevice(device_);
-    if (!rc)
-        rc = read_device_error(req->batch->dl, d2h_);
+    if (!rc) {
+        const int v = *(volatile int *)req->batch->res->err_host;
+        if (v & kErrTimeout)
+            rc = fail(BF_ETIMEDOUT, "a bounded device wait gave up (status 0x%x)", v);
+        else if (v)
+            rc = fail(BF_ECUDA, "device-side check failed (status 0x%x)", v);
+    }
     if (!rc && out) {
-        cudaError_t e = cudaMemcpyAsync(out, req->slot->out.p, req->out_bytes, cudaMemcpyDefault, d2h_);
-        if (e == cudaSuccess)
-            e = cudaStreamSynchronize(d2h_);
+        Slot &s = *req->slot;
+        cudaError_t e;
+        if (pointer_kind(out) != kPageable) {
+            e = cudaMemcpyAsync(out, s.out.p, req->out_bytes, cudaMemcpyDefault, d2h_);
+            if (e == cudaSuccess)
+                e = cudaStreamSynchronize(d2h_);
+        } else if (!s.pin_out.ensure(req->out_bytes)) {
+            e = cudaErrorMemoryAllocation;
+        } else {
+            e = cudaMemcpyAsync(s.pin_out.p, s.out.p, req->out_bytes, cudaMemcpyDeviceToHost, d2h_);
+            if (e == cudaSuccess)
+                e = cudaStreamSynchronize(d2h_);
+            if (e == cudaSuccess)
+                CopyPool::get().copy(out, s.pin_out.p, req->out_bytes);
+        }
         if (e != cudaSuccess)
             rc = cuda_fail(e, "copying the result");
     }
@@ -456,13 +666,13 @@ int Engine::times_of(bf_handle *h, uint64_t ticket, double *start_ms, double *en
             return BF_PENDING;
         b = req->batch;
     }
-    cudaError_t e = cudaEventQuery(b->done);
+    cudaError_t e = cudaEventQuery(b->res->done);
     if (e == cudaErrorNotReady)
         return BF_PENDING;
     float t0 = 0.f, t1 = 0.f;
-    e = cudaEventElapsedTime(&t0, epoch_, b->start);
+    e = cudaEventElapsedTime(&t0, epoch_, b->res->start);
     if (e == cudaSuccess)
-        e = cudaEventElapsedTime(&t1, epoch_, b->done);
+        e = cudaEventElapsedTime(&t1, epoch_, b->res->done);
     if (e != cudaSuccess)
         return cuda_fail(e, "cudaEventElapsedTime");
     *start_ms = t0;

@@ -47,6 +47,7 @@ struct DevMem {
     }
     ~DevMem() { release(); }
     int ensure(size_t n);  // grow to at least n bytes (contents not kept)
+    int reserve(size_t n); // as ensure, growing by half again at least (lists that vary in size)
     void release();
     int upload(const void *src, size_t n);  // synchronous host -> device
 };
