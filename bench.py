@@ -66,6 +66,27 @@ def dist_info():
     return ws, rank, local
 
 
+# DRAM bytes (read + write) of one beamform_kernel launch from an ncu capture
+# (profiles/beamform_kernel_cyst512_8frames.md: 8 frames per launch; the
+# traffic grows with the frames).  Valid only for the kernel source the
+# capture was taken on: any other source reports null.
+TRAFFIC_CAPTURE = {"sources_sha256": "8abbe526af21ce856498e6e949cf4bd6ed11a66712e1079727c57a5bdc6bd550",
+                   "frames": 8, "bytes": 4553216 + 0}
+
+
+def beamform_traffic(frames):
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_2311_00482_gb300", "csrc", "bf_kernels.cu")
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    if digest != TRAFFIC_CAPTURE["sources_sha256"]:
+        return None
+    return TRAFFIC_CAPTURE["bytes"] * frames / TRAFFIC_CAPTURE["frames"]
+
+
 def max_over_ranks(x, device):
     """Largest x over the ranks of the default process group (x itself alone)."""
     import torch
@@ -348,7 +369,8 @@ def run_ours(args):
                      "unit": "G active pixel*ch/s", "frac": achieved_pch / peak_pch,
                      "peak_basis": "%d SMs x 16 SFU/clk x %.0f MHz / 2 square roots per triple"
                                    % (sm_count, sm_max),
-                     "traffic": None},
+                     "traffic": beamform_traffic(B),
+                     "traffic_unit": "DRAM bytes per launch (ncu capture scaled by frames)"},
         "e2e": {"value": job_value(ws, units_step, e2e_steps, t_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": B * rfs[0].nbytes,
                 "d2h_bytes_per_step": B * nm * acq.nx * acq.nz * 4,

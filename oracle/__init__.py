@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline / reference leg are the only importers.  The product
 package never imports it, and it imports nothing from the product package.
 
-* ``beamform`` / ``delayed_samples`` wrap ``bf_oracle.c`` (double precision,
+* ``beamform`` / ``beamform_pdas`` / ``delayed_samples`` wrap ``bf_oracle.c`` (double precision,
   plain loops over pixels, angles and channels; see that file's header for
   the exact definition it follows, Eq. (1) and Sec. II-B of the paper).
 * ``envelope`` is the analytic-signal magnitude along depth computed with a
@@ -56,6 +56,9 @@ def _bind(lib):
     lib.oracle_delayed_samples.argtypes = [p, i32, i32, i32, p, p, i32, i32, d, d, d, d,
                                            i32, i32, d, d, d, p, p, p]
     lib.oracle_delayed_samples.restype = ctypes.c_int
+    lib.oracle_beamform_pdas.argtypes = [p, i32, i32, i32, p, p, i32, i32, d, d, d, d, d, d, d,
+                                         d, p, i64, p, i32]
+    lib.oracle_beamform_pdas.restype = ctypes.c_int
     lib.oracle_max_threads.restype = ctypes.c_int32
     return lib
 
@@ -140,6 +143,30 @@ def beamform(rf, x_elem, angles_rad, grid, fs, c, f_number, *, pixels=None, thre
     if rc != 0:
         raise ValueError("oracle_beamform rejected its arguments (rc=%d)" % rc)
     out["m"] = m
+    return out
+
+
+def beamform_pdas(rf, x_elem, angles_rad, grid, fs, c, f_number, p, *, pixels=None, threads=0):
+    """pDAS image (float64, Eq. (2)-(3)): per angle sign(yt) |yt|^p with
+    yt = sum over active channels of sign(v) |v|^(1/p), summed over angles.
+    Shapes as ``beamform``."""
+    rf = np.ascontiguousarray(rf, dtype=np.int16)
+    na, ne, ns = rf.shape
+    x_elem = np.ascontiguousarray(x_elem, dtype=np.float64)
+    th = np.ascontiguousarray(np.atleast_1d(angles_rad), dtype=np.float64)
+    assert x_elem.shape == (ne,) and th.shape == (na,)
+    nx, nz, x0, x1, z0, z1 = _grid(grid)
+    if pixels is None:
+        shape, pix, npix = (nx, nz), None, nx * nz
+    else:
+        pix = np.ascontiguousarray(pixels, dtype=np.int64)
+        shape, npix = pix.shape, pix.size
+    out = np.empty(shape, np.float64)
+    rc = _load().oracle_beamform_pdas(_ptr(rf), na, ne, ns, _ptr(x_elem), _ptr(th), nx, nz, x0,
+                                      x1, z0, z1, float(fs), float(c), float(f_number), float(p),
+                                      _ptr(pix), npix, _ptr(out), int(threads))
+    if rc != 0:
+        raise ValueError("oracle_beamform_pdas rejected its arguments (rc=%d)" % rc)
     return out
 
 

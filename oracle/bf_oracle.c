@@ -33,6 +33,12 @@
  *     DMAS = sum_theta y
  *     CF   = (DAS^2 / (M_tot * sum_theta Su2)) * DAS   (0 if the denominator is 0)
  *
+ *   pDAS (Eq. (2)-(3), Sec. II-B-2; oracle_beamform_pdas): per angle the
+ *   p-th root of every active delayed sample keeps its sign, the roots are
+ *   summed and the sum is raised to the p-th power, again keeping its sign:
+ *       yt = sum sign(v) |v|^(1/p),   y = sign(yt) |yt|^p,
+ *   compounded coherently over angles like DMAS: pDAS = sum_theta y.
+ *
  * The floating-point expressions above are evaluated exactly as written (no
  * contraction into fused multiply-adds: built with -ffp-contract=off), so
  * every discrete decision (aperture membership, record bounds) is the
@@ -191,6 +197,52 @@ int oracle_beamform(const int16_t *rf, int32_t na, int32_t ne, int32_t ns, const
     }
     free(st);
     free(ct);
+    return 0;
+}
+
+/* sign(v) |v|^e with sign(0) = 0. */
+static double signed_pow(double v, double e)
+{
+    if (v > 0.0)
+        return pow(v, e);
+    if (v < 0.0)
+        return -pow(-v, e);
+    return 0.0;
+}
+
+/* pDAS image (Eq. (2)-(3)) of a pixel list or the whole grid, p >= 1. */
+int oracle_beamform_pdas(const int16_t *rf, int32_t na, int32_t ne, int32_t ns,
+                         const double *x_elem, const double *theta, int32_t nx, int32_t nz,
+                         double x0, double x1, double z0, double z1, double fs, double c,
+                         double fnum, double p, const int64_t *pix, int64_t npix, double *out,
+                         int32_t threads)
+{
+    if (na <= 0 || ne <= 0 || ns < 2 || nx <= 0 || nz <= 0 || fnum <= 0.0 || !(p >= 1.0))
+        return -1;
+    double kappa = fs / c;
+    int64_t total = pix ? npix : (int64_t)nx * nz;
+    int nt = threads > 0 ? threads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nt)
+    for (int64_t q = 0; q < total; ++q) {
+        int64_t lin = pix ? pix[q] : q;
+        int32_t ix = (int32_t)(lin / nz), iz = (int32_t)(lin % nz);
+        double xp = grid_coord(x0, x1, nx, ix);
+        double zp = grid_coord(z0, z1, nz, iz);
+        double y = 0.0;
+        for (int32_t a = 0; a < na; ++a) {
+            double st = sin(theta[a]), ct = cos(theta[a]);
+            double yt = 0.0;
+            for (int32_t i = 0; i < ne; ++i) {
+                const int16_t *u = rf + ((size_t)a * ne + i) * (size_t)ns;
+                double v;
+                int rec;
+                if (channel_sample(u, ns, xp, zp, x_elem[i], st, ct, kappa, fnum, &v, &rec))
+                    yt += signed_pow(v, 1.0 / p);
+            }
+            y += signed_pow(yt, p);
+        }
+        out[q] = y;
+    }
     return 0;
 }
 

@@ -36,6 +36,10 @@ MUTANTS = [
     ("channel record index", "((size_t)a * ne + i) * (size_t)ns", "((size_t)a * ne) * (size_t)ns"),
     ("grid spacing", "(hi - lo) / (double)(n - 1)", "(hi - lo) / (double)n"),
     ("compounding keeps last angle", "s1_tot += s1;", "s1_tot = s1;"),
+    ("pDAS power instead of root", "yt += signed_pow(v, 1.0 / p);", "yt += signed_pow(v, p);"),
+    ("pDAS power dropped", "y += signed_pow(yt, p);", "y += yt;"),
+    ("pDAS root loses the sign", "return -pow(-v, e);", "return pow(-v, e);"),
+    ("pDAS keeps the last angle", "y += signed_pow(yt, p);", "y = signed_pow(yt, p);"),
 ]
 
 
@@ -49,6 +53,9 @@ def _pins_pass(golden_dir):
         pins.test_dmas_identity_against_pairwise_brute_force,
         pins.test_das_is_linear_and_cf_bounded,
         lambda: pins.test_point_scatterer_images_within_quarter_wavelength(10.0, "das"),
+        lambda: pins.test_pdas_constant_record_closed_form(golden_dir),
+        pins.test_pdas_p1_is_das_and_single_channel_is_the_sample,
+        pins.test_pdas_homogeneous_odd_and_brute_force,
     ]
     for check in checks:
         try:

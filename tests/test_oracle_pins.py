@@ -280,3 +280,73 @@ def test_point_scatterer_images_within_quarter_wavelength(deg, mode):
     X, Z = oracle.grid_coords(grid)
     err = math.hypot(X[ix] - xs, Z[iz] - zs)
     assert err <= lam / 4, (mode, deg, err)
+
+
+# ------------------------------------------------------------------ pDAS --
+
+def test_pdas_constant_record_closed_form(golden_dir):
+    """u = c everywhere, M channels in range: yt = M c^(1/p), pDAS = M^p c per
+    angle (Eq. (2)-(3)); the sign of c is kept; angles add."""
+    spec = _load(golden_dir, "aperture_counts.json")
+    n = spec["n_elements"]
+    xe = (np.arange(n) - 0.5 * (n - 1)) * spec["pitch_m"]
+    rb = spec["record_bound"]
+    x, z = rb["pixel_m"]
+    m_in = rb["count"]
+    rf = np.full((1, n, rb["n_samples"]), 1000, np.int16)
+    grid = _single_pixel_grid(x, z)
+    for p in (1.0, 2.0, 3.0, 1.7):
+        y = oracle.beamform_pdas(rf, xe, [0.0], grid, rb["fs_hz"], rb["c_mps"], spec["f_number"], p)
+        assert y[0, 0] == pytest.approx(m_in ** p * 1000.0, rel=1e-12), p
+    m_ap = spec["cases"][0]["count"]
+    rf = np.full((3, n, 4096), -7, np.int16)
+    th = np.deg2rad([-5.0, 0.0, 5.0])
+    y = oracle.beamform_pdas(rf, xe, th, grid, 20e6, 1540.0, 1.5, 2.0)
+    assert y[0, 0] == pytest.approx(-7.0 * 3 * m_ap ** 2, rel=1e-12)
+
+
+def _speckle_case():
+    acq = synth.SPECKLE_POINTS_128.with_(nx=9, nz=7, n_elements=16, n_samples=1024,
+                                         angles_deg=(-5.0, 3.0))
+    rf, _ = synth.speckle_points_frame(acq)
+    grid = (acq.nx, acq.nz, acq.x0_m, acq.x1_m, acq.z0_m, acq.z1_m)
+    return acq, rf, grid
+
+
+def test_pdas_p1_is_das_and_single_channel_is_the_sample():
+    """p = 1: no compression, pDAS = DAS.  One receive element: the root and
+    the power cancel for every p, pDAS = DAS = the delayed sample."""
+    acq, rf, grid = _speckle_case()
+    xe = acq.x_elements()
+    ref = oracle.beamform(rf, xe, acq.angles_rad, grid, acq.fs_hz, acq.c_mps, acq.f_number)
+    y1 = oracle.beamform_pdas(rf, xe, acq.angles_rad, grid, acq.fs_hz, acq.c_mps, acq.f_number, 1.0)
+    np.testing.assert_allclose(y1, ref["das"], rtol=1e-12, atol=1e-9)
+    one = rf[:, 5:6, :]
+    ref1 = oracle.beamform(one, xe[5:6], acq.angles_rad, grid, acq.fs_hz, acq.c_mps, 0.1)
+    for p in (2.0, 3.0, 4.5):
+        y = oracle.beamform_pdas(one, xe[5:6], acq.angles_rad, grid, acq.fs_hz, acq.c_mps, 0.1, p)
+        np.testing.assert_allclose(y, ref1["das"], rtol=1e-10, atol=1e-9)
+
+
+def test_pdas_homogeneous_odd_and_brute_force():
+    """pDAS(2 u) = 2 pDAS(u) (degree-1 homogeneous: (2^(1/p))^p = 2),
+    pDAS(-u) = -pDAS(u), and a per-channel numpy evaluation of Eq. (2)-(3)
+    from the delayed samples agrees."""
+    acq, rf, grid = _speckle_case()
+    rf = (rf // 4).astype(np.int16)
+    xe = acq.x_elements()
+    args = (xe, acq.angles_rad, grid, acq.fs_hz, acq.c_mps, acq.f_number)
+    for p in (2.0, 3.0):
+        y = oracle.beamform_pdas(rf, *args, p)
+        y2 = oracle.beamform_pdas((2 * rf).astype(np.int16), *args, p)
+        yn = oracle.beamform_pdas((-rf).astype(np.int16), *args, p)
+        np.testing.assert_allclose(y2, 2 * y, rtol=1e-9, atol=1e-6 * np.max(np.abs(y)))
+        np.testing.assert_allclose(yn, -y, rtol=1e-12, atol=0)
+        for ix, iz in ((0, 0), (4, 3), (8, 6), (2, 5)):
+            v, act, _ = oracle.delayed_samples(rf, xe, acq.angles_rad, grid, ix, iz, acq.fs_hz,
+                                               acq.c_mps, acq.f_number)
+            expect = 0.0
+            for a in range(v.shape[0]):
+                s = np.sum(np.sign(v[a][act[a]]) * np.abs(v[a][act[a]]) ** (1.0 / p))
+                expect += np.sign(s) * abs(s) ** p
+            assert y[ix, iz] == pytest.approx(expect, rel=1e-10, abs=1e-9)
