@@ -23,6 +23,7 @@
  *   DMAS = sum_theta ((sum s)^2 - sum s^2) / 2,  s = sign(v) sqrt|v|
  *   CF   = (DAS^2 / (M * sum_theta sum_active v^2)) * DAS, M = active (angle, channel) pairs;
  *          0 when the denominator is 0
+ *   pDAS = sum_theta sign(t) |t|^p,  t = sum_active sign(v) |v|^(1/p)   (Eq. (2)-(3); p per handle)
  * The two discrete decisions (aperture membership and 0 <= k <= Ns - 2) are
  * taken on the host in double precision with exactly the expressions above,
  * evaluated left to right without fused multiply-adds; the per-pixel
@@ -71,7 +72,7 @@ typedef struct bf_handle bf_handle;
 typedef struct bf_batch bf_batch;
 
 /* mode_and_flags: combiner bits (any non-empty subset) ... */
-enum { BF_DAS = 1, BF_DMAS = 2, BF_CF = 4, BF_MODE_MASK = 7 };
+enum { BF_DAS = 1, BF_DMAS = 2, BF_CF = 4, BF_PDAS = 8, BF_MODE_MASK = 15 };
 /* ... RF storage precision on the device (bits 4-5; interpolation and sums are always FP32) ... */
 enum { BF_PREC_FP32 = 0, BF_PREC_FP16 = 1 << 4, BF_PREC_BF16 = 2 << 4, BF_PREC_MASK = 3 << 4 };
 /* ... and the output stage (bits 8-9). */
@@ -104,6 +105,14 @@ BF_API int bf_destroy(bf_handle *h);
  * library's own non-blocking stream). */
 BF_API int bf_set_stream(bf_handle *h, void *cuda_stream);
 
+/* Paper: Eq. (2)-(3), Sec. II-B-2.
+ * Order p of the pDAS combiner of this handle: each delayed sample is
+ * compressed to sign(v) |v|^(1/p) before the channel sum, and the sum is
+ * raised back to sign(t) |t|^p per angle.  1 <= p <= 16 (BF_EINVAL
+ * otherwise); default 2.  Applies to work enqueued or submitted after the
+ * call (a prepared batch keeps the value it was created with). */
+BF_API int bf_set_pdas_order(bf_handle *h, double p);
+
 /* Bytes of one output for the given mode_and_flags: popcount(modes) * nx * nz * 4. */
 BF_API size_t bf_output_bytes(const bf_handle *h, uint32_t mode_and_flags);
 
@@ -113,7 +122,9 @@ BF_API size_t bf_output_bytes(const bf_handle *h, uint32_t mode_and_flags);
  * rf_dev: device int16 [n_angles][n_elements][n_samples] (read during the call's
  * stream work), angles_rad: host array of n_angles plane-wave angles in
  * (-pi/2, pi/2); out_dev: device float [popcount(modes)][nx][nz] (modes in bit
- * order DAS, DMAS, CF; z fastest) receiving the stage selected by BF_OUT_*.
+ * order DAS, DMAS, CF, pDAS; z fastest) receiving the stage selected by BF_OUT_*.
+ * The envelope of the DMAS image goes through the [f0, 3 f0] band-pass; the
+ * other images are used as they are.
  * Returns after enqueueing; the caller synchronises the stream.  Calls on one
  * handle share its scratch memory and must be ordered on its stream. */
 BF_API int bf_beamform(bf_handle *h, const int16_t *rf_dev, int32_t n_samples,
@@ -229,6 +240,23 @@ BF_API int bf_host_tables(const bf_geometry *geometry, const bf_grid *grid, doub
 BF_API int bf_plan_info(bf_handle *h, int32_t n_samples, const double *angles_rad,
                         int32_t n_angles, uint32_t mode_and_flags, int32_t *info8, int32_t *wtab,
                         size_t wtab_entries);
+
+/* Paper: no counterpart (tile shape of this implementation).
+ * Autotuner: times the beamforming launches of `frames` (1-256) frames of
+ * this workload (grid of the handle, n_samples, angles, the combiner and
+ * precision bits of mode_and_flags; the output stage is ignored) under each
+ * tile configuration the library knows (rows per thread x channels per
+ * pipeline stage), on synthetic zero records, and keeps the fastest: later
+ * bf_beamform, bf_submit and bf_batch_create work on this workload uses it.
+ * Synchronous; allocates scratch for the frames while it runs.  Optional
+ * outputs: the chosen rows per thread and stage bytes, and the median
+ * beamforming time in microseconds of every candidate (n_candidates
+ * entries; -1 where a configuration does not fit).  The environment variable
+ * BF_TILE_ROWS=4 or 8 overrides any tuned choice. */
+BF_API int bf_autotune(bf_handle *h, int32_t n_samples, const double *angles_rad,
+                       int32_t n_angles, uint32_t mode_and_flags, int32_t frames,
+                       int32_t *rows_out, int32_t *stage_bytes_out, float *candidate_us,
+                       int32_t n_candidates);
 
 /* Allocation-free envelope + log compression, for callers that cannot
  * allocate device memory while running (a real-time acquisition loop that

@@ -20,7 +20,7 @@ import numpy as np
 
 from . import build as _build
 
-BF_DAS, BF_DMAS, BF_CF, BF_MODE_MASK = 1, 2, 4, 7
+BF_DAS, BF_DMAS, BF_CF, BF_PDAS, BF_MODE_MASK = 1, 2, 4, 8, 15
 BF_PREC_FP32, BF_PREC_FP16, BF_PREC_BF16, BF_PREC_MASK = 0, 1 << 4, 2 << 4, 3 << 4
 BF_OUT_RF, BF_OUT_ENV, BF_OUT_LOGDB, BF_OUT_MASK = 0, 1 << 8, 2 << 8, 3 << 8
 BF_OK, BF_PENDING = 0, 1
@@ -29,13 +29,15 @@ BF_EINVAL, BF_EAGAIN, BF_ENOMEM, BF_ECUDA, BF_ETIMEDOUT, BF_ENOTFOUND, BF_ENOSYS
 _NAMES = {-1: "BF_EINVAL", -2: "BF_EAGAIN", -3: "BF_ENOMEM", -4: "BF_ECUDA", -5: "BF_ETIMEDOUT",
           -6: "BF_ENOTFOUND", -7: "BF_ENOSYS"}
 
-EXPORTED = ("bf_create", "bf_destroy", "bf_set_stream", "bf_output_bytes", "bf_beamform",
+EXPORTED = ("bf_create", "bf_destroy", "bf_set_stream", "bf_set_pdas_order", "bf_output_bytes",
+            "bf_beamform",
             "bf_beamform_plain",
             "bf_submit", "bf_poll", "bf_ticket_batch", "bf_ticket_times", "bf_engine_pause",
             "bf_engine_configure", "bf_sync",
             "bf_batch_create", "bf_batch_launch", "bf_batch_status", "bf_batch_timing",
             "bf_batch_destroy",
-            "bf_host_tables", "bf_plan_info", "bf_logdb_static", "bf_last_error", "bf_version")
+            "bf_host_tables", "bf_plan_info", "bf_autotune", "bf_logdb_static", "bf_last_error",
+            "bf_version")
 
 
 class BFError(RuntimeError):
@@ -83,6 +85,7 @@ def load(path: str | None = None):
                        ctypes.c_double, ctypes.c_double, ctypes.POINTER(vp)], ctypes.c_int),
         "bf_destroy": ([vp], ctypes.c_int),
         "bf_set_stream": ([vp, vp], ctypes.c_int),
+        "bf_set_pdas_order": ([vp, ctypes.c_double], ctypes.c_int),
         "bf_output_bytes": ([vp, u32], ctypes.c_size_t),
         "bf_beamform": ([vp, vp, i32, dp, i32, u32, vp], ctypes.c_int),
         "bf_beamform_plain": ([vp, vp, i32, dp, i32, u32, vp], ctypes.c_int),
@@ -102,6 +105,8 @@ def load(path: str | None = None):
         "bf_host_tables": ([ctypes.POINTER(bf_geometry), ctypes.POINTER(bf_grid), ctypes.c_double,
                             ctypes.c_double, ctypes.c_double, i32, dp, i32, vp, vp], ctypes.c_int),
         "bf_plan_info": ([vp, i32, dp, i32, u32, vp, vp, ctypes.c_size_t], ctypes.c_int),
+        "bf_autotune": ([vp, i32, dp, i32, u32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                         ctypes.POINTER(ctypes.c_float), i32], ctypes.c_int),
         "bf_logdb_static": ([vp, i32, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                              ctypes.c_double, i32, vp, vp], ctypes.c_int),
         "bf_last_error": ([], ctypes.c_char_p),
@@ -189,6 +194,11 @@ def bf_set_stream(h, stream=None):
     return _check(load().bf_set_stream(h, s))
 
 
+def bf_set_pdas_order(h, p):
+    """Order p of the handle's pDAS combiner (Eq. (2)-(3)), 1 <= p <= 16."""
+    return _check(load().bf_set_pdas_order(h, float(p)))
+
+
 def bf_output_bytes(h, flags) -> int:
     return int(load().bf_output_bytes(h, int(flags)))
 
@@ -218,6 +228,18 @@ def bf_plan_info(h, n_samples, angles_rad, flags, with_windows=False):
                                    w.ctypes.data, w.size))
         d["windows"] = w.reshape(len(a), d["tiles_x"] * d["tiles_z"], -1)
     return d
+
+
+def bf_autotune(h, n_samples, angles_rad, flags, frames=8):
+    """Pick the fastest tile configuration for this workload (kept by the handle).
+    Returns {"rows", "stage_bytes", "candidates_us"}."""
+    a, ap = _angles(angles_rad)
+    rows, stage = ctypes.c_int32(), ctypes.c_int32()
+    cand = (ctypes.c_float * 8)()
+    _check(load().bf_autotune(h, int(n_samples), ap, len(a), int(flags), int(frames),
+                              ctypes.byref(rows), ctypes.byref(stage), cand, 8))
+    return {"rows": rows.value, "stage_bytes": stage.value,
+            "candidates_us": [round(float(c), 2) for c in cand if c != 0.0]}
 
 
 def bf_logdb_static(y_dev, nx, nz, z0_m, z1_m, f0_hz, c_mps, bandpass, db_dev, stream=None):

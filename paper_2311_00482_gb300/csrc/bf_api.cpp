@@ -171,32 +171,35 @@ static int env_tables(int nz, std::shared_ptr<EnvTablesDev> &out)
 
 // ------------------------------------------------------------------ plans --
 
-// Rows per thread of the beamforming tile: 4 (32-row tiles, three CTAs per SM)
-// measured faster than 8 (one CTA per SM at ~150 registers) on every grid
-// tried; BF_TILE_ROWS=8 overrides.
-static int choose_rows(const GeomHost &g)
+// Tile configuration of a workload: what bf_autotune measured fastest for it,
+// else entry 0 (4 rows per thread, 32-row tiles, three CTAs per SM, measured
+// faster than 8 rows on every grid tried); BF_TILE_ROWS=8 forces entry 3.
+static int choose_cfg(const bf_handle *h, const PlanKey &key)
 {
     if (const char *e = std::getenv("BF_TILE_ROWS")) {
-        const int r = std::atoi(e);
-        if (r == 4 || r == 8)
-            return r;
+        if (std::atoi(e) == 8)
+            return 3;
+        if (std::atoi(e) == 4)
+            return 0;
     }
-    (void)g;
-    return 4;
+    auto it = h->tuned.find(key);
+    return it == h->tuned.end() ? 0 : it->second;
 }
 
-int handle_plan(bf_handle *h, int ns, const double *angles, int na, int prec, Plan **out)
+int handle_plan(bf_handle *h, int ns, const double *angles, int na, int prec, Plan **out, int cfg)
 {
-    PlanKey key{ns, prec, std::vector<double>(angles, angles + na)};
+    PlanKey key{ns, prec, std::vector<double>(angles, angles + na), 0};
     std::lock_guard<std::mutex> lk(h->mu);
+    key.cfg = (cfg >= 0 && cfg < kNumTileConfigs) ? cfg : choose_cfg(h, key);
     auto it = h->plans.find(key);
     if (it != h->plans.end()) {
         *out = it->second.get();
         return BF_OK;
     }
     PlanHost ph;
-    angle_tables(h->g, h->geo, ns, key.angles, prec, choose_rows(h->g), ph);
-    if ((size_t)ph.wmax * pair_bytes(prec) > (size_t)kStageBytes * 4)
+    const TileConfig tc = kTileConfigs[key.cfg];
+    angle_tables(h->g, h->geo, ns, key.angles, prec, tc.rows, tc.stage_bytes, ph);
+    if (beamform_smem_bytes(ph.wmax, ph.group, prec) > (size_t)kMaxSmemPerCta)
         return fail(BF_EINVAL,
                     "pixel spacing too coarse for the sample rate: one tile needs %d samples per channel",
                     ph.wmax);
@@ -278,7 +281,7 @@ int handle_plan(bf_handle *h, int ns, const double *angles, int na, int prec, Pl
 
 // ------------------------------------------------------- frame preparation --
 
-static int popcount3(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1); }
+static int popcount4(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1) + ((m >> 3) & 1); }
 
 int check_frame_args(bf_handle *h, int ns, const double *angles, int na, uint32_t flags)
 {
@@ -295,7 +298,7 @@ int check_frame_args(bf_handle *h, int ns, const double *angles, int na, uint32_
             return fail(BF_EINVAL, "angle %d (%g rad) outside (-pi/2, pi/2)", a, angles[a]);
     const int modes = flags & BF_MODE_MASK;
     if (!modes)
-        return fail(BF_EINVAL, "no combiner selected (BF_DAS / BF_DMAS / BF_CF)");
+        return fail(BF_EINVAL, "no combiner selected (BF_DAS / BF_DMAS / BF_CF / BF_PDAS)");
     if (flags & ~(uint32_t)(BF_MODE_MASK | BF_PREC_MASK | BF_OUT_MASK))
         return fail(BF_EINVAL, "unknown bits in mode_and_flags 0x%x", flags);
     const int prec = (flags & BF_PREC_MASK) >> 4;
@@ -313,21 +316,21 @@ int check_frame_args(bf_handle *h, int ns, const double *angles, int na, uint32_
 
 size_t frame_out_bytes(const bf_handle *h, uint32_t flags)
 {
-    return (size_t)popcount3(flags & BF_MODE_MASK) * (size_t)h->g.nx * (size_t)h->g.nz * sizeof(float);
+    return (size_t)popcount4(flags & BF_MODE_MASK) * (size_t)h->g.nx * (size_t)h->g.nz * sizeof(float);
 }
 
 int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *angles, int na,
-                  uint32_t flags, float *out_dev, FrameScratch &s, FramePrep &fp)
+                  uint32_t flags, float *out_dev, FrameScratch &s, FramePrep &fp, int cfg)
 {
     int rc = check_frame_args(h, ns, angles, na, flags);
     if (rc)
         return rc;
     const int prec = (flags & BF_PREC_MASK) >> 4;
     Plan *plan = nullptr;
-    rc = handle_plan(h, ns, angles, na, prec, &plan);
+    rc = handle_plan(h, ns, angles, na, prec, &plan, cfg);
     if (rc)
         return rc;
-    const int modes = flags & BF_MODE_MASK, nm = popcount3(modes), stage = flags & BF_OUT_MASK;
+    const int modes = flags & BF_MODE_MASK, nm = popcount4(modes), stage = flags & BF_OUT_MASK;
     const size_t img = (size_t)h->g.nx * h->g.nz;
     const int rows = na * h->g.ne;
     rc = s.pairs.ensure((size_t)rows * plan->nsp * pair_bytes(prec));
@@ -348,6 +351,7 @@ int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *ang
     fp.ns = ns;
     fp.na = na;
     fp.modes = modes;
+    fp.pdas_p = h->pdas_p;
     fp.stage = stage;
     fp.prec = prec;
     fp.out = out_dev;
@@ -412,15 +416,17 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
         j.tiles_x = p->tiles_x;
         j.tiles_z = p->tiles_z;
         j.out_scale = f.prec == kPrecF32 ? 1.0f : 32768.0f;
-        const int variant = (p->rows * 4 + f.prec) * 8 + (f.modes & (BF_DMAS | BF_CF));
+        j.pdas_p = (float)f.pdas_p;
+        j.pdas_inv_p = (float)(1.0 / f.pdas_p);
+        const int variant = (p->rows * 4 + f.prec) * 16 + (f.modes & (BF_DMAS | BF_CF | BF_PDAS));
         groups[variant].push_back(j);
         hl.smem = std::max(hl.smem, beamform_smem_bytes(p->wmax, p->group, f.prec));
     }
     for (auto &kv : groups) {
         HostLaunch::Group g;
-        g.rows = kv.first / 32;
-        g.prec = (kv.first / 8) % 4;
-        g.variant = kv.first % 8;
+        g.rows = kv.first / 64;
+        g.prec = (kv.first / 16) % 4;
+        g.variant = kv.first % 16;
         g.first = (int)hl.jobs.size();
         g.count = (int)kv.second.size();
         g.prefix_first = (int)hl.tile_prefix.size();
@@ -459,7 +465,7 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
         const bf_handle *h = f.h;
         const size_t img = (size_t)h->g.nx * h->g.nz;
         int slot = 0;
-        for (int bit = 1; bit <= BF_CF; bit <<= 1) {
+        for (int bit = 1; bit <= BF_PDAS; bit <<= 1) {
             if (!(f.modes & bit))
                 continue;
             EnvJob e{};
@@ -721,6 +727,16 @@ BF_API int bf_set_stream(bf_handle *h, void *stream)
     return BF_OK;
 }
 
+BF_API int bf_set_pdas_order(bf_handle *h, double p)
+{
+    if (!h)
+        return fail(BF_EINVAL, "null handle");
+    if (!(p >= 1.0 && p <= 16.0))
+        return fail(BF_EINVAL, "pDAS order must be in [1, 16], got %g", p);
+    h->pdas_p = p;
+    return BF_OK;
+}
+
 BF_API size_t bf_output_bytes(const bf_handle *h, uint32_t flags)
 {
     return h ? frame_out_bytes(h, flags) : 0;
@@ -853,7 +869,7 @@ BF_API int bf_host_tables(const bf_geometry *geom, const bf_grid *grid, double f
     geometry_tables(g, geo);
     PlanHost ph;
     angle_tables(g, geo, n_samples, std::vector<double>(angles_rad, angles_rad + n_angles),
-                 kPrecF32, 8, ph);
+                 kPrecF32, 8, kTileConfigs[0].stage_bytes, ph);
     const int nxp = pad_cols(g.nx);
     if (valid_rows)  // [na][ne][nxp][2] -> [na][nx][ne][2]
         for (int a = 0; a < n_angles; ++a)
@@ -894,6 +910,104 @@ BF_API int bf_plan_info(bf_handle *h, int32_t n_samples, const double *angles_ra
         if (e != cudaSuccess)
             return cuda_fail(e, "cudaMemcpy (window table)");
     }
+    return BF_OK;
+}
+
+// Autotuner: times the beamforming launches of `frames` copies of this
+// workload under every tile configuration (synthetic zero records: the work
+// does not depend on the data) and keeps the fastest for the handle's later
+// work on it.
+BF_API int bf_autotune(bf_handle *h, int32_t n_samples, const double *angles_rad,
+                       int32_t n_angles, uint32_t flags, int32_t frames, int32_t *rows_out,
+                       int32_t *stage_bytes_out, float *candidate_us, int32_t n_candidates)
+{
+    int rc = check_frame_args(h, n_samples, angles_rad, n_angles, flags);
+    if (rc)
+        return rc;
+    if (frames < 1 || frames > 256)
+        return fail(BF_EINVAL, "frames must be in [1, 256], got %d", frames);
+    cudaSetDevice(h->device);
+    const uint32_t fl = flags & ~(uint32_t)BF_OUT_MASK;  // beamformed output only
+    const size_t rf_bytes = (size_t)n_angles * h->g.ne * n_samples * sizeof(int16_t);
+    const size_t out_bytes = frame_out_bytes(h, fl);
+    DevMem rf, out;
+    rc = rf.ensure(rf_bytes);
+    if (!rc)
+        rc = out.ensure(out_bytes * frames);
+    if (rc)
+        return rc;
+    cudaStream_t st;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaStreamCreate");
+    cudaEvent_t marks[4] = {};
+    for (auto &m : marks)
+        if (e == cudaSuccess)
+            e = cudaEventCreate(&m);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(rf.p, 0, rf_bytes, st);
+    std::vector<FrameScratch> scratch(frames);
+    std::vector<float> best_us(kNumTileConfigs, -1.f);
+    int best = -1;
+    for (int c = 0; c < kNumTileConfigs && e == cudaSuccess && !rc; ++c) {
+        std::vector<FramePrep> fr(frames);
+        int prc = BF_OK;
+        for (int i = 0; i < frames && !prc; ++i)
+            prc = prepare_frame(h, (const int16_t *)rf.p, n_samples, angles_rad, n_angles, fl,
+                                (float *)out.p + (size_t)i * (out_bytes / sizeof(float)),
+                                scratch[i], fr[i], c);
+        if (prc)
+            continue;  // this configuration does not fit the workload
+        HostLaunch hl;
+        build_launch(fr, hl);
+        DeviceLaunch dl;
+        rc = upload_maps(fr, st, false);
+        if (!rc)
+            rc = dl.upload(hl, st, false);
+        if (!rc && cudaMemsetAsync(dl.err.p, 0, sizeof(int), st) != cudaSuccess)
+            rc = fail(BF_ECUDA, "cudaMemsetAsync");
+        std::vector<float> t;
+        for (int rep = 0; rep < 4 && !rc; ++rep) {  // one warm-up, three timed
+            rc = enqueue(fr, hl, dl, st, marks);
+            if (!rc && cudaStreamSynchronize(st) != cudaSuccess)
+                rc = fail(BF_ECUDA, "autotune replay");
+            float ms = 0.f;
+            if (!rc && cudaEventElapsedTime(&ms, marks[1], marks[2]) == cudaSuccess && rep > 0)
+                t.push_back(ms * 1e3f);
+        }
+        if (!rc)
+            rc = read_device_error(dl, st);
+        if (rc || t.empty())
+            break;
+        std::sort(t.begin(), t.end());
+        best_us[c] = t[t.size() / 2];
+        if (best < 0 || best_us[c] < best_us[best])
+            best = c;
+    }
+    for (auto &m : marks)
+        if (m)
+            cudaEventDestroy(m);
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (rc)
+        return rc;
+    if (e != cudaSuccess)
+        return cuda_fail(e, "autotune setup");
+    if (best < 0)
+        return fail(BF_EINVAL, "no tile configuration fits this workload");
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        PlanKey key{n_samples, (int)((flags & BF_PREC_MASK) >> 4),
+                    std::vector<double>(angles_rad, angles_rad + n_angles), 0};
+        h->tuned[key] = best;
+    }
+    if (rows_out)
+        *rows_out = kTileConfigs[best].rows;
+    if (stage_bytes_out)
+        *stage_bytes_out = kTileConfigs[best].stage_bytes;
+    if (candidate_us)
+        for (int c = 0; c < std::min<int>(n_candidates, kNumTileConfigs); ++c)
+            candidate_us[c] = best_us[c];
     return BF_OK;
 }
 

@@ -55,12 +55,15 @@ struct DevMem {
 struct PlanKey {
     int ns, prec;
     std::vector<double> angles;
+    int cfg = 0;  // index into kTileConfigs
     bool operator<(const PlanKey &o) const
     {
         if (ns != o.ns)
             return ns < o.ns;
         if (prec != o.prec)
             return prec < o.prec;
+        if (cfg != o.cfg)
+            return cfg < o.cfg;
         return angles < o.angles;
     }
 };
@@ -96,6 +99,7 @@ struct FramePrep {
     std::shared_ptr<EnvTablesDev> et;
     const int16_t *rf = nullptr;
     int ns = 0, na = 0, modes = 0, stage = 0, prec = 0;
+    double pdas_p = 2.0;
     float *out = nullptr;
     void *pairs = nullptr;
     float *y = nullptr, *env = nullptr;
@@ -145,8 +149,10 @@ struct bf_handle {
     cudaStream_t stream = nullptr, own_stream = nullptr;
     bfi::DevMem rowZ, dx2, apcnt;
     int kb_lo = 1, kb_hi = 0;
+    double pdas_p = 2.0;  // order of the pDAS combiner
     std::mutex mu;  // plans, tickets, slot pool
     std::map<bfi::PlanKey, std::unique_ptr<bfi::Plan>> plans;
+    std::map<bfi::PlanKey, int> tuned;  // tile configuration bf_autotune chose (key cfg = 0)
     bfi::FrameScratch scratch;     // bf_beamform
     bfi::DeviceLaunch launch;      // bf_beamform
     bool err_cleared = false;
@@ -166,11 +172,13 @@ struct bf_batch {
 
 namespace bfi {
 
-int handle_plan(bf_handle *h, int ns, const double *angles, int na, int prec, Plan **out);
+// cfg < 0: the configuration bf_autotune chose for this workload, else the default
+int handle_plan(bf_handle *h, int ns, const double *angles, int na, int prec, Plan **out,
+                int cfg = -1);
 int check_frame_args(bf_handle *h, int ns, const double *angles, int na, uint32_t flags);
 size_t frame_out_bytes(const bf_handle *h, uint32_t flags);
 int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *angles, int na,
-                  uint32_t flags, float *out_dev, FrameScratch &s, FramePrep &fp);
+                  uint32_t flags, float *out_dev, FrameScratch &s, FramePrep &fp, int cfg = -1);
 void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl);
 int upload_maps(std::vector<FramePrep> &frames, cudaStream_t st, bool async);
 // marks (optional, 4 events): recorded before the ingest, before and after the

@@ -20,13 +20,22 @@ constexpr int kWarps = 8;
 constexpr int kThreads = 32 * kWarps;
 constexpr int kMaxGroup = 16;         // channels staged per pipeline stage (upper bound)
 constexpr int kStages = 3;            // pipeline stages in shared memory
-constexpr int kStageBytes = 24 << 10; // target bytes of one stage's RF windows
 constexpr int kMaxBox = 256;          // TMA box extent limit per dimension
+constexpr int kMaxSmemPerCta = 227 << 10;  // dynamic shared memory one CTA may use
 constexpr int kNoWindow = (int)0x80000000;  // window table: no sample of this channel counts
 // Columns of the per-(channel, column) tables are padded to a multiple of 4
 // so that every table row starts 16-byte aligned (a tensor-map requirement).
 inline int pad_cols(int nx) { return (nx + 3) / 4 * 4; }
 inline int tile_rows(int rows_per_thread) { return kWarps * rows_per_thread; }
+
+// Tile configurations the autotuner chooses from: rows per thread (tile
+// height 8 * rows) and the target bytes of one pipeline stage's sample
+// windows (channels per stage).  Entry 0 is the default.
+struct TileConfig {
+    int rows, stage_bytes;
+};
+constexpr TileConfig kTileConfigs[] = {{4, 24 << 10}, {4, 16 << 10}, {4, 32 << 10}, {8, 24 << 10}};
+constexpr int kNumTileConfigs = 4;
 
 enum Prec : int { kPrecF32 = 0, kPrecF16 = 1, kPrecBF16 = 2 };
 
@@ -54,9 +63,11 @@ struct BfJob {
     int box;              // TMA box width (pairs); wmax is a multiple of it
     int group;            // channels per stage
     int rows;             // rows per thread (tile height = kWarps * rows)
-    int modes;            // BF_DAS | BF_DMAS | BF_CF
+    int modes;            // BF_DAS | BF_DMAS | BF_CF | BF_PDAS
     int tiles_x, tiles_z;
     float out_scale;      // 1 (FP32 pairs) or 32768 (FP16 / BF16 data scaled by 2^-15)
+    float pdas_p;         // order p of the pDAS combiner
+    float pdas_inv_p;     // 1 / p
 };
 
 // Inputs of the per-plan window planner (one job per plan).
@@ -106,7 +117,8 @@ struct LogJob {
 
 // Kernel launchers (bf_kernels.cu).  All enqueue on `stream` and return the
 // launch status.  `variant` holds the BF_DMAS / BF_CF bits the launch computes
-// (all its jobs must share them, the precision and the rows per thread).
+// (all its jobs must share them, the precision and the rows per thread);
+// BF_PDAS adds the p-th-root combiner.
 cudaError_t launch_plan(const PlanJob &job, int *err_dev, cudaStream_t stream);
 cudaError_t launch_ingest(const IngestJob *jobs_dev, const int *row_prefix_dev, int njobs,
                           int total_rows, int prec, cudaStream_t stream);

@@ -14,7 +14,7 @@
 //                    window of every channel's record plus the tile's
 //                    per-(channel, column) tables; delays are formed in
 //                    registers, samples interpolated linearly and combined
-//                    (DAS, signed-sqrt DMAS, coherence factor), compounded over
+//                    (DAS, signed-sqrt DMAS, coherence factor, pDAS), compounded over
 //                    angles (Eq. (1), Sec. II-B)
 //   envelope_kernel  per image column the analytic signal along depth via a
 //                    shared-memory radix-2 Stockham FFT (Bluestein for other
@@ -124,6 +124,23 @@ __device__ __forceinline__ float sqrt_approx(float x)
     float y;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// x^e for x >= 0, e > 0 as 2^(e log2 x) on the special-function unit
+// (x = 0: log2 gives -inf, 2^-inf = 0).
+__device__ __forceinline__ float pow_approx(float x, float e)
+{
+    float l, y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(l * e));
+    return y;
+}
+
+// sign(v) |v|^(1/p) of one delayed sample; p = 2 takes the square root.
+__device__ __forceinline__ float pdas_root(float v, float inv_p, bool square)
+{
+    const float av = fabsf(v);
+    return copysignf(square ? sqrt_approx(av) : pow_approx(av, inv_p), v);
 }
 
 // Receive path length beyond the depth term, in samples:
@@ -306,6 +323,21 @@ struct PairIO<kPrecBF16> {
     }
 };
 
+// Loads through 32-bit shared-window addresses (the consumer loop's tables).
+__device__ __forceinline__ int2 lds_int2(uint32_t addr)
+{
+    int2 v;
+    asm volatile("ld.shared.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ float lds_f32(uint32_t addr)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+    return v;
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -320,11 +352,11 @@ __host__ __device__ __forceinline__ int stage_bytes(int group, int wmax, int pb)
 // Accumulate one channel into the ROWS pixels of this thread.  CHECK: test
 // every pixel's row against the channel's counted rows (otherwise the whole
 // row band of the warp counts it).
-template <int PREC, bool DMAS, bool CF, int ROWS, bool CHECK>
+template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS, bool CHECK>
 __device__ __forceinline__ void accumulate(uint32_t win, int wmax, int w0, float d2, int2 vr,
                                            int r_first, const float *Z, const float *fp,
                                            const int *Kc, float *S1, float *T1, float *T2,
-                                           float *Su2)
+                                           float *Su2, float *P1, float inv_p, bool square)
 {
     constexpr int PB = PairIO<PREC>::kBytes;
     const unsigned span = (unsigned)(vr.y - vr.x);
@@ -344,6 +376,8 @@ __device__ __forceinline__ void accumulate(uint32_t win, int wmax, int w0, float
             }
             if (CF)
                 Su2[j] = fmaf(v, v, Su2[j]);
+            if (PDAS)
+                P1[j] += pdas_root(v, inv_p, square);
         }
     }
 }
@@ -351,11 +385,12 @@ __device__ __forceinline__ void accumulate(uint32_t win, int wmax, int w0, float
 // Two channels that every pixel of the band counts, interleaved: twice the
 // independent dependency chains per thread (square roots, reciprocal, shared
 // load) for the scheduler to overlap.
-template <int PREC, bool DMAS, bool CF, int ROWS>
+template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS>
 __device__ __forceinline__ void accumulate2(uint32_t win0, int w00, float d20, uint32_t win1,
                                             int w01, float d21, int wmax, const float *Z,
                                             const float *fp, const int *Kc, float *S1, float *T1,
-                                            float *T2, float *Su2)
+                                            float *T2, float *Su2, float *P1, float inv_p,
+                                            bool square)
 {
     constexpr int PB = PairIO<PREC>::kBytes;
 #pragma unroll
@@ -376,10 +411,12 @@ __device__ __forceinline__ void accumulate2(uint32_t win0, int w00, float d20, u
         }
         if (CF)
             Su2[j] = fmaf(v0, v0, fmaf(v1, v1, Su2[j]));
+        if (PDAS)
+            P1[j] += pdas_root(v0, inv_p, square) + pdas_root(v1, inv_p, square);
     }
 }
 
-template <int PREC, bool DMAS, bool CF, int ROWS>
+template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS>
 __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_kernel(const BfJob *__restrict__ jobs,
                                                                     const int *__restrict__ tile_prefix,
                                                                     int njobs, int *__restrict__ err)
@@ -478,14 +515,16 @@ __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_ker
 
     int Kc[ROWS];
     float Z[ROWS], fp[ROWS];
-    float S1[ROWS], T1[ROWS], T2[ROWS], Yd[ROWS], Su2[ROWS];
+    float S1[ROWS], T1[ROWS], T2[ROWS], Yd[ROWS], Su2[ROWS], P1[ROWS], Yp[ROWS];
 #pragma unroll
     for (int j = 0; j < ROWS; ++j) {
         Z[j] = __ldg(J->rowZ + min(r_first + j, nz - 1));
-        S1[j] = T1[j] = T2[j] = Yd[j] = Su2[j] = 0.f;
+        S1[j] = T1[j] = T2[j] = Yd[j] = Su2[j] = P1[j] = Yp[j] = 0.f;
         Kc[j] = 0;
         fp[j] = 0.f;
     }
+    const float pdas_p = J->pdas_p, inv_p = J->pdas_inv_p;
+    const bool square = pdas_p == 2.0f;  // uniform over the launch
 
     bool ok = true;
 #pragma unroll 1
@@ -500,42 +539,47 @@ __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_ker
                 const int izc = min(r_first + j, nz - 1);
                 Kc[j] = ck + __ldg(rowK + a * nz + izc) + kPadL - kRoundBits;
                 fp[j] = cf + __ldg(rowF + a * nz + izc) - 0.5f;
-                T1[j] = T2[j] = 0.f;
+                T1[j] = T2[j] = P1[j] = 0.f;
             }
         }
         ok = mbar_wait(&sh.full[st], (unsigned)(use & 1), deadline, err);
         if (!ok)
             break;
-        const unsigned char *base = stage_base(st);
-        const int2 *vrb = reinterpret_cast<const int2 *>(base);
-        const float *d2b = reinterpret_cast<const float *>(base + (size_t)G * kTileCols * 8);
-        const uint32_t wins = smem_u32(base) + (uint32_t)G * kTileCols * 12;
+        const uint32_t base = smem_u32(stage_base(st));
+        const uint32_t vrb = base + (uint32_t)lane * 8;                          // int2 [G][32]
+        const uint32_t d2b = base + (uint32_t)G * kTileCols * 8 + (uint32_t)lane * 4;  // float [G][32]
+        const uint32_t wins = base + (uint32_t)G * kTileCols * 12;
+        const uint32_t wfb = smem_u32(&sh.wf[st][0]);
         const int gs = min(G, ne - g * G);
 #pragma unroll 1
         for (int c = 0; c < gs; ++c) {
-            const int2 wf = sh.wf[st][c];
+            const int2 wf = lds_int2(wfb + (uint32_t)c * 8);
             const unsigned bands = (unsigned)wf.y >> warp;
             if (!(bands & 1u))
                 continue;  // no pixel of this warp's row band counts the channel
-            const float d2 = d2b[c * kTileCols + lane];
+            const float d2 = lds_f32(d2b + (uint32_t)c * (kTileCols * 4));
             const uint32_t win = wins + (uint32_t)(c * wmax * PB);
             if ((bands & 0x100u) && c + 1 < gs) {
-                const int2 wf1 = sh.wf[st][c + 1];
+                const int2 wf1 = lds_int2(wfb + (uint32_t)(c + 1) * 8);
                 if (((unsigned)wf1.y >> warp) & 0x100u) {  // two fully counted channels
-                    accumulate2<PREC, DMAS, CF, ROWS>(win, wf.x, d2, win + (uint32_t)(wmax * PB),
-                                                      wf1.x, d2b[(c + 1) * kTileCols + lane], wmax,
-                                                      Z, fp, Kc, S1, T1, T2, Su2);
+                    accumulate2<PREC, DMAS, CF, PDAS, ROWS>(
+                        win, wf.x, d2, win + (uint32_t)(wmax * PB), wf1.x,
+                        lds_f32(d2b + (uint32_t)(c + 1) * (kTileCols * 4)), wmax, Z, fp, Kc, S1,
+                        T1, T2, Su2, P1,
+                        inv_p, square);
                     ++c;
                     continue;
                 }
             }
             if (bands & 0x100u) {  // every pixel of the band counts it
-                accumulate<PREC, DMAS, CF, ROWS, false>(win, wmax, wf.x, d2, make_int2(0, 0),
-                                                        r_first, Z, fp, Kc, S1, T1, T2, Su2);
+                accumulate<PREC, DMAS, CF, PDAS, ROWS, false>(win, wmax, wf.x, d2,
+                                                              make_int2(0, 0), r_first, Z, fp, Kc,
+                                                              S1, T1, T2, Su2, P1, inv_p, square);
             } else {
-                const int2 vr = vrb[c * kTileCols + lane];  // (-1, -1): no row counts
-                accumulate<PREC, DMAS, CF, ROWS, true>(win, wmax, wf.x, d2, vr, r_first, Z, fp, Kc,
-                                                       S1, T1, T2, Su2);
+                const int2 vr = lds_int2(vrb + (uint32_t)c * (kTileCols * 8));  // (-1, -1): no row counts
+                accumulate<PREC, DMAS, CF, PDAS, ROWS, true>(win, wmax, wf.x, d2, vr, r_first, Z,
+                                                             fp, Kc, S1, T1, T2, Su2, P1, inv_p,
+                                                             square);
             }
         }
         __syncwarp();
@@ -545,6 +589,11 @@ __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_ker
 #pragma unroll
             for (int j = 0; j < ROWS; ++j)
                 Yd[j] = fmaf(0.5f * T1[j], T1[j], fmaf(-0.5f, T2[j], Yd[j]));
+        }
+        if (PDAS && g == ngroups - 1) {  // Eq. (3) per angle, then the coherent sum
+#pragma unroll
+            for (int j = 0; j < ROWS; ++j)
+                Yp[j] += copysignf(powf(fabsf(P1[j]), pdas_p), P1[j]);
         }
     }
 
@@ -570,6 +619,8 @@ __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_ker
             const float den = mtot * Su2[j];
             y[(size_t)(slot++) * plane + o] = den > 0.f ? (S1[j] * S1[j] / den) * S1[j] * scale : 0.f;
         }
+        if (modes & BF_PDAS)
+            y[(size_t)(slot++) * plane + o] = Yp[j] * scale;
     }
 }
 
@@ -589,11 +640,12 @@ __global__ void __launch_bounds__(256) plain_kernel(const BfJob J, const int16_t
         return;
     const int ix = (int)(p / J.nz), iz = (int)(p - (long long)ix * J.nz);
     const float Z = __ldg(J.rowZ + iz);
-    float S1 = 0.f, Yd = 0.f, Su2 = 0.f;
+    float S1 = 0.f, Yd = 0.f, Su2 = 0.f, Yp = 0.f;
+    const bool pdas = (J.modes & BF_PDAS) != 0;
     for (int a = 0; a < J.na; ++a) {
         const int K = __ldg(J.colK + a * J.nx + ix) + __ldg(J.rowK + a * J.nz + iz);
         const float f = __ldg(J.colF + a * J.nx + ix) + __ldg(J.rowF + a * J.nz + iz) - 0.5f;
-        float T1 = 0.f, T2 = 0.f;
+        float T1 = 0.f, T2 = 0.f, P1 = 0.f;
         for (int i = 0; i < J.ne; ++i) {
             const int2 vr = __ldg(valid + ((size_t)a * J.ne + i) * nxp + ix);
             if (iz < vr.x || iz > vr.y)
@@ -616,9 +668,13 @@ __global__ void __launch_bounds__(256) plain_kernel(const BfJob J, const int16_t
             }
             if (CF)
                 Su2 = fmaf(v, v, Su2);
+            if (pdas)
+                P1 += copysignf(powf(fabsf(v), J.pdas_inv_p), v);
         }
         if (DMAS)
             Yd = fmaf(0.5f * T1, T1, fmaf(-0.5f, T2, Yd));
+        if (pdas)
+            Yp += copysignf(powf(fabsf(P1), J.pdas_p), P1);
     }
     const size_t plane = (size_t)J.nx * J.nz, o = (size_t)ix * J.nz + iz;
     int slot = 0;
@@ -630,6 +686,8 @@ __global__ void __launch_bounds__(256) plain_kernel(const BfJob J, const int16_t
         const float den = (float)J.na * (float)__ldg(J.apcnt + o) * Su2;
         J.y[(size_t)(slot++) * plane + o] = den > 0.f ? (S1 * S1 / den) * S1 : 0.f;
     }
+    if (pdas)
+        J.y[(size_t)(slot++) * plane + o] = Yp;
 }
 
 // ------------------------------------------------------------- envelope --
@@ -828,11 +886,11 @@ __global__ void __launch_bounds__(256) log_kernel(const LogJob *__restrict__ job
     }
 }
 
-template <int PREC, bool DMAS, bool CF, int ROWS>
+template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS>
 cudaError_t launch_bf_t(const BfJob *jobs, const int *prefix, int njobs, int tiles, size_t smem,
                         int *err, cudaStream_t st)
 {
-    auto k = beamform_kernel<PREC, DMAS, CF, ROWS>;
+    auto k = beamform_kernel<PREC, DMAS, CF, PDAS, ROWS>;
     static size_t configured = 0;
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -847,26 +905,28 @@ cudaError_t launch_bf_t(const BfJob *jobs, const int *prefix, int njobs, int til
     return cudaGetLastError();
 }
 
-template <int PREC, int ROWS>
-cudaError_t launch_bf_pr(const BfJob *jobs, const int *prefix, int njobs, int tiles, size_t smem,
-                         int dmas, int cf, int *err, cudaStream_t st)
+template <int PREC, bool PDAS, int ROWS>
+cudaError_t launch_bf_pdr(const BfJob *jobs, const int *prefix, int njobs, int tiles, size_t smem,
+                          int dmas, int cf, int *err, cudaStream_t st)
 {
     if (dmas && cf)
-        return launch_bf_t<PREC, true, true, ROWS>(jobs, prefix, njobs, tiles, smem, err, st);
+        return launch_bf_t<PREC, true, true, PDAS, ROWS>(jobs, prefix, njobs, tiles, smem, err, st);
     if (dmas)
-        return launch_bf_t<PREC, true, false, ROWS>(jobs, prefix, njobs, tiles, smem, err, st);
+        return launch_bf_t<PREC, true, false, PDAS, ROWS>(jobs, prefix, njobs, tiles, smem, err, st);
     if (cf)
-        return launch_bf_t<PREC, false, true, ROWS>(jobs, prefix, njobs, tiles, smem, err, st);
-    return launch_bf_t<PREC, false, false, ROWS>(jobs, prefix, njobs, tiles, smem, err, st);
+        return launch_bf_t<PREC, false, true, PDAS, ROWS>(jobs, prefix, njobs, tiles, smem, err, st);
+    return launch_bf_t<PREC, false, false, PDAS, ROWS>(jobs, prefix, njobs, tiles, smem, err, st);
 }
 
 template <int PREC>
 cudaError_t launch_bf_p(const BfJob *jobs, const int *prefix, int njobs, int tiles, size_t smem,
-                        int dmas, int cf, int rows, int *err, cudaStream_t st)
+                        int dmas, int cf, int pdas, int rows, int *err, cudaStream_t st)
 {
     if (rows == 4)
-        return launch_bf_pr<PREC, 4>(jobs, prefix, njobs, tiles, smem, dmas, cf, err, st);
-    return launch_bf_pr<PREC, 8>(jobs, prefix, njobs, tiles, smem, dmas, cf, err, st);
+        return pdas ? launch_bf_pdr<PREC, true, 4>(jobs, prefix, njobs, tiles, smem, dmas, cf, err, st)
+                    : launch_bf_pdr<PREC, false, 4>(jobs, prefix, njobs, tiles, smem, dmas, cf, err, st);
+    return pdas ? launch_bf_pdr<PREC, true, 8>(jobs, prefix, njobs, tiles, smem, dmas, cf, err, st)
+                : launch_bf_pdr<PREC, false, 8>(jobs, prefix, njobs, tiles, smem, dmas, cf, err, st);
 }
 
 }  // namespace
@@ -915,14 +975,15 @@ cudaError_t launch_beamform(const BfJob *jobs_dev, const int *tile_prefix_dev, i
     if (njobs <= 0 || total_tiles <= 0)
         return cudaSuccess;
     const int dmas = (variant & BF_DMAS) ? 1 : 0, cf = (variant & BF_CF) ? 1 : 0;
+    const int pdas = (variant & BF_PDAS) ? 1 : 0;
     if (prec == kPrecF32)
         return launch_bf_p<kPrecF32>(jobs_dev, tile_prefix_dev, njobs, total_tiles, smem_bytes,
-                                     dmas, cf, rows, err_dev, stream);
+                                     dmas, cf, pdas, rows, err_dev, stream);
     if (prec == kPrecF16)
         return launch_bf_p<kPrecF16>(jobs_dev, tile_prefix_dev, njobs, total_tiles, smem_bytes,
-                                     dmas, cf, rows, err_dev, stream);
+                                     dmas, cf, pdas, rows, err_dev, stream);
     return launch_bf_p<kPrecBF16>(jobs_dev, tile_prefix_dev, njobs, total_tiles, smem_bytes, dmas,
-                                  cf, rows, err_dev, stream);
+                                  cf, pdas, rows, err_dev, stream);
 }
 
 cudaError_t launch_plain(const BfJob &job, const int16_t *rf, const int2 *valid, const float *dx2,

@@ -106,7 +106,8 @@ void geometry_tables(const GeomHost &g, GeometryHost &out)
 }
 
 void angle_tables(const GeomHost &g, const GeometryHost &geo, int ns,
-                  const std::vector<double> &angles, int prec, int rows_per_thread, PlanHost &out)
+                  const std::vector<double> &angles, int prec, int rows_per_thread,
+                  int stage_bytes, PlanHost &out)
 {
     const double kappa = g.fs / g.c;
     const int na = (int)angles.size();
@@ -184,7 +185,7 @@ void angle_tables(const GeomHost &g, const GeometryHost &geo, int ns,
     out.nsp = (ns + kPadL + 7) / 8 * 8;
     out.rows = rows_per_thread;
     out.align = align;
-    int grp = kStageBytes / (out.wmax * pair_bytes(prec) + kTileCols * 12);
+    int grp = stage_bytes / (out.wmax * pair_bytes(prec) + kTileCols * 12);
     out.group = std::max(1, std::min(kMaxGroup, std::min(grp, g.ne)));
 }
 

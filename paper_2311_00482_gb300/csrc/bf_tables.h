@@ -41,9 +41,12 @@ struct EnvHost {
 
 double grid_coord(double lo, double hi, int n, int j);
 void geometry_tables(const GeomHost &g, GeometryHost &out);
-// rows: rows per thread of the beamforming tile (tile height kWarps * rows)
+// rows: rows per thread of the beamforming tile (tile height kWarps * rows);
+// stage_bytes: target bytes of sample windows per pipeline stage (sets the
+// channels per stage)
 void angle_tables(const GeomHost &g, const GeometryHost &geo, int ns,
-                  const std::vector<double> &angles, int prec, int rows, PlanHost &out);
+                  const std::vector<double> &angles, int prec, int rows, int stage_bytes,
+                  PlanHost &out);
 void bandpass_bins(int nz, double z0, double z1, double c, double f0, int &lo, int &hi);
 void envelope_tables(int nz, EnvHost &out);
 

@@ -59,6 +59,12 @@ def test_bad_arguments_are_rejected_without_a_gpu(lib):
         assert bf.bf_last_error()
 
 
+def test_pdas_order_needs_a_handle(lib):
+    with pytest.raises(bf.BFError) as ei:
+        bf.bf_set_pdas_order(None, 2.0)
+    assert ei.value.code == bf.BF_EINVAL
+
+
 def _compare_tables_with_oracle(acq, angles_rad, ns, x_elem=None):
     grid = (acq.nx, acq.nz, acq.x0_m, acq.x1_m, acq.z0_m, acq.z1_m)
     xe = acq.x_elements() if x_elem is None else np.asarray(x_elem)
