@@ -554,8 +554,20 @@ int enqueue(const std::vector<FramePrep> &frames, const HostLaunch &hl, DeviceLa
             cudaStream_t st, cudaEvent_t *marks)
 {
     cudaError_t e;
-    if (marks)
-        cudaEventRecordWithFlags(marks[0], st, cudaEventRecordExternal);
+    // Inside a stream capture the marks must be external event records (they
+    // become graph nodes that record at replay time); outside, plain records.
+    unsigned mark_flags = cudaEventRecordDefault;
+    if (marks) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing(st, &cs);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaStreamIsCapturing");
+        if (cs == cudaStreamCaptureStatusActive)
+            mark_flags = cudaEventRecordExternal;
+        e = cudaEventRecordWithFlags(marks[0], st, mark_flags);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaEventRecord (mark)");
+    }
     for (const HostLaunch::IGroup &g : hl.igroups) {
         e = launch_ingest((const IngestJob *)dl.ingest.p + g.first,
                           (const int *)dl.ingest_prefix.p + g.prefix_first, g.count, g.rows, g.prec,
@@ -571,7 +583,7 @@ int enqueue(const std::vector<FramePrep> &frames, const HostLaunch &hl, DeviceLa
         }
     }
     if (marks)
-        cudaEventRecordWithFlags(marks[1], st, cudaEventRecordExternal);
+        cudaEventRecordWithFlags(marks[1], st, mark_flags);
     for (const HostLaunch::Group &g : hl.groups) {
         e = launch_beamform((const BfJob *)dl.jobs.p + g.first,
                             (const int *)dl.tile_prefix.p + g.prefix_first, g.count, g.tiles, hl.smem,
@@ -580,7 +592,7 @@ int enqueue(const std::vector<FramePrep> &frames, const HostLaunch &hl, DeviceLa
             return cuda_fail(e, "beamform launch");
     }
     if (marks)
-        cudaEventRecordWithFlags(marks[2], st, cudaEventRecordExternal);
+        cudaEventRecordWithFlags(marks[2], st, mark_flags);
     if (!hl.env.empty()) {
         e = launch_envelope((const EnvJob *)dl.env.p, (const int *)dl.env_prefix.p, (int)hl.env.size(),
                             hl.env_blocks, hl.env_smem, st);
@@ -594,7 +606,7 @@ int enqueue(const std::vector<FramePrep> &frames, const HostLaunch &hl, DeviceLa
             return cuda_fail(e, "log launch");
     }
     if (marks)
-        cudaEventRecordWithFlags(marks[3], st, cudaEventRecordExternal);
+        cudaEventRecordWithFlags(marks[3], st, mark_flags);
     return BF_OK;
 }
 
