@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline / reference leg are the only importers.  The product
 package never imports it, and it imports nothing from the product package.
 
-* ``beamform`` / ``beamform_pdas`` / ``delayed_samples`` wrap ``bf_oracle.c`` (double precision,
+* ``beamform`` / ``beamform_pdas`` / ``beamform_iq`` / ``delayed_samples`` wrap
+  ``bf_oracle.c``; ``demodulate`` forms the complex baseband records of IQ beamforming (double precision,
   plain loops over pixels, angles and channels; see that file's header for
   the exact definition it follows, Eq. (1) and Sec. II-B of the paper).
 * ``envelope`` is the analytic-signal magnitude along depth computed with a
@@ -59,6 +60,9 @@ def _bind(lib):
     lib.oracle_beamform_pdas.argtypes = [p, i32, i32, i32, p, p, i32, i32, d, d, d, d, d, d, d,
                                          d, p, i64, p, i32]
     lib.oracle_beamform_pdas.restype = ctypes.c_int
+    lib.oracle_beamform_iq.argtypes = [p, p, i32, i32, i32, p, p, i32, i32, d, d, d, d, d, d, d,
+                                       d, p, i64, p, p, i32]
+    lib.oracle_beamform_iq.restype = ctypes.c_int
     lib.oracle_max_threads.restype = ctypes.c_int32
     return lib
 
@@ -167,6 +171,43 @@ def beamform_pdas(rf, x_elem, angles_rad, grid, fs, c, f_number, p, *, pixels=No
                                       _ptr(pix), npix, _ptr(out), int(threads))
     if rc != 0:
         raise ValueError("oracle_beamform_pdas rejected its arguments (rc=%d)" % rc)
+    return out
+
+
+def demodulate(rf, fs, f0):
+    """Complex baseband records IQ[k] = a[k] exp(-j 2 pi f0 k / fs), a the analytic
+    signal of each channel record along its samples (one-sided spectrum, the
+    scipy.signal.hilbert convention), in float64.  rf: [..., Ns]."""
+    u = np.asarray(rf, dtype=np.float64)
+    ns = u.shape[-1]
+    a = np.fft.ifft(np.fft.fft(u, axis=-1) * spectral_mask(ns), axis=-1)
+    k = np.arange(ns, dtype=np.float64)
+    return a * np.exp(-2j * np.pi * f0 * k / fs)
+
+
+def beamform_iq(iq, x_elem, angles_rad, grid, fs, c, f_number, f0, *, pixels=None, threads=0):
+    """|IQ-DAS| and |BB-DMAS| (Eq. (4)) images in float64 from complex baseband
+    records iq [A][N][Ns] (``demodulate``).  Shapes as ``beamform``."""
+    iq = np.asarray(iq)
+    na, ne, ns = iq.shape
+    re = np.ascontiguousarray(iq.real, dtype=np.float64)
+    im = np.ascontiguousarray(iq.imag, dtype=np.float64)
+    x_elem = np.ascontiguousarray(x_elem, dtype=np.float64)
+    th = np.ascontiguousarray(np.atleast_1d(angles_rad), dtype=np.float64)
+    assert x_elem.shape == (ne,) and th.shape == (na,)
+    nx, nz, x0, x1, z0, z1 = _grid(grid)
+    if pixels is None:
+        shape, pix, npix = (nx, nz), None, nx * nz
+    else:
+        pix = np.ascontiguousarray(pixels, dtype=np.int64)
+        shape, npix = pix.shape, pix.size
+    out = {"iqdas": np.empty(shape, np.float64), "bbdmas": np.empty(shape, np.float64)}
+    rc = _load().oracle_beamform_iq(_ptr(re), _ptr(im), na, ne, ns, _ptr(x_elem), _ptr(th), nx, nz,
+                                    x0, x1, z0, z1, float(fs), float(c), float(f_number), float(f0),
+                                    _ptr(pix), npix, _ptr(out["iqdas"]), _ptr(out["bbdmas"]),
+                                    int(threads))
+    if rc != 0:
+        raise ValueError("oracle_beamform_iq rejected its arguments (rc=%d)" % rc)
     return out
 
 

@@ -40,6 +40,15 @@ MUTANTS = [
     ("pDAS power dropped", "y += signed_pow(yt, p);", "y += yt;"),
     ("pDAS root loses the sign", "return -pow(-v, e);", "return pow(-v, e);"),
     ("pDAS keeps the last angle", "y += signed_pow(yt, p);", "y = signed_pow(yt, p);"),
+    ("IQ carrier restored with the wrong sign", "double cr = cos(ph), ci = sin(ph);",
+     "double cr = cos(ph), ci = -sin(ph);"),
+    ("IQ interpolation weights swapped",
+     "double br = (1.0 - alpha) * iq_re[o] + alpha * iq_re[o + 1];",
+     "double br = alpha * iq_re[o] + (1.0 - alpha) * iq_re[o + 1];"),
+    ("BB-DMAS without the square root", "double w = 1.0 / sqrt(mag);", "double w = 1.0;"),
+    ("BB-DMAS without 1/M", "double ur = tr / (double)m, ui = ti / (double)m;",
+     "double ur = tr, ui = ti;"),
+    ("BB-DMAS squares the magnitude", "y2r += ur * ur - ui * ui;", "y2r += ur * ur + ui * ui;"),
 ]
 
 
@@ -56,6 +65,9 @@ def _pins_pass(golden_dir):
         lambda: pins.test_pdas_constant_record_closed_form(golden_dir),
         pins.test_pdas_p1_is_das_and_single_channel_is_the_sample,
         pins.test_pdas_homogeneous_odd_and_brute_force,
+        lambda: pins.test_iq_das_and_bb_dmas_hand_derived_case(golden_dir),
+        pins.test_iq_combiners_against_a_numpy_evaluation,
+        pins.test_iq_images_are_homogeneous_and_single_channel_bb_dmas_is_the_magnitude,
     ]
     for check in checks:
         try:

@@ -350,3 +350,99 @@ def test_pdas_homogeneous_odd_and_brute_force():
                 s = np.sum(np.sign(v[a][act[a]]) * np.abs(v[a][act[a]]) ** (1.0 / p))
                 expect += np.sign(s) * abs(s) ** p
             assert y[ix, iz] == pytest.approx(expect, rel=1e-10, abs=1e-9)
+
+
+# ---------------------------------------------------------- IQ / BB-DMAS --
+
+def test_demodulation_of_a_bin_centred_tone_is_constant():
+    """u[k] = A cos(2 pi k0 k / Ns + phi) on an exact bin, demodulated at
+    f0 / fs = k0 / Ns: the analytic signal is A exp(j(2 pi k0 k / Ns + phi)),
+    so the baseband record is the constant A exp(j phi)."""
+    ns, k0, amp, phi = 512, 64, 3.0, 0.7
+    k = np.arange(ns)
+    u = amp * np.cos(2 * np.pi * k0 * k / ns + phi)
+    iq = oracle.demodulate(u, fs=1.0, f0=k0 / ns)
+    np.testing.assert_allclose(iq, amp * np.exp(1j * phi) * np.ones(ns), rtol=0, atol=1e-12)
+    # a tone above the carrier keeps rotating at the difference frequency
+    iq2 = oracle.demodulate(np.cos(2 * np.pi * 80 * k / ns), fs=1.0, f0=k0 / ns)
+    np.testing.assert_allclose(iq2, np.exp(2j * np.pi * 16 * k / ns), rtol=0, atol=1e-12)
+
+
+def test_iq_das_and_bb_dmas_hand_derived_case(golden_dir):
+    spec = _load(golden_dir, "iq_cases.json")
+    geo = _load(golden_dir, "geometry_cases.json")["cases"]
+    steer = [c for c in geo if c["name"].startswith("3-4-5, wave steered")]
+    assert len(steer) == 2
+    ns, k0, amp = spec["n_samples"], spec["bin"], spec["amplitude"]
+    k = np.arange(ns)
+    u = np.rint(amp * np.cos(2 * np.pi * k0 * k / ns)).astype(np.int16)
+    rf = np.stack([u[None, :], u[None, :]])  # [A=2][N=1][Ns]
+    fs, c = steer[0]["fs_hz"], steer[0]["c_mps"]
+    f0 = spec["f0_over_fs"] * fs
+    angles = [steer[0]["angles_rad"][0], steer[1]["angles_rad"][0]]
+    iq = oracle.demodulate(rf, fs, f0)
+    out = oracle.beamform_iq(iq, [0.0], angles, _single_pixel_grid(0.003, 0.004), fs, c, 0.5, f0)
+    r1 = k0 / ns
+    expect_das = 2 * amp * abs(math.cos(math.pi * r1 * 45))
+    expect_dmas = 2 * amp * abs(math.cos(2 * math.pi * r1 * 45))
+    assert expect_das == pytest.approx(spec["expect_iq_das"], rel=1e-8)
+    assert expect_dmas == pytest.approx(spec["expect_bb_dmas"], rel=1e-8)
+    assert out["iqdas"][0, 0] == pytest.approx(expect_das, rel=1e-3)
+    assert out["bbdmas"][0, 0] == pytest.approx(expect_dmas, rel=1e-3)
+
+
+def _iq_case():
+    acq = synth.SPECKLE_POINTS_128.with_(nx=9, nz=7, n_elements=16, n_samples=1024,
+                                         angles_deg=(-5.0, 3.0))
+    rf, _ = synth.speckle_points_frame(acq)
+    grid = (acq.nx, acq.nz, acq.x0_m, acq.x1_m, acq.z0_m, acq.z1_m)
+    return acq, rf, grid
+
+
+def test_iq_combiners_against_a_numpy_evaluation():
+    """Delays from a ramp record (linear interpolation returns n itself), then
+    baseband interpolation, carrier restoration and both combiners in numpy."""
+    acq, rf, grid = _iq_case()
+    xe = acq.x_elements()
+    iq = oracle.demodulate(rf, acq.fs_hz, acq.f0_hz)
+    out = oracle.beamform_iq(iq, xe, acq.angles_rad, grid, acq.fs_hz, acq.c_mps, acq.f_number,
+                             acq.f0_hz)
+    ramp = np.broadcast_to(np.arange(acq.n_samples, dtype=np.int16), rf.shape).copy()
+    for ix, iz in ((0, 0), (4, 3), (8, 6), (2, 5), (6, 1)):
+        n, act, rec = oracle.delayed_samples(ramp, xe, acq.angles_rad, grid, ix, iz, acq.fs_hz,
+                                             acq.c_mps, acq.f_number)
+        y1 = 0j
+        y2 = 0j
+        for a in range(n.shape[0]):
+            t = 0j
+            for i in range(n.shape[1]):
+                if not (act[a, i] and rec[a, i]):
+                    continue
+                k = int(math.floor(n[a, i]))
+                al = n[a, i] - k
+                b = (1 - al) * iq[a, i, k] + al * iq[a, i, k + 1]
+                s = b * np.exp(2j * np.pi * acq.f0_hz * n[a, i] / acq.fs_hz)
+                y1 += s
+                if abs(s) > 0:
+                    t += s / math.sqrt(abs(s))
+            m = int(act[a].sum())
+            if m:
+                y2 += (t / m) ** 2
+        assert out["iqdas"][ix, iz] == pytest.approx(abs(y1), rel=1e-9, abs=1e-9)
+        assert out["bbdmas"][ix, iz] == pytest.approx(abs(y2), rel=1e-9, abs=1e-9)
+
+
+def test_iq_images_are_homogeneous_and_single_channel_bb_dmas_is_the_magnitude():
+    """|IQ-DAS| and |BB-DMAS| are degree-1 homogeneous in the record; with one
+    receive element and one angle, |BB-DMAS| = |s| = |IQ-DAS|."""
+    acq, rf, grid = _iq_case()
+    xe = acq.x_elements()
+    args = (xe, acq.angles_rad, grid, acq.fs_hz, acq.c_mps, acq.f_number, acq.f0_hz)
+    iq = oracle.demodulate(rf, acq.fs_hz, acq.f0_hz)
+    o1 = oracle.beamform_iq(iq, *args)
+    o3 = oracle.beamform_iq(3.0 * iq, *args)
+    np.testing.assert_allclose(o3["iqdas"], 3 * o1["iqdas"], rtol=1e-12, atol=1e-9)
+    np.testing.assert_allclose(o3["bbdmas"], 3 * o1["bbdmas"], rtol=1e-12, atol=1e-9)
+    one = oracle.beamform_iq(iq[:1, 5:6], xe[5:6], acq.angles_rad[:1], grid, acq.fs_hz, acq.c_mps,
+                             0.1, acq.f0_hz)
+    np.testing.assert_allclose(one["bbdmas"], one["iqdas"], rtol=1e-12, atol=1e-9)
