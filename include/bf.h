@@ -77,6 +77,16 @@ enum { BF_DAS = 1, BF_DMAS = 2, BF_CF = 4, BF_PDAS = 8, BF_MODE_MASK = 15 };
 enum { BF_PREC_FP32 = 0, BF_PREC_FP16 = 1 << 4, BF_PREC_BF16 = 2 << 4, BF_PREC_MASK = 3 << 4 };
 /* ... and the output stage (bits 8-9). */
 enum { BF_OUT_RF = 0, BF_OUT_ENV = 1 << 8, BF_OUT_LOGDB = 2 << 8, BF_OUT_MASK = 3 << 8 };
+/* IQ combiners (bits 12-13; not with the RF combiners above in one call, FP32
+ * storage, n_samples a power of two <= 8192): each channel record is
+ * demodulated to complex baseband (analytic signal times exp(-j 2 pi f0 k / fs)),
+ * interpolated linearly at the delay and re-modulated by exp(j 2 pi f0 n / fs):
+ *   IQ-DAS  = |sum_theta sum_active s|                        (Sec. II-B-1)
+ *   BB-DMAS = |sum_theta ((1/M) sum_active sqrt|s| e^{j arg s})^2|, M = channels
+ *             inside the aperture                             (Eq. (4))
+ * Their outputs are magnitude images: BF_OUT_RF and BF_OUT_ENV both return
+ * them, BF_OUT_LOGDB their -70 dB log compression. */
+enum { BF_IQDAS = 1 << 12, BF_BBDMAS = 1 << 13, BF_IQ_MASK = 3 << 12 };
 
 enum {
     BF_OK = 0,
@@ -113,7 +123,7 @@ BF_API int bf_set_stream(bf_handle *h, void *cuda_stream);
  * call (a prepared batch keeps the value it was created with). */
 BF_API int bf_set_pdas_order(bf_handle *h, double p);
 
-/* Bytes of one output for the given mode_and_flags: popcount(modes) * nx * nz * 4. */
+/* Bytes of one output for the given mode_and_flags: images * nx * nz * 4. */
 BF_API size_t bf_output_bytes(const bf_handle *h, uint32_t mode_and_flags);
 
 /* Paper: Sec. II-B, Eq. (1) (delay, interpolation, apodization, sum), the
@@ -121,8 +131,9 @@ BF_API size_t bf_output_bytes(const bf_handle *h, uint32_t mode_and_flags);
  * Stream-ordered beamforming of one frame, device-resident data.
  * rf_dev: device int16 [n_angles][n_elements][n_samples] (read during the call's
  * stream work), angles_rad: host array of n_angles plane-wave angles in
- * (-pi/2, pi/2); out_dev: device float [popcount(modes)][nx][nz] (modes in bit
- * order DAS, DMAS, CF, pDAS; z fastest) receiving the stage selected by BF_OUT_*.
+ * (-pi/2, pi/2); out_dev: device float [images][nx][nz] (one image per selected
+ * combiner in bit order DAS, DMAS, CF, pDAS, IQ-DAS, BB-DMAS; z fastest)
+ * receiving the stage selected by BF_OUT_*.
  * The envelope of the DMAS image goes through the [f0, 3 f0] band-pass; the
  * other images are used as they are.
  * Returns after enqueueing; the caller synchronises the stream.  Calls on one

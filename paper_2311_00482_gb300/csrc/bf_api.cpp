@@ -133,7 +133,8 @@ static int encode_map(CUtensorMap *map, void *base, int rows, int cols, int elem
 
 static int encode_pairs_map(CUtensorMap *map, void *base, int rows, int nsp, int box, int prec)
 {
-    return encode_map(map, base, rows, nsp, pair_bytes(prec), box, 1);
+    const int k = pair_elems(prec);  // IQ pairs: two 8-byte elements each
+    return encode_map(map, base, rows, nsp * k, pair_bytes(prec) / k, box * k, 1);
 }
 
 // -------------------------------------------------------- envelope tables --
@@ -281,7 +282,21 @@ int handle_plan(bf_handle *h, int ns, const double *angles, int na, int prec, Pl
 
 // ------------------------------------------------------- frame preparation --
 
+static constexpr double kPi = 3.14159265358979323846;
+
 static int popcount4(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1) + ((m >> 3) & 1); }
+
+// Images one frame produces: one per selected RF or IQ combiner.
+static int frame_images(uint32_t flags)
+{
+    return popcount4(flags & BF_MODE_MASK) + ((flags & BF_IQDAS) ? 1 : 0) +
+           ((flags & BF_BBDMAS) ? 1 : 0);
+}
+
+int frame_prec(uint32_t flags)
+{
+    return (flags & BF_IQ_MASK) ? (int)kPrecIQ : (int)((flags & BF_PREC_MASK) >> 4);
+}
 
 int check_frame_args(bf_handle *h, int ns, const double *angles, int na, uint32_t flags)
 {
@@ -296,14 +311,24 @@ int check_frame_args(bf_handle *h, int ns, const double *angles, int na, uint32_
     for (int a = 0; a < na; ++a)
         if (!std::isfinite(angles[a]) || std::fabs(angles[a]) >= 1.5707963267948966)
             return fail(BF_EINVAL, "angle %d (%g rad) outside (-pi/2, pi/2)", a, angles[a]);
-    const int modes = flags & BF_MODE_MASK;
-    if (!modes)
-        return fail(BF_EINVAL, "no combiner selected (BF_DAS / BF_DMAS / BF_CF / BF_PDAS)");
-    if (flags & ~(uint32_t)(BF_MODE_MASK | BF_PREC_MASK | BF_OUT_MASK))
+    const int modes = flags & BF_MODE_MASK, iq = flags & BF_IQ_MASK;
+    if (!modes && !iq)
+        return fail(BF_EINVAL,
+                    "no combiner selected (BF_DAS / BF_DMAS / BF_CF / BF_PDAS / BF_IQDAS / BF_BBDMAS)");
+    if (flags & ~(uint32_t)(BF_MODE_MASK | BF_IQ_MASK | BF_PREC_MASK | BF_OUT_MASK))
         return fail(BF_EINVAL, "unknown bits in mode_and_flags 0x%x", flags);
     const int prec = (flags & BF_PREC_MASK) >> 4;
     if (prec > kPrecBF16)
         return fail(BF_EINVAL, "unknown precision bits");
+    if (iq) {
+        if (modes)
+            return fail(BF_EINVAL, "IQ combiners cannot be combined with RF combiners in one call");
+        if (prec != kPrecF32)
+            return fail(BF_EINVAL, "IQ combiners use FP32 storage");
+        if (ns < 4 || ns > 8192 || (ns & (ns - 1)) != 0)
+            return fail(BF_EINVAL, "IQ combiners need a power-of-two n_samples in [4, 8192] (got %d)",
+                        ns);
+    }
     const int stage = flags & BF_OUT_MASK;
     if (stage != BF_OUT_RF && stage != BF_OUT_ENV && stage != BF_OUT_LOGDB)
         return fail(BF_EINVAL, "unknown output stage bits");
@@ -316,7 +341,7 @@ int check_frame_args(bf_handle *h, int ns, const double *angles, int na, uint32_
 
 size_t frame_out_bytes(const bf_handle *h, uint32_t flags)
 {
-    return (size_t)popcount4(flags & BF_MODE_MASK) * (size_t)h->g.nx * (size_t)h->g.nz * sizeof(float);
+    return (size_t)frame_images(flags) * (size_t)h->g.nx * (size_t)h->g.nz * sizeof(float);
 }
 
 int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *angles, int na,
@@ -325,16 +350,18 @@ int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *ang
     int rc = check_frame_args(h, ns, angles, na, flags);
     if (rc)
         return rc;
-    const int prec = (flags & BF_PREC_MASK) >> 4;
+    const int prec = frame_prec(flags);
+    const bool iq = prec == kPrecIQ;
     Plan *plan = nullptr;
     rc = handle_plan(h, ns, angles, na, prec, &plan, cfg);
     if (rc)
         return rc;
-    const int modes = flags & BF_MODE_MASK, nm = popcount4(modes), stage = flags & BF_OUT_MASK;
+    const int modes = flags & (BF_MODE_MASK | BF_IQ_MASK), nm = frame_images(flags);
+    const int stage = flags & BF_OUT_MASK;
     const size_t img = (size_t)h->g.nx * h->g.nz;
     const int rows = na * h->g.ne;
     rc = s.pairs.ensure((size_t)rows * plan->nsp * pair_bytes(prec));
-    if (!rc && stage != BF_OUT_RF)
+    if (!rc && stage != BF_OUT_RF && !iq)  // IQ images are magnitudes already
         rc = s.y.ensure(nm * img * sizeof(float));
     if (!rc && stage == BF_OUT_LOGDB)
         rc = s.env.ensure(nm * img * sizeof(float));
@@ -356,8 +383,13 @@ int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *ang
     fp.prec = prec;
     fp.out = out_dev;
     fp.pairs = s.pairs.p;
-    fp.y = stage == BF_OUT_RF ? out_dev : (float *)s.y.p;
-    fp.env = stage == BF_OUT_ENV ? out_dev : (stage == BF_OUT_LOGDB ? (float *)s.env.p : nullptr);
+    if (iq) {  // the beamformer writes magnitudes: straight out, or into the log stage's input
+        fp.y = stage == BF_OUT_LOGDB ? (float *)s.env.p : out_dev;
+        fp.env = stage == BF_OUT_LOGDB ? (float *)s.env.p : nullptr;
+    } else {
+        fp.y = stage == BF_OUT_RF ? out_dev : (float *)s.y.p;
+        fp.env = stage == BF_OUT_ENV ? out_dev : (stage == BF_OUT_LOGDB ? (float *)s.env.p : nullptr);
+    }
     fp.maxbits = (unsigned *)s.maxbits.p;
     fp.map_dev = (CUtensorMap *)s.map.p;
     if (s.map_base != s.pairs.p || s.map_rows != rows || s.map_nsp != plan->nsp ||
@@ -375,8 +407,13 @@ int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *ang
     fp.map_host = s.map_host;
     fp.map_dirty = s.map_dirty;
     fp.scratch = &s;
-    if (stage != BF_OUT_RF) {
+    if (stage != BF_OUT_RF && !iq) {
         rc = env_tables(h->g.nz, fp.et);
+        if (rc)
+            return rc;
+    }
+    if (iq) {
+        rc = env_tables(ns, fp.dt);  // twiddles of the length-ns transforms
         if (rc)
             return rc;
     }
@@ -412,13 +449,20 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
         j.box = p->box;
         j.group = p->group;
         j.rows = p->rows;
-        j.modes = f.modes;
+        // the IQ kernel reads its two combiners from the DAS / DMAS slots of the mode word
+        j.modes = f.prec == kPrecIQ ? (((f.modes & BF_IQDAS) ? BF_DAS : 0) |
+                                       ((f.modes & BF_BBDMAS) ? BF_DMAS : 0))
+                                    : f.modes;
         j.tiles_x = p->tiles_x;
         j.tiles_z = p->tiles_z;
-        j.out_scale = f.prec == kPrecF32 ? 1.0f : 32768.0f;
+        j.out_scale = (f.prec == kPrecF32 || f.prec == kPrecIQ) ? 1.0f : 32768.0f;
         j.pdas_p = (float)f.pdas_p;
         j.pdas_inv_p = (float)(1.0 / f.pdas_p);
-        const int variant = (p->rows * 4 + f.prec) * 16 + (f.modes & (BF_DMAS | BF_CF | BF_PDAS));
+        const double r = h->g.f0 / h->g.fs;  // carrier cycles per sample
+        j.iq_c1 = (float)(2.0 * kPi * r);
+        j.iq_c2 = (float)(kPi * r);
+        j.maxbits = (f.prec == kPrecIQ && f.stage == BF_OUT_LOGDB) ? f.maxbits : nullptr;
+        const int variant = (p->rows * 4 + f.prec) * 16 + (j.modes & (BF_DMAS | BF_CF | BF_PDAS));
         groups[variant].push_back(j);
         hl.smem = std::max(hl.smem, beamform_smem_bytes(p->wmax, p->group, f.prec));
     }
@@ -440,8 +484,28 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
         hl.groups.push_back(g);
     }
     std::map<int, std::vector<IngestJob>> ig;
-    for (const FramePrep &f : frames)
+    for (const FramePrep &f : frames) {
+        if (f.prec == kPrecIQ) {
+            const double r = f.h->g.f0 / f.h->g.fs;
+            DemodJob d{};
+            d.rf = f.rf;
+            d.pairs = (float4 *)f.pairs;
+            d.rows = f.na * f.h->g.ne;
+            d.ns = f.ns;
+            d.nsp = f.plan->nsp;
+            d.lgn = 0;
+            while ((1 << d.lgn) < f.ns)
+                ++d.lgn;
+            d.rot = make_float2((float)std::cos(2.0 * kPi * r), (float)-std::sin(2.0 * kPi * r));
+            d.tw = (const float2 *)f.dt->tw.p;
+            hl.demod_prefix.push_back(hl.demod_rows);
+            hl.demod_rows += d.rows;
+            hl.demod_max_ns = std::max(hl.demod_max_ns, f.ns);
+            hl.demod.push_back(d);
+            continue;
+        }
         ig[f.prec].push_back(IngestJob{f.rf, f.pairs, f.na * f.h->g.ne, f.ns, f.plan->nsp});
+    }
     for (auto &kv : ig) {
         HostLaunch::IGroup g;
         g.prec = kv.first;
@@ -464,6 +528,22 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
             continue;
         const bf_handle *h = f.h;
         const size_t img = (size_t)h->g.nx * h->g.nz;
+        if (f.prec == kPrecIQ) {  // magnitude images: only the log stage follows
+            if (f.stage != BF_OUT_LOGDB)
+                continue;
+            const int nimg = ((f.modes & BF_IQDAS) ? 1 : 0) + ((f.modes & BF_BBDMAS) ? 1 : 0);
+            for (int slot = 0; slot < nimg; ++slot) {
+                LogJob l{};
+                l.env = f.env + slot * img;
+                l.out = f.out + slot * img;
+                l.maxbits = f.maxbits + slot;
+                l.n = (int)img;
+                hl.blk_prefix.push_back((int)blks);
+                blks += log_blocks((long long)img);
+                hl.log.push_back(l);
+            }
+            continue;
+        }
         int slot = 0;
         for (int bit = 1; bit <= BF_PDAS; bit <<= 1) {
             if (!(f.modes & bit))
@@ -524,6 +604,8 @@ int DeviceLaunch::upload(const HostLaunch &hl, cudaStream_t st, bool async)
     if (!rc) rc = put(env_prefix, hl.env_prefix.data(), hl.env_prefix.size() * sizeof(int));
     if (!rc) rc = put(log, hl.log.data(), hl.log.size() * sizeof(LogJob));
     if (!rc) rc = put(blk_prefix, hl.blk_prefix.data(), hl.blk_prefix.size() * sizeof(int));
+    if (!rc) rc = put(demod, hl.demod.data(), hl.demod.size() * sizeof(DemodJob));
+    if (!rc) rc = put(demod_prefix, hl.demod_prefix.data(), hl.demod_prefix.size() * sizeof(int));
     if (!rc) rc = err.ensure(sizeof(int));
     return rc;
 }
@@ -574,6 +656,12 @@ int enqueue(const std::vector<FramePrep> &frames, const HostLaunch &hl, DeviceLa
                           st);
         if (e != cudaSuccess)
             return cuda_fail(e, "ingest launch");
+    }
+    if (!hl.demod.empty()) {
+        e = launch_demod((const DemodJob *)dl.demod.p, (const int *)dl.demod_prefix.p,
+                         (int)hl.demod.size(), hl.demod_rows, hl.demod_max_ns, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "demodulation launch");
     }
     for (const FramePrep &f : frames) {
         if (f.stage != BF_OUT_RF) {
@@ -793,6 +881,8 @@ BF_API int bf_beamform_plain(bf_handle *h, const int16_t *rf_dev, int32_t n_samp
         return fail(BF_EINVAL, "null data pointer");
     if (flags & BF_PREC_MASK)
         return fail(BF_EINVAL, "the plain kernel computes from int16 records in FP32 only");
+    if (flags & BF_IQ_MASK)
+        return fail(BF_EINVAL, "the plain kernel computes the RF combiners only");
     cudaSetDevice(h->device);
     if (!is_device_pointer(rf_dev) || !is_device_pointer(out_dev))
         return fail(BF_EINVAL, "bf_beamform_plain needs device pointers");
@@ -908,7 +998,7 @@ BF_API int bf_plan_info(bf_handle *h, int32_t n_samples, const double *angles_ra
         return fail(BF_EINVAL, "null info");
     cudaSetDevice(h->device);
     Plan *p = nullptr;
-    rc = handle_plan(h, n_samples, angles_rad, n_angles, (flags & BF_PREC_MASK) >> 4, &p);
+    rc = handle_plan(h, n_samples, angles_rad, n_angles, frame_prec(flags), &p);
     if (rc)
         return rc;
     const size_t n = (size_t)n_angles * p->tiles_x * p->tiles_z * h->g.ne;
@@ -1009,7 +1099,7 @@ BF_API int bf_autotune(bf_handle *h, int32_t n_samples, const double *angles_rad
         return fail(BF_EINVAL, "no tile configuration fits this workload");
     {
         std::lock_guard<std::mutex> lk(h->mu);
-        PlanKey key{n_samples, (int)((flags & BF_PREC_MASK) >> 4),
+        PlanKey key{n_samples, frame_prec(flags),
                     std::vector<double>(angles_rad, angles_rad + n_angles), 0};
         h->tuned[key] = best;
     }
@@ -1066,8 +1156,8 @@ BF_API int bf_batch_create(const bf_frame *frames, int32_t n, bf_batch **out)
     for (auto &m : b->marks)
         if (e == cudaSuccess)
             e = cudaEventCreate(&m);
-    b->launches = (int)b->hl.igroups.size() + (int)b->hl.groups.size() + (b->hl.env.empty() ? 0 : 1) +
-                  (b->hl.log.empty() ? 0 : 1);
+    b->launches = (int)b->hl.igroups.size() + (b->hl.demod.empty() ? 0 : 1) +
+                  (int)b->hl.groups.size() + (b->hl.env.empty() ? 0 : 1) + (b->hl.log.empty() ? 0 : 1);
     if (e == cudaSuccess)
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {

@@ -367,7 +367,7 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
     Slot &s = *req->slot;
     const size_t before = s.device_bytes();
     // admission by device memory: the slot may have to grow
-    const int prec = (flags & BF_PREC_MASK) >> 4;
+    const int prec = frame_prec(flags);
     Plan *plan = nullptr;
     rc = handle_plan(h, ns, angles, na, prec, &plan);
     size_t need = rf_bytes + out_bytes + (size_t)na * h->g.ne * (plan ? plan->nsp : 0) * pair_bytes(prec);

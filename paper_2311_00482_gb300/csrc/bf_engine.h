@@ -96,7 +96,8 @@ struct FrameScratch {
 struct FramePrep {
     bf_handle *h = nullptr;
     Plan *plan = nullptr;
-    std::shared_ptr<EnvTablesDev> et;
+    std::shared_ptr<EnvTablesDev> et;   // envelope transform tables (nz)
+    std::shared_ptr<EnvTablesDev> dt;   // demodulation transform tables (n_samples; IQ only)
     const int16_t *rf = nullptr;
     int ns = 0, na = 0, modes = 0, stage = 0, prec = 0;
     double pdas_p = 2.0;
@@ -131,10 +132,14 @@ struct HostLaunch {
     std::vector<LogJob> log;
     std::vector<int> blk_prefix;
     int log_blocks = 0;
+    std::vector<DemodJob> demod;   // IQ frames: records to analytic-signal pairs
+    std::vector<int> demod_prefix;
+    int demod_rows = 0, demod_max_ns = 0;
 };
 
 struct DeviceLaunch {
     DevMem jobs, tile_prefix, ingest, ingest_prefix, env, env_prefix, log, blk_prefix, err;
+    DevMem demod, demod_prefix;
     int upload(const HostLaunch &hl, cudaStream_t st, bool async);
 };
 
@@ -177,6 +182,8 @@ int handle_plan(bf_handle *h, int ns, const double *angles, int na, int prec, Pl
                 int cfg = -1);
 int check_frame_args(bf_handle *h, int ns, const double *angles, int na, uint32_t flags);
 size_t frame_out_bytes(const bf_handle *h, uint32_t flags);
+// Storage code of a frame's staged records (kPrecIQ for the IQ combiners).
+int frame_prec(uint32_t flags);
 int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *angles, int na,
                   uint32_t flags, float *out_dev, FrameScratch &s, FramePrep &fp, int cfg = -1);
 void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl);

@@ -37,7 +37,9 @@ struct TileConfig {
 constexpr TileConfig kTileConfigs[] = {{4, 24 << 10}, {4, 16 << 10}, {4, 32 << 10}, {8, 24 << 10}};
 constexpr int kNumTileConfigs = 4;
 
-enum Prec : int { kPrecF32 = 0, kPrecF16 = 1, kPrecBF16 = 2 };
+// Storage of the staged records: RF sample pairs in FP32 (mid, diff), FP16 or
+// BF16, or complex analytic-signal pairs for IQ beamforming (kPrecIQ, FP32).
+enum Prec : int { kPrecF32 = 0, kPrecF16 = 1, kPrecBF16 = 2, kPrecIQ = 3 };
 
 // Device-side error bits (written with atomicOr into a per-launch word).
 enum DevErr : int { kErrTimeout = 1, kErrWindow = 2, kErrConfig = 4 };
@@ -68,6 +70,12 @@ struct BfJob {
     float out_scale;      // 1 (FP32 pairs) or 32768 (FP16 / BF16 data scaled by 2^-15)
     float pdas_p;         // order p of the pDAS combiner
     float pdas_inv_p;     // 1 / p
+    // IQ beamforming: the carrier phase 2 pi (f0 / fs) (alpha' + 1/2) of the
+    // fractional offset alpha' in [-1/2, 1/2] is fma(alpha', iq_c1, iq_c2);
+    // maxbits (non-null when the magnitude images feed the log stage) receives
+    // each image's maximum (float bits), one word per output slot.
+    float iq_c1, iq_c2;
+    unsigned *maxbits;
 };
 
 // Inputs of the per-plan window planner (one job per plan).
@@ -89,6 +97,19 @@ struct IngestJob {
     const int16_t *rf;    // [rows][ns]
     void *pairs;          // [rows][nsp]
     int rows, ns, nsp;
+};
+
+// One frame's int16 records to complex analytic-signal pairs for IQ
+// beamforming: per record the analytic signal a[k] (one-sided spectrum of a
+// power-of-two-length FFT), then pair j (samples k = j - kPadL and k + 1)
+// holds mid = (A + B) / 2 and diff = B - A with A = a[k],
+// B = a[k + 1] exp(-j 2 pi f0 / fs) (zero outside the record).
+struct DemodJob {
+    const int16_t *rf;    // [rows][ns]
+    float4 *pairs;        // [rows][nsp] (mid.re, mid.im, diff.re, diff.im)
+    int rows, ns, nsp, lgn;
+    float2 rot;           // exp(-j 2 pi f0 / fs)
+    const float2 *tw;     // [ns] exp(-2 pi i k / ns)
 };
 
 // One (frame, mode) image through the analytic-signal envelope along z.
@@ -122,6 +143,9 @@ struct LogJob {
 cudaError_t launch_plan(const PlanJob &job, int *err_dev, cudaStream_t stream);
 cudaError_t launch_ingest(const IngestJob *jobs_dev, const int *row_prefix_dev, int njobs,
                           int total_rows, int prec, cudaStream_t stream);
+cudaError_t launch_demod(const DemodJob *jobs_dev, const int *row_prefix_dev, int njobs,
+                         int total_rows, int max_ns, cudaStream_t stream);
+size_t demod_smem_bytes(int ns);
 cudaError_t launch_beamform(const BfJob *jobs_dev, const int *tile_prefix_dev, int njobs,
                             int total_tiles, size_t smem_bytes, int prec, int variant, int rows,
                             int *err_dev, cudaStream_t stream);
@@ -139,6 +163,11 @@ int envelope_cols_per_block(int fft_m);
 size_t envelope_smem_bytes(int fft_m, int bluestein);
 
 // Bytes of one stored sample pair for a precision.
-inline int pair_bytes(int prec) { return prec == kPrecF32 ? 8 : 4; }
+inline int pair_bytes(int prec) { return prec == kPrecIQ ? 16 : prec == kPrecF32 ? 8 : 4; }
+// Largest TMA box of staged pairs (a box spans at most 256 elements of 8 bytes
+// for FP32 and IQ pairs, 4 bytes for FP16 / BF16).
+inline int max_box_pairs(int prec) { return prec == kPrecIQ ? 128 : 256; }
+// Tensor-map elements per staged pair.
+inline int pair_elems(int prec) { return prec == kPrecIQ ? 2 : 1; }
 
 }  // namespace bfi

@@ -276,6 +276,45 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestJob *__restrict
 // Shared memory of one CTA: the mbarrier ring and window starts, then
 // kStages stages, each holding the tile's per-(channel, column) tables of one
 // channel group and the channels' record windows.
+// --------------------------------------------------------- demodulation --
+
+// One channel record per CTA: analytic signal by a length-ns transform pair
+// (one-sided spectrum: H = 1 at 0 and ns/2, 2 between, 0 above), then the
+// complex interpolation pairs of the IQ beamformer.
+__global__ void __launch_bounds__(256) demod_kernel(const DemodJob *__restrict__ jobs,
+                                                    const int *__restrict__ row_prefix, int njobs)
+{
+    extern __shared__ __align__(16) float2 dbuf[];
+    const int jb = find_job(row_prefix, njobs, blockIdx.x);
+    const DemodJob J = jobs[jb];
+    const int row = blockIdx.x - __ldg(row_prefix + jb);
+    const int m = J.ns, lgm = J.lgn;
+    float2 *X = dbuf, *Y = dbuf + m, *tw = dbuf + 2 * (size_t)m;
+    const int16_t *__restrict__ u = J.rf + (size_t)row * m;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        tw[k] = __ldg(J.tw + k);
+        X[k] = make_float2((float)__ldg(u + k), 0.f);
+    }
+    __syncthreads();
+    float2 *S = fft_r4(X, Y, m, lgm, 1, tw, false);
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        const float h = (k == 0 || 2 * k == m) ? 1.f : (2 * k < m ? 2.f : 0.f);
+        S[k] = make_float2(S[k].x * h, S[k].y * h);
+    }
+    __syncthreads();
+    float2 *A = fft_r4(S, S == X ? Y : X, m, lgm, 1, tw, true);  // m * analytic signal
+    const float inv = 1.f / (float)m;
+    float4 *__restrict__ out = J.pairs + (size_t)row * J.nsp;
+    for (int j = threadIdx.x; j < J.nsp; j += blockDim.x) {
+        const int k = j - kPadL;
+        const float2 a0 = (k >= 0 && k < m) ? A[k] : make_float2(0.f, 0.f);
+        const float2 a1 = (k + 1 >= 0 && k + 1 < m) ? A[k + 1] : make_float2(0.f, 0.f);
+        const float2 b = cmul(a1, J.rot);
+        out[j] = make_float4(0.5f * (a0.x + b.x) * inv, 0.5f * (a0.y + b.y) * inv, (b.x - a0.x) * inv,
+                             (b.y - a0.y) * inv);
+    }
+}
+
 struct SmemHeader {
     uint64_t full[kStages];   // producer -> consumers: the stage's copies have landed
     uint64_t empty[kStages];  // consumers -> producer: every consumer warp is done with it
@@ -416,6 +455,53 @@ __device__ __forceinline__ void accumulate2(uint32_t win0, int w00, float d20, u
     }
 }
 
+__device__ __forceinline__ float4 lds_f32x4(uint32_t addr)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr));
+    return v;
+}
+
+// One channel of IQ beamforming into the ROWS pixels of this thread.  The
+// staged pair holds mid = (A + B) / 2, diff = B - A of the analytic samples
+// A = a[k], B = a[k + 1] exp(-j 2 pi r) (r = f0 / fs), so that
+//   s = exp(j 2 pi r alpha) (mid + (alpha - 1/2) diff)
+// is the baseband sample interpolated at n = k + alpha with its carrier
+// exp(j 2 pi r n) restored.  IQ-DAS sums s; BB-DMAS (BB) sums
+// s / sqrt|s| = sqrt|s| exp(j arg s) per angle.
+template <bool BB, int ROWS, bool CHECK>
+__device__ __forceinline__ void accumulate_iq(uint32_t win, int wmax, int w0, float d2, int2 vr,
+                                              int r_first, const float *Z, const float *fp,
+                                              const int *Kc, float c1, float c2, float *Yr,
+                                              float *Yi, float *Tr, float *Ti)
+{
+    const unsigned span = (unsigned)(vr.y - vr.x);
+#pragma unroll
+    for (int j = 0; j < ROWS; ++j) {
+        const float x = rx_excess(d2, Z[j]) + fp[j];
+        const float m = x + kRoundMagic;
+        const float al = x - (m - kRoundMagic);  // alpha - 1/2
+        const unsigned idx = min((unsigned)(__float_as_int(m) + Kc[j] - w0), (unsigned)(wmax - 1));
+        const float4 p = lds_f32x4(win + idx * 16u);
+        const float br = fmaf(al, p.z, p.x), bi = fmaf(al, p.w, p.y);
+        float sn, cs;
+        __sincosf(fmaf(al, c1, c2), &sn, &cs);
+        const float sr = fmaf(br, cs, -bi * sn), si = fmaf(br, sn, bi * cs);
+        if (!CHECK || (unsigned)(r_first + j - vr.x) <= span) {
+            Yr[j] += sr;
+            Yi[j] += si;
+            if (BB) {
+                // |s|^(-1/2); the floor keeps s = 0 at 0 instead of 0 * inf
+                const float w = rsqrt_approx(sqrt_approx(fmaf(sr, sr, fmaf(si, si, 1e-30f))));
+                Tr[j] = fmaf(sr, w, Tr[j]);
+                Ti[j] = fmaf(si, w, Ti[j]);
+            }
+        }
+    }
+}
+
 template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS>
 __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_kernel(const BfJob *__restrict__ jobs,
                                                                     const int *__restrict__ tile_prefix,
@@ -423,7 +509,9 @@ __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_ker
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     SmemHeader &sh = *reinterpret_cast<SmemHeader *>(smem);
-    constexpr int PB = PairIO<PREC>::kBytes;
+    constexpr bool IQ = PREC == kPrecIQ;
+    constexpr int PB = IQ ? 16 : PairIO<IQ ? kPrecF32 : PREC>::kBytes;
+    constexpr int XS = IQ ? 2 : 1;  // tensor-map elements per staged pair
 
     // ---- which frame and tile
     const int jb = find_job(tile_prefix, njobs, blockIdx.x);
@@ -496,7 +584,7 @@ __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_ker
                 unsigned char *dst = base + (size_t)G * kTileCols * 12 + (size_t)lane * wmax * PB;
                 const int row = a * ne + i0 + lane;
                 for (int off = 0; off < wmax; off += box)
-                    tma_2d(dst + (size_t)off * PB, rf_map, w0 + off, row, &sh.full[st]);
+                    tma_2d(dst + (size_t)off * PB, rf_map, (w0 + off) * XS, row, &sh.full[st]);
             }
             wf = wf_next;
         }
@@ -525,6 +613,19 @@ __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_ker
     }
     const float pdas_p = J->pdas_p, inv_p = J->pdas_inv_p;
     const bool square = pdas_p == 2.0f;  // uniform over the launch
+    // IQ: S1 / Y1i the IQ-DAS sum, T1 / Ti the per-angle BB-DMAS sum, Yd / Y2i BB-DMAS
+    float Y1i[ROWS], Ti[ROWS], Y2i[ROWS], invM[ROWS];
+    const float c1 = J->iq_c1, c2 = J->iq_c2;
+#pragma unroll
+    for (int j = 0; j < ROWS; ++j) {
+        Y1i[j] = Ti[j] = Y2i[j] = 0.f;
+        invM[j] = 0.f;
+        if (IQ && DMAS) {
+            const int izc = min(r_first + j, nz - 1);
+            const float m = (float)__ldg(J->apcnt + (size_t)ixc * nz + izc);
+            invM[j] = m > 0.f ? 1.f / m : 0.f;
+        }
+    }
 
     bool ok = true;
 #pragma unroll 1
@@ -539,7 +640,7 @@ __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_ker
                 const int izc = min(r_first + j, nz - 1);
                 Kc[j] = ck + __ldg(rowK + a * nz + izc) + kPadL - kRoundBits;
                 fp[j] = cf + __ldg(rowF + a * nz + izc) - 0.5f;
-                T1[j] = T2[j] = P1[j] = 0.f;
+                T1[j] = T2[j] = P1[j] = Ti[j] = 0.f;
             }
         }
         ok = mbar_wait(&sh.full[st], (unsigned)(use & 1), deadline, err);
@@ -559,36 +660,54 @@ __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_ker
                 continue;  // no pixel of this warp's row band counts the channel
             const float d2 = lds_f32(d2b + (uint32_t)c * (kTileCols * 4));
             const uint32_t win = wins + (uint32_t)(c * wmax * PB);
-            if ((bands & 0x100u) && c + 1 < gs) {
-                const int2 wf1 = lds_int2(wfb + (uint32_t)(c + 1) * 8);
-                if (((unsigned)wf1.y >> warp) & 0x100u) {  // two fully counted channels
-                    accumulate2<PREC, DMAS, CF, PDAS, ROWS>(
-                        win, wf.x, d2, win + (uint32_t)(wmax * PB), wf1.x,
-                        lds_f32(d2b + (uint32_t)(c + 1) * (kTileCols * 4)), wmax, Z, fp, Kc, S1,
-                        T1, T2, Su2, P1,
-                        inv_p, square);
-                    ++c;
-                    continue;
-                }
-            }
-            if (bands & 0x100u) {  // every pixel of the band counts it
-                accumulate<PREC, DMAS, CF, PDAS, ROWS, false>(win, wmax, wf.x, d2,
-                                                              make_int2(0, 0), r_first, Z, fp, Kc,
-                                                              S1, T1, T2, Su2, P1, inv_p, square);
+            if constexpr (IQ) {
+                if (bands & 0x100u)
+                    accumulate_iq<DMAS, ROWS, false>(win, wmax, wf.x, d2, make_int2(0, 0), r_first,
+                                                     Z, fp, Kc, c1, c2, S1, Y1i, T1, Ti);
+                else
+                    accumulate_iq<DMAS, ROWS, true>(win, wmax, wf.x, d2,
+                                                    lds_int2(vrb + (uint32_t)c * (kTileCols * 8)),
+                                                    r_first, Z, fp, Kc, c1, c2, S1, Y1i, T1, Ti);
             } else {
-                const int2 vr = lds_int2(vrb + (uint32_t)c * (kTileCols * 8));  // (-1, -1): no row counts
-                accumulate<PREC, DMAS, CF, PDAS, ROWS, true>(win, wmax, wf.x, d2, vr, r_first, Z,
-                                                             fp, Kc, S1, T1, T2, Su2, P1, inv_p,
-                                                             square);
+                if ((bands & 0x100u) && c + 1 < gs) {
+                    const int2 wf1 = lds_int2(wfb + (uint32_t)(c + 1) * 8);
+                    if (((unsigned)wf1.y >> warp) & 0x100u) {  // two fully counted channels
+                        accumulate2<PREC, DMAS, CF, PDAS, ROWS>(
+                            win, wf.x, d2, win + (uint32_t)(wmax * PB), wf1.x,
+                            lds_f32(d2b + (uint32_t)(c + 1) * (kTileCols * 4)), wmax, Z, fp, Kc, S1,
+                            T1, T2, Su2, P1,
+                            inv_p, square);
+                        ++c;
+                        continue;
+                    }
+                }
+                if (bands & 0x100u) {  // every pixel of the band counts it
+                    accumulate<PREC, DMAS, CF, PDAS, ROWS, false>(win, wmax, wf.x, d2,
+                                                                  make_int2(0, 0), r_first, Z, fp, Kc,
+                                                                  S1, T1, T2, Su2, P1, inv_p, square);
+                } else {
+                    const int2 vr = lds_int2(vrb + (uint32_t)c * (kTileCols * 8));  // (-1, -1): no row counts
+                    accumulate<PREC, DMAS, CF, PDAS, ROWS, true>(win, wmax, wf.x, d2, vr, r_first, Z,
+                                                                 fp, Kc, S1, T1, T2, Su2, P1, inv_p,
+                                                                 square);
+                }
             }
         }
         __syncwarp();
         if (lane == 0)
             mbar_arrive(&sh.empty[st]);
-        if (DMAS && g == ngroups - 1) {
+        if (DMAS && !IQ && g == ngroups - 1) {
 #pragma unroll
             for (int j = 0; j < ROWS; ++j)
                 Yd[j] = fmaf(0.5f * T1[j], T1[j], fmaf(-0.5f, T2[j], Yd[j]));
+        }
+        if (DMAS && IQ && g == ngroups - 1) {  // Eq. (4): ((1/M) sum s^)^2 per angle
+#pragma unroll
+            for (int j = 0; j < ROWS; ++j) {
+                const float ur = T1[j] * invM[j], ui = Ti[j] * invM[j];
+                Yd[j] += fmaf(ur, ur, -ui * ui);
+                Y2i[j] = fmaf(2.f * ur, ui, Y2i[j]);
+            }
         }
         if (PDAS && g == ngroups - 1) {  // Eq. (3) per angle, then the coherent sum
 #pragma unroll
@@ -597,6 +716,44 @@ __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_ker
         }
     }
 
+    if constexpr (IQ) {  // magnitude images (and their maxima for the log stage)
+        const size_t plane = (size_t)nx * nz;
+        float *__restrict__ y = J->y;
+        const int modes = J->modes;
+        float m0 = 0.f, m1 = 0.f;
+        if (ok && col_ok) {
+#pragma unroll
+            for (int j = 0; j < ROWS; ++j) {
+                const int iz = r_first + j;
+                if (iz >= nz)
+                    break;
+                const size_t o = (size_t)ix * nz + iz;
+                int slot = 0;
+                if (modes & BF_DAS) {
+                    const float v = sqrtf(fmaf(S1[j], S1[j], Y1i[j] * Y1i[j]));
+                    y[(size_t)(slot++) * plane + o] = v;
+                    m0 = fmaxf(m0, v);
+                }
+                if (modes & BF_DMAS) {
+                    const float v = sqrtf(fmaf(Yd[j], Yd[j], Y2i[j] * Y2i[j]));
+                    y[(size_t)(slot++) * plane + o] = v;
+                    m1 = fmaxf(m1, v);
+                }
+            }
+        }
+        if (J->maxbits) {  // uniform per launch; every lane of the warp is here
+            const unsigned r0 = __reduce_max_sync(0xffffffffu, __float_as_uint(m0));
+            const unsigned r1 = __reduce_max_sync(0xffffffffu, __float_as_uint(m1));
+            if (lane == 0) {
+                int slot = 0;
+                if (modes & BF_DAS)
+                    atomicMax(J->maxbits + slot++, r0);
+                if (modes & BF_DMAS)
+                    atomicMax(J->maxbits + slot, r1);
+            }
+        }
+        return;
+    }
     if (!ok || !col_ok)
         return;
     const int modes = J->modes;
@@ -968,6 +1125,26 @@ cudaError_t launch_ingest(const IngestJob *jobs_dev, const int *row_prefix_dev, 
     return cudaGetLastError();
 }
 
+size_t demod_smem_bytes(int ns) { return (size_t)3 * ns * sizeof(float2); }
+
+cudaError_t launch_demod(const DemodJob *jobs_dev, const int *row_prefix_dev, int njobs,
+                         int total_rows, int max_ns, cudaStream_t stream)
+{
+    if (njobs <= 0 || total_rows <= 0)
+        return cudaSuccess;
+    const size_t smem = demod_smem_bytes(max_ns);
+    static size_t configured = 0;
+    if (smem > 48u * 1024u && smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(demod_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        configured = smem;
+    }
+    demod_kernel<<<total_rows, 256, smem, stream>>>(jobs_dev, row_prefix_dev, njobs);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_beamform(const BfJob *jobs_dev, const int *tile_prefix_dev, int njobs,
                             int total_tiles, size_t smem_bytes, int prec, int variant, int rows,
                             int *err_dev, cudaStream_t stream)
@@ -976,6 +1153,17 @@ cudaError_t launch_beamform(const BfJob *jobs_dev, const int *tile_prefix_dev, i
         return cudaSuccess;
     const int dmas = (variant & BF_DMAS) ? 1 : 0, cf = (variant & BF_CF) ? 1 : 0;
     const int pdas = (variant & BF_PDAS) ? 1 : 0;
+    if (prec == kPrecIQ) {  // IQ-DAS always, BB-DMAS in the DMAS slot
+        if (rows == 4)
+            return dmas ? launch_bf_t<kPrecIQ, true, false, false, 4>(jobs_dev, tile_prefix_dev, njobs,
+                                                                     total_tiles, smem_bytes, err_dev, stream)
+                        : launch_bf_t<kPrecIQ, false, false, false, 4>(jobs_dev, tile_prefix_dev, njobs,
+                                                                      total_tiles, smem_bytes, err_dev, stream);
+        return dmas ? launch_bf_t<kPrecIQ, true, false, false, 8>(jobs_dev, tile_prefix_dev, njobs,
+                                                                 total_tiles, smem_bytes, err_dev, stream)
+                    : launch_bf_t<kPrecIQ, false, false, false, 8>(jobs_dev, tile_prefix_dev, njobs,
+                                                                  total_tiles, smem_bytes, err_dev, stream);
+    }
     if (prec == kPrecF32)
         return launch_bf_p<kPrecF32>(jobs_dev, tile_prefix_dev, njobs, total_tiles, smem_bytes,
                                      dmas, cf, pdas, rows, err_dev, stream);

@@ -177,7 +177,8 @@ void angle_tables(const GeomHost &g, const GeometryHost &geo, int ns,
     // destination of a tensor copy (channel stride wmax, box offsets) stays
     // 128-byte aligned; start coordinates are 16-byte aligned (align pairs).
     const int box_align = 128 / pair_bytes(prec);
-    int nb = (span + kMaxBox - 1) / kMaxBox;
+    const int maxbox = max_box_pairs(prec);
+    int nb = (span + maxbox - 1) / maxbox;
     int box = (span + nb - 1) / nb;
     box = (box + box_align - 1) / box_align * box_align;
     out.box = box;
