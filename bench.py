@@ -53,7 +53,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--workload", default="cyst512",
-                   choices=["cyst512", "batch256", "serving", "precision", "sweep"],
+                   choices=["cyst512", "batch256", "serving", "precision", "sweep", "iq"],
                    help="cyst512: the headline line; the others print informational lines")
     p.add_argument("--requests", type=int, default=2000, help="serving: requests per rate")
     return p.parse_args()
@@ -460,6 +460,63 @@ def run_batch256(args):
         bf.bf_destroy(h)
 
 
+def run_iq(args):
+    """IQ-DAS + BB-DMAS (Eq. (4)) of the 512x512 workload, 64 frames in one graph,
+    log-compressed magnitude images; rel-L2 of one frame against the oracle."""
+    import oracle
+
+    torch, bf = _setup_gpu()
+    acq, rfs = frames_rf(4)
+    B = args.frames
+    h = _handle(bf, acq)
+    flags = bf.BF_IQDAS | bf.BF_BBDMAS | bf.BF_OUT_LOGDB
+    tune = bf.bf_autotune(h, acq.n_samples, acq.angles_rad, flags, frames=16)
+    rf_dev = [torch.from_numpy(rfs[k % len(rfs)]).cuda() for k in range(B)]
+    out_dev = [torch.empty((2, acq.nx, acq.nz), dtype=torch.float32, device="cuda") for _ in range(B)]
+    batch = bf.Batch([(h, rf_dev[k], acq.n_samples, acq.angles_rad, flags, out_dev[k])
+                      for k in range(B)])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        batch.launch(st)
+    torch.cuda.synchronize()
+    times, split = [], []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        batch.launch(st)
+        b.record(st)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+        split.append(batch.timing()[0])
+    batch.status(st)
+    t = sum(times) / 1e3
+    # accuracy of the beamformed magnitudes on sampled pixels of one frame
+    out = torch.empty((2, acq.nx, acq.nz), dtype=torch.float32, device="cuda")
+    bf.bf_beamform(h, rf_dev[0], acq.n_samples, acq.angles_rad, bf.BF_IQDAS | bf.BF_BBDMAS, out)
+    bf.bf_sync(h)
+    pix = np.random.default_rng(3).integers(0, acq.nx * acq.nz, 20000)
+    iq = oracle.demodulate(rfs[0], acq.fs_hz, acq.f0_hz)
+    ref = oracle.beamform_iq(iq, acq.x_elements(), acq.angles_rad, grid_of(acq), acq.fs_hz,
+                             acq.c_mps, acq.f_number, acq.f0_hz, pixels=pix)
+    got = out.cpu().numpy().reshape(2, -1)[:, pix].astype(np.float64)
+    err = {name: float(np.linalg.norm(got[k] - ref[name]) / np.linalg.norm(ref[name]))
+           for k, name in enumerate(("iqdas", "bbdmas"))}
+    batch.close()
+    bf.bf_destroy(h)
+    print(json.dumps({"workload": "IQ-DAS + BB-DMAS, cyst+wires 512x512 px, 64 ch, 2048 samples, 0 deg, "
+                                  "demodulation + beamforming + log, %d frames per graph" % B,
+                      "gpixel_ch_per_s": args.steps * B * nominal_units(acq) / t / 1e9,
+                      "frames_per_s": args.steps * B / t, "ms_per_step": 1e3 * t / args.steps,
+                      "kernel_ms": {"demod": statistics.median(x[0] for x in split),
+                                    "beamform": statistics.median(x[1] for x in split),
+                                    "log": statistics.median(x[2] for x in split)},
+                      "tile": tune, "rel_l2": err,
+                      "rel_l2_sample": "20000 random pixels of one frame vs the FP64 oracle"}),
+          flush=True)
+
+
 def run_precision(args):
     """1024x1024, 128 elements, 4096 samples, 7 angles: time per frame and rel-L2 per storage."""
     import oracle
@@ -676,6 +733,8 @@ def main():
         run_batch256(args)
     elif args.workload == "precision":
         run_precision(args)
+    elif args.workload == "iq":
+        run_iq(args)
     elif args.workload == "sweep":
         run_sweep(args)
     elif args.workload == "serving":
