@@ -319,8 +319,12 @@ struct SmemHeader {
     uint64_t full[kStages];   // producer -> consumers: the stage's copies have landed
     uint64_t empty[kStages];  // consumers -> producer: every consumer warp is done with it
     int2 wf[kStages][kMaxGroup];  // (window start, band flags) per staged channel
+    // per row band (consumer warp): the stage's channels that every pixel of the
+    // band counts, then those that only some pixels count
+    uint8_t list[kStages][kWarps][kMaxGroup];
+    uint8_t nfull[kStages][kWarps], ntot[kStages][kWarps];
 };
-constexpr int kHeaderBytes = 512;
+constexpr int kHeaderBytes = 1024;
 static_assert(sizeof(SmemHeader) <= kHeaderBytes, "header");
 
 // Sample pairs read from shared memory through 32-bit shared-window addresses.
@@ -565,6 +569,25 @@ __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_ker
             const bool mine = lane < G && i0 + lane < ne;
             if (mine)
                 sh.wf[st][lane] = wf;
+            {  // channel lists of every row band (lane = channel of the group)
+                const unsigned fl = (mine && wf.x != kNoWindow) ? (unsigned)wf.y : 0u;
+                const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+                for (int b = 0; b < kWarps; ++b) {
+                    const bool full = (fl >> (8 + b)) & 1u;
+                    const bool part = !full && ((fl >> b) & 1u);
+                    const unsigned fm = __ballot_sync(0xffffffffu, full);
+                    const unsigned pm = __ballot_sync(0xffffffffu, part);
+                    if (full)
+                        sh.list[st][b][__popc(fm & lt)] = (uint8_t)lane;
+                    else if (part)
+                        sh.list[st][b][__popc(fm) + __popc(pm & lt)] = (uint8_t)lane;
+                    if (lane == 0) {
+                        sh.nfull[st][b] = (uint8_t)__popc(fm);
+                        sh.ntot[st][b] = (uint8_t)(__popc(fm) + __popc(pm));
+                    }
+                }
+            }
             const int w0 = wf.x;
             const unsigned bytes = (mine && w0 != kNoWindow) ? (unsigned)(wmax * PB) : 0u;
             unsigned total = bytes;
@@ -651,46 +674,50 @@ __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_ker
         const uint32_t d2b = base + (uint32_t)G * kTileCols * 8 + (uint32_t)lane * 4;  // float [G][32]
         const uint32_t wins = base + (uint32_t)G * kTileCols * 12;
         const uint32_t wfb = smem_u32(&sh.wf[st][0]);
-        const int gs = min(G, ne - g * G);
+        const int nf = sh.nfull[st][warp], nt = sh.ntot[st][warp];
+        const uint8_t *L = sh.list[st][warp];
+        auto win_of = [&](int c) { return wins + (uint32_t)(c * wmax * PB); };
+        auto w0_of = [&](int c) { return lds_int2(wfb + (uint32_t)c * 8).x; };
+        auto d2_of = [&](int c) { return lds_f32(d2b + (uint32_t)c * (kTileCols * 4)); };
+        auto vr_of = [&](int c) { return lds_int2(vrb + (uint32_t)c * (kTileCols * 8)); };
+        int k = 0;
+        if constexpr (IQ) {
 #pragma unroll 1
-        for (int c = 0; c < gs; ++c) {
-            const int2 wf = lds_int2(wfb + (uint32_t)c * 8);
-            const unsigned bands = (unsigned)wf.y >> warp;
-            if (!(bands & 1u))
-                continue;  // no pixel of this warp's row band counts the channel
-            const float d2 = lds_f32(d2b + (uint32_t)c * (kTileCols * 4));
-            const uint32_t win = wins + (uint32_t)(c * wmax * PB);
-            if constexpr (IQ) {
-                if (bands & 0x100u)
-                    accumulate_iq<DMAS, ROWS, false>(win, wmax, wf.x, d2, make_int2(0, 0), r_first,
-                                                     Z, fp, Kc, c1, c2, S1, Y1i, T1, Ti);
-                else
-                    accumulate_iq<DMAS, ROWS, true>(win, wmax, wf.x, d2,
-                                                    lds_int2(vrb + (uint32_t)c * (kTileCols * 8)),
-                                                    r_first, Z, fp, Kc, c1, c2, S1, Y1i, T1, Ti);
-            } else {
-                if ((bands & 0x100u) && c + 1 < gs) {
-                    const int2 wf1 = lds_int2(wfb + (uint32_t)(c + 1) * 8);
-                    if (((unsigned)wf1.y >> warp) & 0x100u) {  // two fully counted channels
-                        accumulate2<PREC, DMAS, CF, PDAS, ROWS>(
-                            win, wf.x, d2, win + (uint32_t)(wmax * PB), wf1.x,
-                            lds_f32(d2b + (uint32_t)(c + 1) * (kTileCols * 4)), wmax, Z, fp, Kc, S1,
-                            T1, T2, Su2, P1,
-                            inv_p, square);
-                        ++c;
-                        continue;
-                    }
-                }
-                if (bands & 0x100u) {  // every pixel of the band counts it
-                    accumulate<PREC, DMAS, CF, PDAS, ROWS, false>(win, wmax, wf.x, d2,
-                                                                  make_int2(0, 0), r_first, Z, fp, Kc,
-                                                                  S1, T1, T2, Su2, P1, inv_p, square);
-                } else {
-                    const int2 vr = lds_int2(vrb + (uint32_t)c * (kTileCols * 8));  // (-1, -1): no row counts
-                    accumulate<PREC, DMAS, CF, PDAS, ROWS, true>(win, wmax, wf.x, d2, vr, r_first, Z,
-                                                                 fp, Kc, S1, T1, T2, Su2, P1, inv_p,
-                                                                 square);
-                }
+            for (; k < nf; ++k) {
+                const int c = L[k];
+                accumulate_iq<DMAS, ROWS, false>(win_of(c), wmax, w0_of(c), d2_of(c),
+                                                 make_int2(0, 0), r_first, Z, fp, Kc, c1, c2, S1,
+                                                 Y1i, T1, Ti);
+            }
+#pragma unroll 1
+            for (; k < nt; ++k) {
+                const int c = L[k];
+                accumulate_iq<DMAS, ROWS, true>(win_of(c), wmax, w0_of(c), d2_of(c), vr_of(c),
+                                                r_first, Z, fp, Kc, c1, c2, S1, Y1i, T1, Ti);
+            }
+        } else {
+            // channels every pixel of the band counts, two at a time (twice the
+            // independent dependency chains per thread), then the rest with a
+            // per-pixel row test
+#pragma unroll 1
+            for (; k + 1 < nf; k += 2) {
+                const int c0 = L[k], c1 = L[k + 1];
+                accumulate2<PREC, DMAS, CF, PDAS, ROWS>(win_of(c0), w0_of(c0), d2_of(c0), win_of(c1),
+                                                        w0_of(c1), d2_of(c1), wmax, Z, fp, Kc, S1,
+                                                        T1, T2, Su2, P1, inv_p, square);
+            }
+            if (k < nf) {
+                const int c = L[k++];
+                accumulate<PREC, DMAS, CF, PDAS, ROWS, false>(win_of(c), wmax, w0_of(c), d2_of(c),
+                                                              make_int2(0, 0), r_first, Z, fp, Kc,
+                                                              S1, T1, T2, Su2, P1, inv_p, square);
+            }
+#pragma unroll 1
+            for (; k < nt; ++k) {
+                const int c = L[k];
+                accumulate<PREC, DMAS, CF, PDAS, ROWS, true>(win_of(c), wmax, w0_of(c), d2_of(c),
+                                                             vr_of(c), r_first, Z, fp, Kc, S1, T1,
+                                                             T2, Su2, P1, inv_p, square);
             }
         }
         __syncwarp();
