@@ -563,6 +563,10 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
             e.chirp = (const float2 *)f.et->chirp.p;
             e.bhat = (const float2 *)f.et->bhat.p;
             e.cols_per_block = e.bluestein ? 1 : envelope_cols_per_block(e.fft_m);
+            e.vec4 = (!e.bluestein && e.nz % 4 == 0 && ((uintptr_t)e.y & 15) == 0 &&
+                      ((uintptr_t)e.env & 15) == 0)
+                         ? 1
+                         : 0;
             hl.env_prefix.push_back(cols);
             cols += (h->g.nx + e.cols_per_block - 1) / e.cols_per_block;
             hl.env.push_back(e);

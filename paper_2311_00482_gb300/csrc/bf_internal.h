@@ -123,6 +123,7 @@ struct EnvJob {
     int band;             // 1: keep only bins [kb_lo, kb_hi] (DMAS second-harmonic band-pass)
     int kb_lo, kb_hi;
     int cols_per_block;   // image columns transformed together by one CTA
+    int vec4;             // 1: y and env are 16-byte aligned and nz a multiple of 4 (vector access)
     const float2 *tw;     // [fft_m] exp(-2 pi i k / fft_m)
     const float2 *chirp;  // [nz] exp(i pi n^2 / nz)              (Bluestein only)
     const float2 *bhat;   // [fft_m] DFT of the chirp convolution kernel (Bluestein only)

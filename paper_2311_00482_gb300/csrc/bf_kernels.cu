@@ -17,7 +17,7 @@
 //                    (DAS, signed-sqrt DMAS, coherence factor, pDAS), compounded over
 //                    angles (Eq. (1), Sec. II-B)
 //   envelope_kernel  per image column the analytic signal along depth via a
-//                    shared-memory radix-2 Stockham FFT (Bluestein for other
+//                    shared-memory radix-8 Stockham FFT (Bluestein for other
 //                    lengths), one-sided mask and optional [f0, 3 f0]
 //                    band-pass, magnitude, and the frame maximum
 //   log_kernel       20 log10(env / max) clipped to the -70 dB range of Fig. 3
@@ -296,13 +296,13 @@ __global__ void __launch_bounds__(256) demod_kernel(const DemodJob *__restrict__
         X[k] = make_float2((float)__ldg(u + k), 0.f);
     }
     __syncthreads();
-    float2 *S = fft_r4(X, Y, m, lgm, 1, tw, false);
+    float2 *S = fft_r8(X, Y, m, lgm, 1, tw, false);
     for (int k = threadIdx.x; k < m; k += blockDim.x) {
         const float h = (k == 0 || 2 * k == m) ? 1.f : (2 * k < m ? 2.f : 0.f);
         S[k] = make_float2(S[k].x * h, S[k].y * h);
     }
     __syncthreads();
-    float2 *A = fft_r4(S, S == X ? Y : X, m, lgm, 1, tw, true);  // m * analytic signal
+    float2 *A = fft_r8(S, S == X ? Y : X, m, lgm, 1, tw, true);  // m * analytic signal
     const float inv = 1.f / (float)m;
     float4 *__restrict__ out = J.pairs + (size_t)row * J.nsp;
     for (int j = threadIdx.x; j < J.nsp; j += blockDim.x) {
@@ -912,15 +912,26 @@ __global__ void __launch_bounds__(256) envelope_kernel(const EnvJob *__restrict_
         float2 *tw = sbuf + (size_t)3 * C * m;
         for (int k = threadIdx.x; k < m; k += blockDim.x)
             tw[k] = __ldg(J.tw + k);
-        for (int t = threadIdx.x; t < C * m; t += blockDim.x) {
+        // columns in: four depths per thread and 16-byte accesses (m >= 4: nz = m)
+        const int vec = J.vec4 ? 4 : 1;
+        for (int t = threadIdx.x * vec; t < C * m; t += blockDim.x * vec) {
             const int c = t >> lgm, n = t & (m - 1);
             const int ca = c0 + 2 * c, cb = ca + 1;
-            const float ya = ca < J.nx ? __ldg(J.y + (size_t)ca * nz + n) : 0.f;
-            const float yb = cb < J.nx ? __ldg(J.y + (size_t)cb * nz + n) : 0.f;
-            Zb[t] = make_float2(ya, yb);
+            if (vec == 4) {
+                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 a = ca < J.nx ? __ldg(reinterpret_cast<const float4 *>(J.y + (size_t)ca * nz + n)) : z4;
+                const float4 b = cb < J.nx ? __ldg(reinterpret_cast<const float4 *>(J.y + (size_t)cb * nz + n)) : z4;
+                float4 *z = reinterpret_cast<float4 *>(Zb + t);
+                z[0] = make_float4(a.x, b.x, a.y, b.y);
+                z[1] = make_float4(a.z, b.z, a.w, b.w);
+            } else {
+                const float ya = ca < J.nx ? __ldg(J.y + (size_t)ca * nz + n) : 0.f;
+                const float yb = cb < J.nx ? __ldg(J.y + (size_t)cb * nz + n) : 0.f;
+                Zb[t] = make_float2(ya, yb);
+            }
         }
         __syncthreads();
-        float2 *S = fft_r4(Zb, Pb, m, lgm, C, tw, false);  // spectrum of a + i b
+        float2 *S = fft_r8(Zb, Pb, m, lgm, C, tw, false);  // spectrum of a + i b
         float2 *F1 = S == Zb ? Pb : Zb;                    // free buffer
         const float inv = 1.f / (float)m;
         if (!J.band) {
@@ -930,10 +941,29 @@ __global__ void __launch_bounds__(256) envelope_kernel(const EnvJob *__restrict_
                 F1[t] = make_float2(S[t].y * sg, -S[t].x * sg);  // -i sgn(k) S
             }
             __syncthreads();
-            const float2 *Hh = fft_r4(F1, S, m, lgm, C, tw, true);
-            for (int t = threadIdx.x; t < C * m; t += blockDim.x) {
+            const float2 *Hh = fft_r8(F1, S, m, lgm, C, tw, true);
+            for (int t = threadIdx.x * vec; t < C * m; t += blockDim.x * vec) {
                 const int c = t >> lgm, n = t & (m - 1);
                 const int ca = c0 + 2 * c, cb = ca + 1;
+                if (vec == 4) {
+                    const float4 h01 = *reinterpret_cast<const float4 *>(Hh + t);
+                    const float4 h23 = *reinterpret_cast<const float4 *>(Hh + t + 2);
+                    if (ca < J.nx) {
+                        const float4 a = __ldg(reinterpret_cast<const float4 *>(J.y + (size_t)ca * nz + n));
+                        const float4 e = make_float4(hypotf(a.x, h01.x * inv), hypotf(a.y, h01.z * inv),
+                                                     hypotf(a.z, h23.x * inv), hypotf(a.w, h23.z * inv));
+                        *reinterpret_cast<float4 *>(J.env + (size_t)ca * nz + n) = e;
+                        lmax = fmaxf(lmax, fmaxf(fmaxf(e.x, e.y), fmaxf(e.z, e.w)));
+                    }
+                    if (cb < J.nx) {
+                        const float4 b = __ldg(reinterpret_cast<const float4 *>(J.y + (size_t)cb * nz + n));
+                        const float4 e = make_float4(hypotf(b.x, h01.y * inv), hypotf(b.y, h01.w * inv),
+                                                     hypotf(b.z, h23.y * inv), hypotf(b.w, h23.w * inv));
+                        *reinterpret_cast<float4 *>(J.env + (size_t)cb * nz + n) = e;
+                        lmax = fmaxf(lmax, fmaxf(fmaxf(e.x, e.y), fmaxf(e.z, e.w)));
+                    }
+                    continue;
+                }
                 if (ca < J.nx) {
                     const float e = hypotf(__ldg(J.y + (size_t)ca * nz + n), Hh[t].x * inv);
                     J.env[(size_t)ca * nz + n] = e;
@@ -956,12 +986,31 @@ __global__ void __launch_bounds__(256) envelope_kernel(const EnvJob *__restrict_
                 Qb[t] = make_float2(r.y * sg, -r.x * sg);
             }
             __syncthreads();
-            float2 *R = fft_r4(S, F1, m, lgm, C, tw, true);
+            float2 *R = fft_r8(S, F1, m, lgm, C, tw, true);
             float2 *F2 = R == S ? F1 : S;
-            const float2 *Hh = fft_r4(Qb, F2, m, lgm, C, tw, true);
-            for (int t = threadIdx.x; t < C * m; t += blockDim.x) {
+            const float2 *Hh = fft_r8(Qb, F2, m, lgm, C, tw, true);
+            for (int t = threadIdx.x * vec; t < C * m; t += blockDim.x * vec) {
                 const int c = t >> lgm, n = t & (m - 1);
                 const int ca = c0 + 2 * c, cb = ca + 1;
+                if (vec == 4) {
+                    const float4 r01 = *reinterpret_cast<const float4 *>(R + t);
+                    const float4 r23 = *reinterpret_cast<const float4 *>(R + t + 2);
+                    const float4 h01 = *reinterpret_cast<const float4 *>(Hh + t);
+                    const float4 h23 = *reinterpret_cast<const float4 *>(Hh + t + 2);
+                    if (ca < J.nx) {
+                        const float4 e = make_float4(hypotf(r01.x, h01.x) * inv, hypotf(r01.z, h01.z) * inv,
+                                                     hypotf(r23.x, h23.x) * inv, hypotf(r23.z, h23.z) * inv);
+                        *reinterpret_cast<float4 *>(J.env + (size_t)ca * nz + n) = e;
+                        lmax = fmaxf(lmax, fmaxf(fmaxf(e.x, e.y), fmaxf(e.z, e.w)));
+                    }
+                    if (cb < J.nx) {
+                        const float4 e = make_float4(hypotf(r01.y, h01.y) * inv, hypotf(r01.w, h01.w) * inv,
+                                                     hypotf(r23.y, h23.y) * inv, hypotf(r23.w, h23.w) * inv);
+                        *reinterpret_cast<float4 *>(J.env + (size_t)cb * nz + n) = e;
+                        lmax = fmaxf(lmax, fmaxf(fmaxf(e.x, e.y), fmaxf(e.z, e.w)));
+                    }
+                    continue;
+                }
                 if (ca < J.nx) {
                     const float e = hypotf(R[t].x, Hh[t].x) * inv;
                     J.env[(size_t)ca * nz + n] = e;
@@ -995,12 +1044,12 @@ __global__ void __launch_bounds__(256) envelope_kernel(const EnvJob *__restrict_
             A[n] = v;
         }
         __syncthreads();
-        float2 *X = fft_r4(A, B, m, lgm, 1, tw, false);
+        float2 *X = fft_r8(A, B, m, lgm, 1, tw, false);
         for (int k = threadIdx.x; k < m; k += blockDim.x)
             X[k] = cmul(X[k], __ldg(bh + k));
         __syncthreads();
         float2 *O = X == A ? B : A;
-        float2 *Cb = fft_r4(X, O, m, lgm, 1, tw, true);
+        float2 *Cb = fft_r8(X, O, m, lgm, 1, tw, true);
         float2 *D = Cb == A ? B : A;
         // masked spectrum, conjugated and pre-multiplied by conj(w) for the second
         // pass: the inverse DFT of S is conj(DFT(conj S)) / nz
@@ -1017,11 +1066,11 @@ __global__ void __launch_bounds__(256) envelope_kernel(const EnvJob *__restrict_
             D[k] = v;
         }
         __syncthreads();
-        float2 *E = fft_r4(D, Cb, m, lgm, 1, tw, false);
+        float2 *E = fft_r8(D, Cb, m, lgm, 1, tw, false);
         for (int k = threadIdx.x; k < m; k += blockDim.x)
             E[k] = cmul(E[k], __ldg(bh + k));
         __syncthreads();
-        float2 *F = fft_r4(E, E == A ? B : A, m, lgm, 1, tw, true);
+        float2 *F = fft_r8(E, E == A ? B : A, m, lgm, 1, tw, true);
         const float inv = inv_m / (float)nz;
         float *__restrict__ env = J.env + (size_t)c0 * nz;
         for (int n = threadIdx.x; n < nz; n += blockDim.x) {

@@ -318,3 +318,31 @@ def test_every_counted_sample_lies_in_its_tile_window(torch, shape):
                     continue
                 # pair j holds samples j - 2 and j - 1: samples k, k + 1 are pair k + 2
                 assert w0 <= min(ks) + 2 - 1 and max(ks) + 2 + 1 < w0 + info["wmax"], (a, t, i, w0, min(ks), max(ks))
+
+
+def test_envelope_into_an_unaligned_output_matches(torch):
+    """The envelope stage writes 16-byte vectors only where the destination is
+    16-byte aligned; a destination 4 bytes off takes the scalar path, same values."""
+    acq = synth.SPECKLE_POINTS_128.with_(nx=40, nz=128)
+    rf, _ = synth.speckle_points_frame(acq)
+    flags = bf.BF_DAS | bf.BF_DMAS | bf.BF_OUT_ENV
+    h = make_handle(acq)
+    try:
+        rf_d = torch.from_numpy(rf).cuda()
+        n = 2 * acq.nx * acq.nz
+        aligned = torch.zeros(n, device="cuda")
+        big = torch.zeros(n + 1, device="cuda")
+        shifted = big[1:]
+        assert shifted.data_ptr() % 16 == 4
+        bf.bf_beamform(h, rf_d, acq.n_samples, acq.angles_rad, flags, aligned)
+        bf.bf_beamform(h, rf_d, acq.n_samples, acq.angles_rad, flags, shifted)
+        bf.bf_sync(h)
+        np.testing.assert_array_equal(aligned.cpu().numpy(), shifted.cpu().numpy())
+        ref = oracle_all(acq, rf)
+        dz = (acq.z1_m - acq.z0_m) / (acq.nz - 1)
+        env = aligned.cpu().numpy().reshape(2, acq.nx, acq.nz).astype(np.float64)
+        assert_close(env[0], oracle.envelope(ref["das"]), bf.BF_PREC_FP32, "das env")
+        assert_close(env[1], oracle.envelope(ref["dmas"], bandpass=True, dz=dz, c=acq.c_mps,
+                                             f0=acq.f0_hz), bf.BF_PREC_FP32, "dmas env")
+    finally:
+        bf.bf_destroy(h)
