@@ -538,6 +538,9 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
                 l.out = f.out + slot * img;
                 l.maxbits = f.maxbits + slot;
                 l.n = (int)img;
+                l.vec4 = (img % 4 == 0 && ((uintptr_t)l.env & 15) == 0 && ((uintptr_t)l.out & 15) == 0)
+                             ? 1
+                             : 0;
                 hl.blk_prefix.push_back((int)blks);
                 blks += log_blocks((long long)img);
                 hl.log.push_back(l);
@@ -577,6 +580,9 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
                 l.out = f.out + slot * img;
                 l.maxbits = e.maxbits;
                 l.n = (int)img;
+                l.vec4 = (img % 4 == 0 && ((uintptr_t)l.env & 15) == 0 && ((uintptr_t)l.out & 15) == 0)
+                             ? 1
+                             : 0;
                 hl.blk_prefix.push_back((int)blks);
                 blks += log_blocks((long long)img);
                 hl.log.push_back(l);

@@ -135,6 +135,7 @@ struct LogJob {
     float *out;
     const unsigned *maxbits;
     int n;                // pixels
+    int vec4;             // 1: env and out 16-byte aligned and n a multiple of 4
 };
 
 // Kernel launchers (bf_kernels.cu).  All enqueue on `stream` and return the

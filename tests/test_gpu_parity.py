@@ -338,6 +338,14 @@ def test_envelope_into_an_unaligned_output_matches(torch):
         bf.bf_beamform(h, rf_d, acq.n_samples, acq.angles_rad, flags, shifted)
         bf.bf_sync(h)
         np.testing.assert_array_equal(aligned.cpu().numpy(), shifted.cpu().numpy())
+        # the log stage too (scalar path into the shifted destination)
+        lg = flags & ~bf.BF_OUT_MASK | bf.BF_OUT_LOGDB
+        bf.bf_beamform(h, rf_d, acq.n_samples, acq.angles_rad, lg, aligned)
+        bf.bf_beamform(h, rf_d, acq.n_samples, acq.angles_rad, lg, shifted)
+        bf.bf_sync(h)
+        np.testing.assert_array_equal(aligned.cpu().numpy(), shifted.cpu().numpy())
+        bf.bf_beamform(h, rf_d, acq.n_samples, acq.angles_rad, flags, aligned)
+        bf.bf_sync(h)
         ref = oracle_all(acq, rf)
         dz = (acq.z1_m - acq.z0_m) / (acq.nz - 1)
         env = aligned.cpu().numpy().reshape(2, acq.nx, acq.nz).astype(np.float64)
