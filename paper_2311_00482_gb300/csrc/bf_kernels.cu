@@ -25,6 +25,8 @@
 #include <cuda_fp16.h>
 #include <limits.h>
 
+#include <algorithm>
+
 #include "../../include/bf.h"
 #include "bf_fft.cuh"
 #include "bf_internal.h"
@@ -323,8 +325,14 @@ struct SmemHeader {
     // band counts, then those that only some pixels count
     uint8_t list[kStages][kWarps][kMaxGroup];
     uint8_t nfull[kStages][kWarps], ntot[kStages][kWarps];
+    // per stage that starts an angle: the tile's delay tables (integer part and
+    // remainder of the column terms [32], then of the row terms [up to 64];
+    // kappa z of the rows)
+    int tK[kStages][kTileCols + 64];
+    float tF[kStages][kTileCols + 64];
+    float tZ[kStages][64];
 };
-constexpr int kHeaderBytes = 1024;
+constexpr int kHeaderBytes = 4096;
 static_assert(sizeof(SmemHeader) <= kHeaderBytes, "header");
 
 // Sample pairs read from shared memory through 32-bit shared-window addresses.
@@ -507,29 +515,24 @@ __device__ __forceinline__ void accumulate_iq(uint32_t win, int wmax, int w0, fl
 }
 
 template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS>
-__global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_kernel(const BfJob *__restrict__ jobs,
-                                                                    const int *__restrict__ tile_prefix,
-                                                                    int njobs, int *__restrict__ err)
+__global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3)
+    beamform_kernel(const BfJob *__restrict__ jobs, const int *__restrict__ tile_prefix, int njobs,
+                    int total_tiles, int stage_stride, int *__restrict__ err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     SmemHeader &sh = *reinterpret_cast<SmemHeader *>(smem);
     constexpr bool IQ = PREC == kPrecIQ;
     constexpr int PB = IQ ? 16 : PairIO<IQ ? kPrecF32 : PREC>::kBytes;
     constexpr int XS = IQ ? 2 : 1;  // tensor-map elements per staged pair
-
-    // ---- which frame and tile
-    const int jb = find_job(tile_prefix, njobs, blockIdx.x);
-    const BfJob *J = jobs + jb;
-    const int nx = J->nx, nz = J->nz, na = J->na, ne = J->ne;
-    const int wmax = J->wmax, G = J->group;
-    const int tile = blockIdx.x - __ldg(tile_prefix + jb);
-    const int tx = tile % J->tiles_x, tz = tile / J->tiles_x;
+    constexpr int TR = kWarps * ROWS;  // tile rows
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ngroups = (ne + G - 1) / G;
-    const int steps = na * ngroups;
-    const int sbytes = stage_bytes(G, wmax, PB);
-    // stage layout: int2 rows [G][32], float dx^2 [G][32], windows [G][wmax]
-    auto stage_base = [&](int st) { return smem + kHeaderBytes + (size_t)st * sbytes; };
+    // Persistent CTAs: tiles blockIdx.x, blockIdx.x + gridDim.x, ... of the
+    // launch's flat (frame, tile) list.  The stage ring runs on across tiles
+    // (ring position r), so the copies of a CTA's next tile are in flight while
+    // it finishes the current one.  Every stage has the launch's largest
+    // stage size; inside a stage the layout is the job's: int2 rows [G][32],
+    // float dx^2 [G][32], windows [G][wmax].
+    auto stage_base = [&](int st) { return smem + kHeaderBytes + (size_t)st * stage_stride; };
 
     if (threadIdx.x == 0) {
         for (int st = 0; st < kStages; ++st) {
@@ -539,272 +542,343 @@ __global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3) beamform_ker
         mbar_fence_init();
     }
     __syncthreads();
-    const unsigned long long deadline = global_ns() + kWaitNs;
 
     if (warp == kWarps) {
         // ================= producer warp: TMA copies of every step's stage
-        const int *__restrict__ wtab = J->wtab;
-        const CUtensorMap *rf_map = J->rf_map;
-        const CUtensorMap *valid_map = J->valid_map;
-        const CUtensorMap *dx2_map = J->dx2_map;
-        const int box = J->box;
-        const int ntiles = J->tiles_x * J->tiles_z;
-        const unsigned meta_bytes = (unsigned)G * kTileCols * 12;
-        const int *__restrict__ btab = J->btab;
-        auto window_of = [&](int s) -> int2 {
-            const int a = s / ngroups, g = s - a * ngroups;
-            const int c = g * G + lane;
-            if (s >= steps || lane >= G || c >= ne)
-                return make_int2(kNoWindow, 0);
-            const size_t o = ((size_t)a * ntiles + tile) * ne + c;
-            return make_int2(__ldg(wtab + o), __ldg(btab + o));
-        };
-        int2 wf = window_of(0);
-        for (int s = 0; s < steps; ++s) {
-            const int st = s % kStages, use = s / kStages;
-            const int2 wf_next = window_of(s + 1);  // in flight while we wait
-            if (use > 0 && !mbar_wait(&sh.empty[st], (unsigned)((use - 1) & 1), deadline, err))
-                break;
-            const int a = s / ngroups, g = s - a * ngroups, i0 = g * G;
-            const bool mine = lane < G && i0 + lane < ne;
-            if (mine)
-                sh.wf[st][lane] = wf;
-            {  // channel lists of every row band (lane = channel of the group)
-                const unsigned fl = (mine && wf.x != kNoWindow) ? (unsigned)wf.y : 0u;
-                const unsigned lt = (1u << lane) - 1u;
-#pragma unroll
-                for (int b = 0; b < kWarps; ++b) {
-                    const bool full = (fl >> (8 + b)) & 1u;
-                    const bool part = !full && ((fl >> b) & 1u);
-                    const unsigned fm = __ballot_sync(0xffffffffu, full);
-                    const unsigned pm = __ballot_sync(0xffffffffu, part);
-                    if (full)
-                        sh.list[st][b][__popc(fm & lt)] = (uint8_t)lane;
-                    else if (part)
-                        sh.list[st][b][__popc(fm) + __popc(pm & lt)] = (uint8_t)lane;
-                    if (lane == 0) {
-                        sh.nfull[st][b] = (uint8_t)__popc(fm);
-                        sh.ntot[st][b] = (uint8_t)(__popc(fm) + __popc(pm));
+        unsigned r = 0;
+        for (int tg = blockIdx.x; tg < total_tiles; tg += gridDim.x) {
+            const unsigned long long deadline = global_ns() + kWaitNs;
+            const int jb = find_job(tile_prefix, njobs, tg);
+            const BfJob *J = jobs + jb;
+            const int tile = tg - __ldg(tile_prefix + jb);
+            const int nx = J->nx, nz = J->nz, ne = J->ne, G = J->group, wmax = J->wmax;
+            const int tiles_x = J->tiles_x, ntiles = tiles_x * J->tiles_z;
+            const int tx = tile % tiles_x, tz = tile / tiles_x;
+            const int ngroups = (ne + G - 1) / G, steps = J->na * ngroups;
+            const int *__restrict__ wtab = J->wtab;
+            const int *__restrict__ btab = J->btab;
+            const CUtensorMap *rf_map = J->rf_map;
+            const CUtensorMap *valid_map = J->valid_map;
+            const CUtensorMap *dx2_map = J->dx2_map;
+            const int box = J->box;
+            const unsigned meta_bytes = (unsigned)G * kTileCols * 12;
+            // window start and band flags of this lane's channel at step s
+            auto window_of = [&](int s) -> int2 {
+                const int a = s / ngroups, g = s - a * ngroups;
+                const int c = g * G + lane;
+                if (s >= steps || lane >= G || c >= ne)
+                    return make_int2(kNoWindow, 0);
+                const size_t o = ((size_t)a * ntiles + tile) * ne + c;
+                return make_int2(__ldg(wtab + o), __ldg(btab + o));
+            };
+            // the tile's delay tables of angle a: this lane's column and rows lane, lane + 32
+            const int cx = min(tx * kTileCols + lane, nx - 1);
+            const int rz0 = min(tz * TR + lane, nz - 1), rz1 = min(tz * TR + lane + 32, nz - 1);
+            struct Tabs {
+                int ck, rk0, rk1;
+                float cf, rf0, rf1, z0, z1;
+            };
+            auto tabs_of = [&](int a) -> Tabs {
+                Tabs t;
+                t.ck = __ldg(J->colK + a * nx + cx);
+                t.cf = __ldg(J->colF + a * nx + cx);
+                t.rk0 = __ldg(J->rowK + a * nz + rz0);
+                t.rf0 = __ldg(J->rowF + a * nz + rz0);
+                t.z0 = __ldg(J->rowZ + rz0);
+                t.rk1 = t.rf1 = 0, t.z1 = 0.f;
+                if (TR > 32) {
+                    t.rk1 = __ldg(J->rowK + a * nz + rz1);
+                    t.rf1 = __ldg(J->rowF + a * nz + rz1);
+                    t.z1 = __ldg(J->rowZ + rz1);
+                }
+                return t;
+            };
+            int2 wf = window_of(0);
+            Tabs tb = tabs_of(0);
+            bool ok = true;
+            for (int s = 0; s < steps; ++s, ++r) {
+                const int st = (int)(r % kStages);
+                const unsigned use = r / kStages;
+                const int a = s / ngroups, g = s - a * ngroups, i0 = g * G;
+                // next step's loads in flight while we wait
+                const int2 wf_next = window_of(s + 1);
+                const bool next_angle = s + 1 < steps && (s + 1) % ngroups == 0;
+                Tabs tb_next = tb;
+                if (next_angle)
+                    tb_next = tabs_of(a + 1);
+                if (use > 0 && !mbar_wait(&sh.empty[st], (use - 1) & 1u, deadline, err)) {
+                    ok = false;
+                    break;
+                }
+                if (g == 0) {  // delay tables of the angle, read by the consumers at this step
+                    sh.tK[st][lane] = tb.ck;
+                    sh.tF[st][lane] = tb.cf;
+                    sh.tK[st][kTileCols + lane] = tb.rk0;
+                    sh.tF[st][kTileCols + lane] = tb.rf0;
+                    sh.tZ[st][lane] = tb.z0;
+                    if (TR > 32) {
+                        sh.tK[st][kTileCols + 32 + lane] = tb.rk1;
+                        sh.tF[st][kTileCols + 32 + lane] = tb.rf1;
+                        sh.tZ[st][32 + lane] = tb.z1;
                     }
                 }
-            }
-            const int w0 = wf.x;
-            const unsigned bytes = (mine && w0 != kNoWindow) ? (unsigned)(wmax * PB) : 0u;
-            unsigned total = bytes;
+                const bool mine = lane < G && i0 + lane < ne;
+                if (mine)
+                    sh.wf[st][lane] = wf;
+                {  // channel lists of every row band (lane = channel of the group)
+                    const unsigned fl = (mine && wf.x != kNoWindow) ? (unsigned)wf.y : 0u;
+                    const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
-            for (int off = 16; off; off >>= 1)
-                total += __shfl_xor_sync(0xffffffffu, total, off);
-            unsigned char *base = stage_base(st);
-            // the window starts are read by the consumers after the full barrier
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive_expect_tx(&sh.full[st], total + meta_bytes);
-                tma_2d(base, valid_map, tx * kTileCols, a * ne + i0, &sh.full[st]);
-                tma_2d(base + (size_t)G * kTileCols * 8, dx2_map, tx * kTileCols, i0, &sh.full[st]);
+                    for (int b = 0; b < kWarps; ++b) {
+                        const bool full = (fl >> (8 + b)) & 1u;
+                        const bool part = !full && ((fl >> b) & 1u);
+                        const unsigned fm = __ballot_sync(0xffffffffu, full);
+                        const unsigned pm = __ballot_sync(0xffffffffu, part);
+                        if (full)
+                            sh.list[st][b][__popc(fm & lt)] = (uint8_t)lane;
+                        else if (part)
+                            sh.list[st][b][__popc(fm) + __popc(pm & lt)] = (uint8_t)lane;
+                        if (lane == 0) {
+                            sh.nfull[st][b] = (uint8_t)__popc(fm);
+                            sh.ntot[st][b] = (uint8_t)(__popc(fm) + __popc(pm));
+                        }
+                    }
+                }
+                const int w0 = wf.x;
+                const unsigned bytes = (mine && w0 != kNoWindow) ? (unsigned)(wmax * PB) : 0u;
+                unsigned total = bytes;
+#pragma unroll
+                for (int off = 16; off; off >>= 1)
+                    total += __shfl_xor_sync(0xffffffffu, total, off);
+                unsigned char *base = stage_base(st);
+                // everything written above is read by the consumers after the full barrier
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(&sh.full[st], total + meta_bytes);
+                    tma_2d(base, valid_map, tx * kTileCols, a * ne + i0, &sh.full[st]);
+                    tma_2d(base + (size_t)G * kTileCols * 8, dx2_map, tx * kTileCols, i0,
+                           &sh.full[st]);
+                }
+                __syncwarp();
+                if (bytes) {
+                    unsigned char *dst = base + (size_t)G * kTileCols * 12 + (size_t)lane * wmax * PB;
+                    const int row = a * ne + i0 + lane;
+                    for (int off = 0; off < wmax; off += box)
+                        tma_2d(dst + (size_t)off * PB, rf_map, (w0 + off) * XS, row, &sh.full[st]);
+                }
+                wf = wf_next;
+                tb = tb_next;
             }
-            __syncwarp();
-            if (bytes) {
-                unsigned char *dst = base + (size_t)G * kTileCols * 12 + (size_t)lane * wmax * PB;
-                const int row = a * ne + i0 + lane;
-                for (int off = 0; off < wmax; off += box)
-                    tma_2d(dst + (size_t)off * PB, rf_map, (w0 + off) * XS, row, &sh.full[st]);
-            }
-            wf = wf_next;
+            if (!ok)
+                return;  // the consumers' waits run out too
         }
         return;
     }
 
     // ================= consumer warps: one column per lane, ROWS rows per thread
-    const int ix = tx * kTileCols + lane;
-    const bool col_ok = ix < nx;
-    const int ixc = min(ix, nx - 1);
-    const int r_first = tz * kWarps * ROWS + warp * ROWS;
-    const int *__restrict__ colK = J->colK;
-    const float *__restrict__ colF = J->colF;
-    const int *__restrict__ rowK = J->rowK;
-    const float *__restrict__ rowF = J->rowF;
+    unsigned r = 0;
+    for (int tg = blockIdx.x; tg < total_tiles; tg += gridDim.x) {
+        const unsigned long long deadline = global_ns() + kWaitNs;
+        const int jb = find_job(tile_prefix, njobs, tg);
+        const BfJob *J = jobs + jb;
+        const int tile = tg - __ldg(tile_prefix + jb);
+        const int nx = J->nx, nz = J->nz, na = J->na, ne = J->ne, G = J->group, wmax = J->wmax;
+        const int tx = tile % J->tiles_x, tz = tile / J->tiles_x;
+        const int ngroups = (ne + G - 1) / G, steps = na * ngroups;
+        const int ix = tx * kTileCols + lane;
+        const bool col_ok = ix < nx;
+        const int ixc = min(ix, nx - 1);
+        const int r_first = tz * TR + warp * ROWS;
 
-    int Kc[ROWS];
-    float Z[ROWS], fp[ROWS];
-    float S1[ROWS], T1[ROWS], T2[ROWS], Yd[ROWS], Su2[ROWS], P1[ROWS], Yp[ROWS];
+        int Kc[ROWS];
+        float Z[ROWS], fp[ROWS];
+        float S1[ROWS], T1[ROWS], T2[ROWS], Yd[ROWS], Su2[ROWS], P1[ROWS], Yp[ROWS];
 #pragma unroll
-    for (int j = 0; j < ROWS; ++j) {
-        Z[j] = __ldg(J->rowZ + min(r_first + j, nz - 1));
-        S1[j] = T1[j] = T2[j] = Yd[j] = Su2[j] = P1[j] = Yp[j] = 0.f;
-        Kc[j] = 0;
-        fp[j] = 0.f;
-    }
-    const float pdas_p = J->pdas_p, inv_p = J->pdas_inv_p;
-    const bool square = pdas_p == 2.0f;  // uniform over the launch
-    // IQ: S1 / Y1i the IQ-DAS sum, T1 / Ti the per-angle BB-DMAS sum, Yd / Y2i BB-DMAS
-    float Y1i[ROWS], Ti[ROWS], Y2i[ROWS], invM[ROWS];
-    const float c1 = J->iq_c1, c2 = J->iq_c2;
-#pragma unroll
-    for (int j = 0; j < ROWS; ++j) {
-        Y1i[j] = Ti[j] = Y2i[j] = 0.f;
-        invM[j] = 0.f;
-        if (IQ && DMAS) {
-            const int izc = min(r_first + j, nz - 1);
-            const float m = (float)__ldg(J->apcnt + (size_t)ixc * nz + izc);
-            invM[j] = m > 0.f ? 1.f / m : 0.f;
+        for (int j = 0; j < ROWS; ++j) {
+            S1[j] = T1[j] = T2[j] = Yd[j] = Su2[j] = P1[j] = Yp[j] = 0.f;
+            Kc[j] = 0;
+            fp[j] = Z[j] = 0.f;
         }
-    }
-
-    bool ok = true;
-#pragma unroll 1
-    for (int s = 0; s < steps && ok; ++s) {
-        const int a = s / ngroups, g = s - a * ngroups;
-        const int st = s % kStages, use = s / kStages;
-        if (g == 0) {
-            const int ck = __ldg(colK + a * nx + ixc);
-            const float cf = __ldg(colF + a * nx + ixc);
+        const float pdas_p = J->pdas_p, inv_p = J->pdas_inv_p;
+        const bool square = pdas_p == 2.0f;  // uniform over the job
+        // IQ: S1 / Y1i the IQ-DAS sum, T1 / Ti the per-angle BB-DMAS sum, Yd / Y2i BB-DMAS
+        float Y1i[ROWS], Ti[ROWS], Y2i[ROWS], invM[ROWS];
+        const float c1 = J->iq_c1, c2 = J->iq_c2;
 #pragma unroll
-            for (int j = 0; j < ROWS; ++j) {
+        for (int j = 0; j < ROWS; ++j) {
+            Y1i[j] = Ti[j] = Y2i[j] = 0.f;
+            invM[j] = 0.f;
+            if (IQ && DMAS) {
                 const int izc = min(r_first + j, nz - 1);
-                Kc[j] = ck + __ldg(rowK + a * nz + izc) + kPadL - kRoundBits;
-                fp[j] = cf + __ldg(rowF + a * nz + izc) - 0.5f;
-                T1[j] = T2[j] = P1[j] = Ti[j] = 0.f;
+                const float m = (float)__ldg(J->apcnt + (size_t)ixc * nz + izc);
+                invM[j] = m > 0.f ? 1.f / m : 0.f;
             }
         }
-        ok = mbar_wait(&sh.full[st], (unsigned)(use & 1), deadline, err);
-        if (!ok)
-            break;
-        const uint32_t base = smem_u32(stage_base(st));
-        const uint32_t vrb = base + (uint32_t)lane * 8;                          // int2 [G][32]
-        const uint32_t d2b = base + (uint32_t)G * kTileCols * 8 + (uint32_t)lane * 4;  // float [G][32]
-        const uint32_t wins = base + (uint32_t)G * kTileCols * 12;
-        const uint32_t wfb = smem_u32(&sh.wf[st][0]);
-        const int nf = sh.nfull[st][warp], nt = sh.ntot[st][warp];
-        const uint8_t *L = sh.list[st][warp];
-        auto win_of = [&](int c) { return wins + (uint32_t)(c * wmax * PB); };
-        auto w0_of = [&](int c) { return lds_int2(wfb + (uint32_t)c * 8).x; };
-        auto d2_of = [&](int c) { return lds_f32(d2b + (uint32_t)c * (kTileCols * 4)); };
-        auto vr_of = [&](int c) { return lds_int2(vrb + (uint32_t)c * (kTileCols * 8)); };
-        int k = 0;
-        if constexpr (IQ) {
-#pragma unroll 1
-            for (; k < nf; ++k) {
-                const int c = L[k];
-                accumulate_iq<DMAS, ROWS, false>(win_of(c), wmax, w0_of(c), d2_of(c),
-                                                 make_int2(0, 0), r_first, Z, fp, Kc, c1, c2, S1,
-                                                 Y1i, T1, Ti);
-            }
-#pragma unroll 1
-            for (; k < nt; ++k) {
-                const int c = L[k];
-                accumulate_iq<DMAS, ROWS, true>(win_of(c), wmax, w0_of(c), d2_of(c), vr_of(c),
-                                                r_first, Z, fp, Kc, c1, c2, S1, Y1i, T1, Ti);
-            }
-        } else {
-            // channels every pixel of the band counts, two at a time (twice the
-            // independent dependency chains per thread), then the rest with a
-            // per-pixel row test
-#pragma unroll 1
-            for (; k + 1 < nf; k += 2) {
-                const int c0 = L[k], c1 = L[k + 1];
-                accumulate2<PREC, DMAS, CF, PDAS, ROWS>(win_of(c0), w0_of(c0), d2_of(c0), win_of(c1),
-                                                        w0_of(c1), d2_of(c1), wmax, Z, fp, Kc, S1,
-                                                        T1, T2, Su2, P1, inv_p, square);
-            }
-            if (k < nf) {
-                const int c = L[k++];
-                accumulate<PREC, DMAS, CF, PDAS, ROWS, false>(win_of(c), wmax, w0_of(c), d2_of(c),
-                                                              make_int2(0, 0), r_first, Z, fp, Kc,
-                                                              S1, T1, T2, Su2, P1, inv_p, square);
-            }
-#pragma unroll 1
-            for (; k < nt; ++k) {
-                const int c = L[k];
-                accumulate<PREC, DMAS, CF, PDAS, ROWS, true>(win_of(c), wmax, w0_of(c), d2_of(c),
-                                                             vr_of(c), r_first, Z, fp, Kc, S1, T1,
-                                                             T2, Su2, P1, inv_p, square);
-            }
-        }
-        __syncwarp();
-        if (lane == 0)
-            mbar_arrive(&sh.empty[st]);
-        if (DMAS && !IQ && g == ngroups - 1) {
-#pragma unroll
-            for (int j = 0; j < ROWS; ++j)
-                Yd[j] = fmaf(0.5f * T1[j], T1[j], fmaf(-0.5f, T2[j], Yd[j]));
-        }
-        if (DMAS && IQ && g == ngroups - 1) {  // Eq. (4): ((1/M) sum s^)^2 per angle
-#pragma unroll
-            for (int j = 0; j < ROWS; ++j) {
-                const float ur = T1[j] * invM[j], ui = Ti[j] * invM[j];
-                Yd[j] += fmaf(ur, ur, -ui * ui);
-                Y2i[j] = fmaf(2.f * ur, ui, Y2i[j]);
-            }
-        }
-        if (PDAS && g == ngroups - 1) {  // Eq. (3) per angle, then the coherent sum
-#pragma unroll
-            for (int j = 0; j < ROWS; ++j)
-                Yp[j] += copysignf(powf(fabsf(P1[j]), pdas_p), P1[j]);
-        }
-    }
 
-    if constexpr (IQ) {  // magnitude images (and their maxima for the log stage)
+        bool ok = true;
+#pragma unroll 1
+        for (int s = 0; s < steps; ++s, ++r) {
+            const int a = s / ngroups, g = s - a * ngroups;
+            (void)a;
+            const int st = (int)(r % kStages);
+            const unsigned use = r / kStages;
+            ok = __all_sync(0xffffffffu, mbar_wait(&sh.full[st], use & 1u, deadline, err));
+            if (!ok)
+                break;
+            if (g == 0) {  // this angle's delay tables, staged by the producer
+                const int ck = sh.tK[st][lane];
+                const float cf = sh.tF[st][lane];
+#pragma unroll
+                for (int j = 0; j < ROWS; ++j) {
+                    const int rr = warp * ROWS + j;
+                    Kc[j] = ck + sh.tK[st][kTileCols + rr] + kPadL - kRoundBits;
+                    fp[j] = cf + sh.tF[st][kTileCols + rr] - 0.5f;
+                    Z[j] = sh.tZ[st][rr];
+                    T1[j] = T2[j] = P1[j] = Ti[j] = 0.f;
+                }
+            }
+            const uint32_t base = smem_u32(stage_base(st));
+            const uint32_t vrb = base + (uint32_t)lane * 8;                          // int2 [G][32]
+            const uint32_t d2b = base + (uint32_t)G * kTileCols * 8 + (uint32_t)lane * 4;  // float [G][32]
+            const uint32_t wins = base + (uint32_t)G * kTileCols * 12;
+            const uint32_t wfb = smem_u32(&sh.wf[st][0]);
+            const int nf = sh.nfull[st][warp], nt = sh.ntot[st][warp];
+            const uint8_t *L = sh.list[st][warp];
+            auto win_of = [&](int c) { return wins + (uint32_t)(c * wmax * PB); };
+            auto w0_of = [&](int c) { return lds_int2(wfb + (uint32_t)c * 8).x; };
+            auto d2_of = [&](int c) { return lds_f32(d2b + (uint32_t)c * (kTileCols * 4)); };
+            auto vr_of = [&](int c) { return lds_int2(vrb + (uint32_t)c * (kTileCols * 8)); };
+            int k = 0;
+            if constexpr (IQ) {
+#pragma unroll 1
+                for (; k < nf; ++k) {
+                    const int c = L[k];
+                    accumulate_iq<DMAS, ROWS, false>(win_of(c), wmax, w0_of(c), d2_of(c),
+                                                     make_int2(0, 0), r_first, Z, fp, Kc, c1, c2,
+                                                     S1, Y1i, T1, Ti);
+                }
+#pragma unroll 1
+                for (; k < nt; ++k) {
+                    const int c = L[k];
+                    accumulate_iq<DMAS, ROWS, true>(win_of(c), wmax, w0_of(c), d2_of(c), vr_of(c),
+                                                    r_first, Z, fp, Kc, c1, c2, S1, Y1i, T1, Ti);
+                }
+            } else {
+                // channels every pixel of the band counts, two at a time (twice the
+                // independent dependency chains per thread), then the rest with a
+                // per-pixel row test
+#pragma unroll 1
+                for (; k + 1 < nf; k += 2) {
+                    const int c0 = L[k], c1 = L[k + 1];
+                    accumulate2<PREC, DMAS, CF, PDAS, ROWS>(win_of(c0), w0_of(c0), d2_of(c0),
+                                                            win_of(c1), w0_of(c1), d2_of(c1), wmax,
+                                                            Z, fp, Kc, S1, T1, T2, Su2, P1, inv_p,
+                                                            square);
+                }
+                if (k < nf) {
+                    const int c = L[k++];
+                    accumulate<PREC, DMAS, CF, PDAS, ROWS, false>(win_of(c), wmax, w0_of(c),
+                                                                  d2_of(c), make_int2(0, 0),
+                                                                  r_first, Z, fp, Kc, S1, T1, T2,
+                                                                  Su2, P1, inv_p, square);
+                }
+#pragma unroll 1
+                for (; k < nt; ++k) {
+                    const int c = L[k];
+                    accumulate<PREC, DMAS, CF, PDAS, ROWS, true>(win_of(c), wmax, w0_of(c),
+                                                                 d2_of(c), vr_of(c), r_first, Z,
+                                                                 fp, Kc, S1, T1, T2, Su2, P1,
+                                                                 inv_p, square);
+                }
+            }
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&sh.empty[st]);
+            if (DMAS && !IQ && g == ngroups - 1) {
+#pragma unroll
+                for (int j = 0; j < ROWS; ++j)
+                    Yd[j] = fmaf(0.5f * T1[j], T1[j], fmaf(-0.5f, T2[j], Yd[j]));
+            }
+            if (DMAS && IQ && g == ngroups - 1) {  // Eq. (4): ((1/M) sum s^)^2 per angle
+#pragma unroll
+                for (int j = 0; j < ROWS; ++j) {
+                    const float ur = T1[j] * invM[j], ui = Ti[j] * invM[j];
+                    Yd[j] += fmaf(ur, ur, -ui * ui);
+                    Y2i[j] = fmaf(2.f * ur, ui, Y2i[j]);
+                }
+            }
+            if (PDAS && g == ngroups - 1) {  // Eq. (3) per angle, then the coherent sum
+#pragma unroll
+                for (int j = 0; j < ROWS; ++j)
+                    Yp[j] += copysignf(powf(fabsf(P1[j]), pdas_p), P1[j]);
+            }
+        }
+        if (!ok)
+            return;  // warp-uniform: a bounded wait ran out (error bit set)
+
+        if constexpr (IQ) {  // magnitude images (and their maxima for the log stage)
+            const size_t plane = (size_t)nx * nz;
+            float *__restrict__ y = J->y;
+            const int modes = J->modes;
+            float m0 = 0.f, m1 = 0.f;
+            if (ok && col_ok) {
+    #pragma unroll
+                for (int j = 0; j < ROWS; ++j) {
+                    const int iz = r_first + j;
+                    if (iz >= nz)
+                        break;
+                    const size_t o = (size_t)ix * nz + iz;
+                    int slot = 0;
+                    if (modes & BF_DAS) {
+                        const float v = sqrtf(fmaf(S1[j], S1[j], Y1i[j] * Y1i[j]));
+                        y[(size_t)(slot++) * plane + o] = v;
+                        m0 = fmaxf(m0, v);
+                    }
+                    if (modes & BF_DMAS) {
+                        const float v = sqrtf(fmaf(Yd[j], Yd[j], Y2i[j] * Y2i[j]));
+                        y[(size_t)(slot++) * plane + o] = v;
+                        m1 = fmaxf(m1, v);
+                    }
+                }
+            }
+            if (J->maxbits) {  // uniform per job; every lane of the warp is here
+                const unsigned r0 = __reduce_max_sync(0xffffffffu, __float_as_uint(m0));
+                const unsigned r1 = __reduce_max_sync(0xffffffffu, __float_as_uint(m1));
+                if (lane == 0) {
+                    int slot = 0;
+                    if (modes & BF_DAS)
+                        atomicMax(J->maxbits + slot++, r0);
+                    if (modes & BF_DMAS)
+                        atomicMax(J->maxbits + slot, r1);
+                }
+            }
+            continue;
+        }
+        if (!col_ok)
+            continue;
+        const int modes = J->modes;
+        const float scale = J->out_scale;
         const size_t plane = (size_t)nx * nz;
         float *__restrict__ y = J->y;
-        const int modes = J->modes;
-        float m0 = 0.f, m1 = 0.f;
-        if (ok && col_ok) {
-#pragma unroll
-            for (int j = 0; j < ROWS; ++j) {
-                const int iz = r_first + j;
-                if (iz >= nz)
-                    break;
-                const size_t o = (size_t)ix * nz + iz;
-                int slot = 0;
-                if (modes & BF_DAS) {
-                    const float v = sqrtf(fmaf(S1[j], S1[j], Y1i[j] * Y1i[j]));
-                    y[(size_t)(slot++) * plane + o] = v;
-                    m0 = fmaxf(m0, v);
-                }
-                if (modes & BF_DMAS) {
-                    const float v = sqrtf(fmaf(Yd[j], Yd[j], Y2i[j] * Y2i[j]));
-                    y[(size_t)(slot++) * plane + o] = v;
-                    m1 = fmaxf(m1, v);
-                }
+    #pragma unroll
+        for (int j = 0; j < ROWS; ++j) {
+            const int iz = r_first + j;
+            if (iz >= nz)
+                break;
+            const size_t o = (size_t)ix * nz + iz;
+            int slot = 0;
+            if (modes & BF_DAS)
+                y[(size_t)(slot++) * plane + o] = S1[j] * scale;
+            if (modes & BF_DMAS)
+                y[(size_t)(slot++) * plane + o] = Yd[j] * scale;
+            if (modes & BF_CF) {
+                const float mtot = (float)na * (float)__ldg(J->apcnt + o);
+                const float den = mtot * Su2[j];
+                y[(size_t)(slot++) * plane + o] = den > 0.f ? (S1[j] * S1[j] / den) * S1[j] * scale : 0.f;
             }
+            if (modes & BF_PDAS)
+                y[(size_t)(slot++) * plane + o] = Yp[j] * scale;
         }
-        if (J->maxbits) {  // uniform per launch; every lane of the warp is here
-            const unsigned r0 = __reduce_max_sync(0xffffffffu, __float_as_uint(m0));
-            const unsigned r1 = __reduce_max_sync(0xffffffffu, __float_as_uint(m1));
-            if (lane == 0) {
-                int slot = 0;
-                if (modes & BF_DAS)
-                    atomicMax(J->maxbits + slot++, r0);
-                if (modes & BF_DMAS)
-                    atomicMax(J->maxbits + slot, r1);
-            }
-        }
-        return;
-    }
-    if (!ok || !col_ok)
-        return;
-    const int modes = J->modes;
-    const float scale = J->out_scale;
-    const size_t plane = (size_t)nx * nz;
-    float *__restrict__ y = J->y;
-#pragma unroll
-    for (int j = 0; j < ROWS; ++j) {
-        const int iz = r_first + j;
-        if (iz >= nz)
-            break;
-        const size_t o = (size_t)ix * nz + iz;
-        int slot = 0;
-        if (modes & BF_DAS)
-            y[(size_t)(slot++) * plane + o] = S1[j] * scale;
-        if (modes & BF_DMAS)
-            y[(size_t)(slot++) * plane + o] = Yd[j] * scale;
-        if (modes & BF_CF) {
-            const float mtot = (float)na * (float)__ldg(J->apcnt + o);
-            const float den = mtot * Su2[j];
-            y[(size_t)(slot++) * plane + o] = den > 0.f ? (S1[j] * S1[j] / den) * S1[j] * scale : 0.f;
-        }
-        if (modes & BF_PDAS)
-            y[(size_t)(slot++) * plane + o] = Yp[j] * scale;
     }
 }
 
@@ -1138,8 +1212,11 @@ cudaError_t launch_bf_t(const BfJob *jobs, const int *prefix, int njobs, int til
 {
     auto k = beamform_kernel<PREC, DMAS, CF, PDAS, ROWS>;
     static size_t configured = 0;
+    static size_t occ_smem = 0;
+    static int occ = 0, sms = 0;
+    cudaError_t e = cudaSuccess;
     if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)  // several CTAs per SM need the largest shared-memory carveout
             e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      (int)cudaSharedmemCarveoutMaxShared);
@@ -1147,7 +1224,24 @@ cudaError_t launch_bf_t(const BfJob *jobs, const int *prefix, int njobs, int til
             return e;
         configured = smem;
     }
-    k<<<tiles, kThreads + 32, smem, st>>>(jobs, prefix, njobs, err);
+    if (sms == 0) {
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess)
+            return e;
+    }
+    if (smem != occ_smem) {  // resident CTAs per SM at this shared-memory size
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kThreads + 32, smem);
+        if (e != cudaSuccess)
+            return e;
+        occ_smem = smem;
+    }
+    // persistent grid: every CTA resident at once, each walking the tiles
+    const int grid = std::max(1, std::min(tiles, std::max(occ, 1) * sms));
+    const int stride = (int)((smem - kHeaderBytes) / kStages);
+    k<<<grid, kThreads + 32, smem, st>>>(jobs, prefix, njobs, tiles, stride, err);
     return cudaGetLastError();
 }
 
