@@ -514,8 +514,17 @@ __device__ __forceinline__ void accumulate_iq(uint32_t win, int wmax, int w0, fl
     }
 }
 
+// Resident CTAs per SM the register budget is sized for: three 32-row tiles;
+// two 64-row tiles, or one where the combiners need more registers than two
+// CTAs leave.
 template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS>
-__global__ void __launch_bounds__(kThreads + 32, ROWS == 8 ? 1 : 3)
+constexpr int beamform_min_blocks()
+{
+    return ROWS != 8 ? 3 : ((DMAS && (CF || PDAS)) || (PREC == kPrecIQ && DMAS)) ? 1 : 2;
+}
+
+template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS>
+__global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS, CF, PDAS, ROWS>()))
     beamform_kernel(const BfJob *__restrict__ jobs, const int *__restrict__ tile_prefix, int njobs,
                     int total_tiles, int stage_stride, int *__restrict__ err)
 {
