@@ -514,13 +514,13 @@ __device__ __forceinline__ void accumulate_iq(uint32_t win, int wmax, int w0, fl
     }
 }
 
-// Resident CTAs per SM the register budget is sized for: three 32-row tiles;
-// two 64-row tiles, or one where the combiners need more registers than two
-// CTAs leave.
+// Resident CTAs per SM the register budget is sized for: three 32-row tiles,
+// one 64-row tile (measured: capping 64-row tiles at two CTAs per SM costs
+// more in spills and lost overlap than the extra warps win).
 template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS>
 constexpr int beamform_min_blocks()
 {
-    return ROWS != 8 ? 3 : ((DMAS && (CF || PDAS)) || (PREC == kPrecIQ && DMAS)) ? 1 : 2;
+    return ROWS != 8 ? 3 : 1;
 }
 
 template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS>
