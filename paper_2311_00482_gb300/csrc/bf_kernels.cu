@@ -159,21 +159,6 @@ __device__ __forceinline__ float rx_excess(float dx2, float z)
     return dx2 * rcp_approx(r + z);
 }
 
-// The same receive excess with one special-function operation: r = s rsqrt(s)
-// is sqrt(s) to a few ulp, h = r - z, and one Newton step h + e / (2 r) with
-// the residual e = dx2 - 2 z h - h^2 (= dx2 + z^2 - r^2, formed from the exact
-// inputs without cancellation: both products are exact inside the fused
-// multiply-adds) brings it to ~1e-7 samples.
-__device__ __forceinline__ float rx_excess_n(float dx2, float z)
-{
-    const float s = fmaf(z, z, dx2);
-    const float u = rsqrt_approx(s);
-    const float r = s * u;
-    const float h = r - z;
-    const float e = fmaf(-h, h, fmaf(-2.f * z, h, dx2));
-    return fmaf(0.5f * e, u, h);
-}
-
 __device__ __forceinline__ int find_job(const int *__restrict__ prefix, int njobs, int bid)
 {
     int lo = 0, hi = njobs - 1;
@@ -428,7 +413,7 @@ __device__ __forceinline__ void accumulate(uint32_t win, int wmax, int w0, float
     const unsigned span = (unsigned)(vr.y - vr.x);
 #pragma unroll
     for (int j = 0; j < ROWS; ++j) {
-        const float x = rx_excess_n(d2, Z[j]) + fp[j];
+        const float x = rx_excess(d2, Z[j]) + fp[j];
         const float m = x + kRoundMagic;
         const float al = x - (m - kRoundMagic);  // in [-1/2, 1/2]
         const unsigned idx = min((unsigned)(__float_as_int(m) + Kc[j] - w0), (unsigned)(wmax - 1));
@@ -461,8 +446,8 @@ __device__ __forceinline__ void accumulate2(uint32_t win0, int w00, float d20, u
     constexpr int PB = PairIO<PREC>::kBytes;
 #pragma unroll
     for (int j = 0; j < ROWS; ++j) {
-        const float x0 = rx_excess_n(d20, Z[j]) + fp[j];
-        const float x1 = rx_excess_n(d21, Z[j]) + fp[j];
+        const float x0 = rx_excess(d20, Z[j]) + fp[j];
+        const float x1 = rx_excess(d21, Z[j]) + fp[j];
         const float m0 = x0 + kRoundMagic, m1 = x1 + kRoundMagic;
         const float al0 = x0 - (m0 - kRoundMagic), al1 = x1 - (m1 - kRoundMagic);
         const unsigned i0 = min((unsigned)(__float_as_int(m0) + Kc[j] - w00), (unsigned)(wmax - 1));
@@ -507,7 +492,7 @@ __device__ __forceinline__ void accumulate_iq(uint32_t win, int wmax, int w0, fl
     const unsigned span = (unsigned)(vr.y - vr.x);
 #pragma unroll
     for (int j = 0; j < ROWS; ++j) {
-        const float x = rx_excess_n(d2, Z[j]) + fp[j];
+        const float x = rx_excess(d2, Z[j]) + fp[j];
         const float m = x + kRoundMagic;
         const float al = x - (m - kRoundMagic);  // alpha - 1/2
         const unsigned idx = min((unsigned)(__float_as_int(m) + Kc[j] - w0), (unsigned)(wmax - 1));
