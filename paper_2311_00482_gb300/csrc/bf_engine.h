@@ -145,6 +145,34 @@ struct DeviceLaunch {
 
 struct Request;
 
+// The last bf_beamform call of a handle, kept so that the same call again
+// (same plan, flags, buffers, order p and stream) skips the host-side
+// preparation and, from its second repetition on, replays one CUDA graph.
+struct CallCache {
+    bool valid = false;
+    const Plan *plan = nullptr;
+    uint32_t flags = 0;
+    const int16_t *rf = nullptr;
+    float *out = nullptr;
+    int ns = 0, na = 0;
+    double pdas_p = 0;
+    cudaStream_t stream = nullptr;
+    int hits = 0;
+    std::vector<FramePrep> frames;
+    HostLaunch hl;
+    cudaGraphExec_t exec = nullptr;
+    void clear()
+    {
+        if (exec)
+            cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        valid = false;
+        hits = 0;
+        frames.clear();
+        hl = HostLaunch{};
+    }
+};
+
 }  // namespace bfi
 
 struct bf_handle {
@@ -160,6 +188,7 @@ struct bf_handle {
     std::map<bfi::PlanKey, int> tuned;  // tile configuration bf_autotune chose (key cfg = 0)
     bfi::FrameScratch scratch;     // bf_beamform
     bfi::DeviceLaunch launch;      // bf_beamform
+    bfi::CallCache call;           // bf_beamform's last call
     bool err_cleared = false;
     std::map<uint64_t, std::shared_ptr<bfi::Request>> tickets;
 };
