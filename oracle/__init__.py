@@ -224,48 +224,56 @@ def fk_sizes(n_elements, n_samples):
 def fk_migrate(rf, pitch, angles_rad, fs, c):
     """Plane-wave f-k migration (exact mapping of the delay model of Eq. (1) with
     the plane-wave transmit), compounded over angles; returns |image| on the
-    native grid [N][Ns]: column i at element i, row m at depth m c / (2 fs).
+    native grid [N][Ns]: column i at element i, row m at depth m dz, dz = c / (2 fs).
 
-    Steps, per angle theta, in float64:
-      1. D(f, x_i) = DFT over n of u_i[n] (records zero-padded to nt), f >= 0;
-      2. the transmit's lateral delay is removed: D *= exp(+j 2 pi f x_i sin(theta) / c);
-      3. DFT over the elements (zero-padded to nk): D(f, Kx);
-      4. for every (Kx, Kz > 0) of the output spectrum, the wavenumber
-         k = (Kx^2 + Kz^2) / (2 (Kx sin(theta) + Kz cos(theta))) with f = k c / (2 pi)
-         (the transmit wave k (sin, cos) plus the receive wave of lateral
-         wavenumber Kx - k sin(theta) reach (Kx, Kz)); kept where the
-         denominator is positive, |Kx - k sin(theta)| <= k and f < fs / 2; the
-         spectrum D(f, Kx) is interpolated linearly in f and weighted by dk/dKz;
+    Per angle theta (s = sin, c_ = cos), in float64:
+      1. D(b, x_i) = DFT over n of u_i[n] (records zero-padded to nt), bins
+         b = 0 .. nt/2 (frequency b fs / nt);
+      2. the transmit's lateral delay is removed:
+         D *= exp(+j 2 pi (b fs / nt) x_i s / c) = exp(+j pi b x_i s / (nt dz));
+      3. DFT over the elements (zero-padded to nk): D(b, m), lateral wavenumber
+         Kx = 2 pi m_s / (nk pitch) with m_s the signed index of bin m;
+      4. the output spectrum at (m, q), depth wavenumber Kz = 2 pi q / (nt dz),
+         q = 1 .. nt/2, takes the temporal bin where the transmit wave
+         k (s, c_) plus a receive wave of lateral wavenumber Kx - k s reach
+         (Kx, Kz): k = (Kx^2 + Kz^2) / (2 (Kx s + Kz c_)).  In bins, with
+         X = m_s nt dz / (nk pitch) and Q = q:
+             pos = (X^2 + Q^2) / (X s + Q c_),
+         kept where X s + Q c_ > 0, |2 X - pos s| <= pos (a propagating
+         receive wave) and 0 <= pos < nt / 2; D(., m) is interpolated linearly
+         at pos and weighted by dk/dKz = (1/2) dpos/dQ
+             = (Q (X s + Q c_) - (X^2 + Q^2) c_ / 2) / (X s + Q c_)^2;
       5. the spectra of all angles are summed, inverse 2-D DFT, magnitude.
     """
     rf = np.asarray(rf, dtype=np.float64)
     na, ne, ns = rf.shape
     nt, nk = fk_sizes(ne, ns)
+    dz = c / (2.0 * fs)
     x = (np.arange(ne) - 0.5 * (ne - 1)) * pitch
-    f = np.arange(nt // 2 + 1) * fs / nt                      # frequencies of the one-sided spectrum
-    kx = 2 * np.pi * np.fft.fftfreq(nk, d=pitch)              # lateral wavenumbers (rad/m)
-    dz = c / (2 * fs)
-    kz = 2 * np.pi * np.arange(1, nt // 2 + 1) / (nt * dz)    # Kz > 0 (rad/m); Kz = 0 carries nothing
-    spec = np.zeros((nt, nk), dtype=np.complex128)            # [Kz index][Kx index]
-    KX, KZ = np.meshgrid(kx, kz)                              # [Kz][Kx]
+    b = np.arange(nt // 2 + 1, dtype=np.float64)
+    ms = np.where(np.arange(nk) < nk // 2, np.arange(nk), np.arange(nk) - nk).astype(np.float64)
+    X = ms * (nt * dz / (nk * pitch))                         # [nk]
+    Q = np.arange(1, nt // 2 + 1, dtype=np.float64)           # [nt/2]
+    XX, QQ = np.meshgrid(X, Q)                                # [q][m]
+    spec = np.zeros((nt, nk), dtype=np.complex128)            # [Kz bin][Kx bin]
+    cols = np.broadcast_to(np.arange(nk)[None, :], XX.shape)
     for a in range(na):
         st, ct = np.sin(angles_rad[a]), np.cos(angles_rad[a])
         D = np.fft.rfft(rf[a], n=nt, axis=1)                  # [N][nt/2+1]
-        D = D * np.exp(2j * np.pi * f[None, :] * x[:, None] * st / c)
+        D = D * np.exp(1j * np.pi * b[None, :] * x[:, None] * st / (nt * dz))
         D = np.fft.fft(D, n=nk, axis=0)                       # [nk][nt/2+1]
-        den = 2.0 * (KX * st + KZ * ct)
+        den = XX * st + QQ * ct
+        num = XX * XX + QQ * QQ
         with np.errstate(divide="ignore", invalid="ignore"):
-            k = (KX ** 2 + KZ ** 2) / den
-            dk = (2.0 * KZ * den - (KX ** 2 + KZ ** 2) * 2.0 * ct) / den ** 2
-        fk = k * c / (2 * np.pi)
-        ok = (den > 0) & (np.abs(KX - k * st) <= k) & (fk >= 0) & (fk < fs / 2)
-        pos = np.where(ok, fk / (fs / nt), 0.0)               # fractional frequency bin
+            pos = num / den
+            w = (QQ * den - 0.5 * num * ct) / (den * den)
+        ok = (den > 0) & (np.abs(2.0 * XX - pos * st) <= pos) & (pos >= 0) & (pos < nt // 2)
+        pos = np.where(ok, pos, 0.0)
         i0 = np.floor(pos).astype(np.int64)
         al = pos - i0
         i1 = np.minimum(i0 + 1, nt // 2)
-        cols = np.broadcast_to(np.arange(nk)[None, :], KX.shape)
         val = (1 - al) * D[cols, i0] + al * D[cols, i1]
-        spec[1:nt // 2 + 1] += np.where(ok, val * dk, 0.0)
+        spec[1:nt // 2 + 1] += np.where(ok, val * w, 0.0)
     img = np.fft.ifft2(spec)                                  # [z][x]
     return np.abs(img[:ns, :ne]).T.copy()
 

@@ -75,14 +75,15 @@ def test_homogeneous_and_zero():
 
 
 MUTANTS = [
-    ("lateral delay compensated with the wrong sign", "np.exp(2j * np.pi * f[None, :]",
-     "np.exp(-2j * np.pi * f[None, :]"),
-    ("mapping without the factor 2", "k = (KX ** 2 + KZ ** 2) / den", "k = (KX ** 2 + KZ ** 2) / (2 * den)"),
-    ("depth spacing of a one-way path", "dz = c / (2 * fs)", "dz = c / fs"),
-    ("steering dropped from the mapping", "den = 2.0 * (KX * st + KZ * ct)", "den = 2.0 * (KZ * ct)"),
+    ("lateral delay compensated with the wrong sign", "D = D * np.exp(1j * np.pi",
+     "D = D * np.exp(-1j * np.pi"),
+    ("mapping without the steering term", "den = XX * st + QQ * ct", "den = QQ * ct"),
+    ("mapping off by a factor 2", "pos = num / den", "pos = 0.5 * num / den"),
+    ("depth spacing of a one-way path", "dz = c / (2.0 * fs)", "dz = c / fs"),
     ("interpolation weights swapped", "val = (1 - al) * D[cols, i0] + al * D[cols, i1]",
      "val = al * D[cols, i0] + (1 - al) * D[cols, i1]"),
-    ("lateral wavenumbers of a one-sample pitch", "np.fft.fftfreq(nk, d=pitch)", "np.fft.fftfreq(nk, d=1.0)"),
+    ("lateral wavenumbers of a one-sample pitch", "X = ms * (nt * dz / (nk * pitch))",
+     "X = ms * (nt * dz / nk)"),
 ]
 
 
