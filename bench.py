@@ -53,7 +53,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--workload", default="cyst512",
-                   choices=["cyst512", "batch256", "serving", "precision", "sweep", "iq"],
+                   choices=["cyst512", "batch256", "serving", "precision", "sweep", "iq", "fk"],
                    help="cyst512: the headline line; the others print informational lines")
     p.add_argument("--requests", type=int, default=2000, help="serving: requests per rate")
     return p.parse_args()
@@ -517,6 +517,48 @@ def run_iq(args):
           flush=True)
 
 
+def run_fk(args):
+    """Plane-wave f-k migration of the 64-channel, 2048-sample cyst record (one
+    and three angles): time per frame on the device and rel-L2 against the oracle."""
+    import oracle
+
+    torch, bf = _setup_gpu()
+    rows = []
+    for angles in ((0.0,), (-7.0, 0.0, 7.0)):
+        acq = synth.CYST_WIRES_512.with_(angles_deg=angles)
+        rf, _ = synth.cyst_wires_frame(acq)
+        h = _handle(bf, acq)
+        stream = torch.cuda.Stream()
+        bf.bf_set_stream(h, stream)
+        rf_d = torch.from_numpy(rf).cuda()
+        out = torch.empty((acq.n_elements, acq.n_samples), dtype=torch.float32, device="cuda")
+        for _ in range(5):
+            bf.bf_fkmig(h, rf_d, acq.n_samples, acq.angles_rad, bf.BF_OUT_LOGDB, out)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(50):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            bf.bf_fkmig(h, rf_d, acq.n_samples, acq.angles_rad, bf.BF_OUT_LOGDB, out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        bf.bf_fkmig(h, rf_d, acq.n_samples, acq.angles_rad, bf.BF_OUT_RF, out)
+        torch.cuda.synchronize()
+        ref = oracle.fk_migrate(rf, acq.pitch_m, acq.angles_rad, acq.fs_hz, acq.c_mps)
+        got = out.cpu().numpy().astype(np.float64)
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        t0 = time.perf_counter()
+        oracle.fk_migrate(rf, acq.pitch_m, acq.angles_rad, acq.fs_hz, acq.c_mps)
+        cpu_ms = 1e3 * (time.perf_counter() - t0)
+        rows.append({"angles": len(angles), "gpu_ms": statistics.median(ts), "frames_per_s":
+                     1e3 / statistics.median(ts), "oracle_ms_numpy": cpu_ms, "rel_l2": err})
+        bf.bf_destroy(h)
+    print(json.dumps({"workload": "plane-wave f-k migration, 64 ch x 2048 samples (cyst + wires), "
+                                  "native grid 64 x 2048, -70 dB log, one frame per call",
+                      "rows": rows}), flush=True)
+
+
 def run_precision(args):
     """1024x1024, 128 elements, 4096 samples, 7 angles: time per frame and rel-L2 per storage."""
     import oracle
@@ -735,6 +777,8 @@ def main():
         run_precision(args)
     elif args.workload == "iq":
         run_iq(args)
+    elif args.workload == "fk":
+        run_fk(args)
     elif args.workload == "sweep":
         run_sweep(args)
     elif args.workload == "serving":

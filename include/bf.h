@@ -115,6 +115,25 @@ BF_API int bf_destroy(bf_handle *h);
  * library's own non-blocking stream). */
 BF_API int bf_set_stream(bf_handle *h, void *cuda_stream);
 
+/* Paper: Sec. II-B-3 (the f-k migrations the paper evaluates next to the
+ * beamformers).  Plane-wave f-k migration of one device-resident frame: per
+ * angle the records' spectrum along time (zero-padded to nt, the power of two
+ * >= 2 n_samples), the transmit's lateral delay x_i sin(theta) / c removed,
+ * the spectrum along the elements (zero-padded to nk >= 2 n_elements), then
+ * every output wavenumber (Kx, Kz > 0) takes the temporal frequency
+ * f = c k / (2 pi), k = (Kx^2 + Kz^2) / (2 (Kx sin + Kz cos)) (the exact
+ * mapping of the delay model above), interpolated linearly and weighted by
+ * dk/dKz where the receive wave propagates; the angles' spectra are summed and
+ * transformed back.  Output on the native grid, not the handle's pixel grid:
+ * out_dev float [n_elements][n_samples], column i at element i, row m at depth
+ * m c / (2 fs), holding |image| (flags BF_OUT_RF or BF_OUT_ENV) or its -70 dB
+ * log compression (BF_OUT_LOGDB); no other flag bits.  Needs equally spaced
+ * elements (2 to 2048), 2 <= n_samples <= 4096; BF_EINVAL otherwise.  Enqueued
+ * on the handle's stream; uses scratch owned by the handle. */
+BF_API int bf_fkmig(bf_handle *h, const int16_t *rf_dev, int32_t n_samples,
+                    const double *angles_rad, int32_t n_angles, uint32_t mode_and_flags,
+                    float *out_dev);
+
 /* Paper: Eq. (2)-(3), Sec. II-B-2.
  * Order p of the pDAS combiner of this handle: each delayed sample is
  * compressed to sign(v) |v|^(1/p) before the channel sum, and the sum is

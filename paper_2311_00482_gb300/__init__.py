@@ -32,7 +32,7 @@ _NAMES = {-1: "BF_EINVAL", -2: "BF_EAGAIN", -3: "BF_ENOMEM", -4: "BF_ECUDA", -5:
 
 EXPORTED = ("bf_create", "bf_destroy", "bf_set_stream", "bf_set_pdas_order", "bf_output_bytes",
             "bf_beamform",
-            "bf_beamform_plain",
+            "bf_beamform_plain", "bf_fkmig",
             "bf_submit", "bf_poll", "bf_ticket_batch", "bf_ticket_times", "bf_engine_pause",
             "bf_engine_configure", "bf_sync",
             "bf_batch_create", "bf_batch_launch", "bf_batch_status", "bf_batch_timing",
@@ -90,6 +90,7 @@ def load(path: str | None = None):
         "bf_output_bytes": ([vp, u32], ctypes.c_size_t),
         "bf_beamform": ([vp, vp, i32, dp, i32, u32, vp], ctypes.c_int),
         "bf_beamform_plain": ([vp, vp, i32, dp, i32, u32, vp], ctypes.c_int),
+        "bf_fkmig": ([vp, vp, i32, dp, i32, u32, vp], ctypes.c_int),
         "bf_submit": ([vp, vp, i32, dp, i32, u32, ctypes.POINTER(u64)], ctypes.c_int),
         "bf_poll": ([vp, u64, vp, ctypes.c_size_t, i64], ctypes.c_int),
         "bf_ticket_batch": ([vp, u64, ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
@@ -214,6 +215,13 @@ def bf_beamform_plain(h, rf_dev, n_samples, angles_rad, flags, out_dev):
     a, ap = _angles(angles_rad)
     return _check(load().bf_beamform_plain(h, _ptr(rf_dev), int(n_samples), ap, len(a), int(flags),
                                            _ptr(out_dev)))
+
+
+def bf_fkmig(h, rf_dev, n_samples, angles_rad, flags, out_dev):
+    """Plane-wave f-k migration onto the native grid [n_elements][n_samples] (see include/bf.h)."""
+    a, ap = _angles(angles_rad)
+    return _check(load().bf_fkmig(h, _ptr(rf_dev), int(n_samples), ap, len(a), int(flags),
+                                  _ptr(out_dev)))
 
 
 def bf_plan_info(h, n_samples, angles_rad, flags, with_windows=False):

@@ -938,6 +938,129 @@ BF_API int bf_beamform(bf_handle *h, const int16_t *rf_dev, int32_t n_samples,
     return rc;
 }
 
+// Plane-wave f-k migration of one device-resident frame onto the native grid
+// (one column per element, depth step c / (2 fs)).
+BF_API int bf_fkmig(bf_handle *h, const int16_t *rf_dev, int32_t n_samples,
+                    const double *angles_rad, int32_t n_angles, uint32_t flags, float *out_dev)
+{
+    if (!h)
+        return fail(BF_EINVAL, "null handle");
+    if (!rf_dev || !out_dev || !angles_rad)
+        return fail(BF_EINVAL, "null argument");
+    if (flags & ~(uint32_t)BF_OUT_MASK)
+        return fail(BF_EINVAL, "bf_fkmig takes only an output stage in its flags");
+    const int stage = flags & BF_OUT_MASK;
+    if (stage != BF_OUT_RF && stage != BF_OUT_ENV && stage != BF_OUT_LOGDB)
+        return fail(BF_EINVAL, "unknown output stage bits");
+    if (n_samples < 2 || n_samples > 4096)
+        return fail(BF_EINVAL, "bf_fkmig handles 2 <= n_samples <= 4096 (got %d)", n_samples);
+    if (n_angles < 1 || n_angles > 256)
+        return fail(BF_EINVAL, "n_angles must be in [1, 256], got %d", n_angles);
+    for (int a = 0; a < n_angles; ++a)
+        if (!std::isfinite(angles_rad[a]) || std::fabs(angles_rad[a]) >= 1.5707963267948966)
+            return fail(BF_EINVAL, "angle %d (%g rad) outside (-pi/2, pi/2)", a, angles_rad[a]);
+    const int ne = h->g.ne;
+    if (ne < 2 || ne > 2048)
+        return fail(BF_EINVAL, "bf_fkmig needs 2 to 2048 elements (got %d)", ne);
+    const double pitch = (h->g.xe[ne - 1] - h->g.xe[0]) / (double)(ne - 1);
+    for (int i = 0; i < ne; ++i)
+        if (std::fabs(h->g.xe[i] - (h->g.xe[0] + i * pitch)) > 1e-9 * std::fabs(pitch) * ne)
+            return fail(BF_EINVAL, "bf_fkmig needs equally spaced elements");
+    cudaSetDevice(h->device);
+    if (!is_device_pointer(rf_dev) || !is_device_pointer(out_dev))
+        return fail(BF_EINVAL, "bf_fkmig needs device pointers");
+    int nt = 1, lgt = 0, nk = 1, lgk = 0;
+    while (nt < 2 * n_samples) {
+        nt <<= 1;
+        ++lgt;
+    }
+    while (nk < 2 * ne) {
+        nk <<= 1;
+        ++lgk;
+    }
+    const double c = h->g.c, fs = h->g.fs, dz = c / (2.0 * fs);
+    std::vector<float> beta((size_t)n_angles * ne);
+    std::vector<double> sc((size_t)2 * n_angles);
+    for (int a = 0; a < n_angles; ++a) {
+        sc[2 * a] = std::sin(angles_rad[a]);
+        sc[2 * a + 1] = std::cos(angles_rad[a]);
+        for (int i = 0; i < ne; ++i) {
+            const double x = ((double)i - 0.5 * (double)(ne - 1)) * pitch;
+            beta[(size_t)a * ne + i] = (float)(kPi * x * sc[2 * a] / ((double)nt * dz));
+        }
+    }
+    std::shared_ptr<EnvTablesDev> tt, tk;
+    int rc = env_tables(nt, tt);
+    if (!rc)
+        rc = env_tables(nk, tk);
+    const size_t nf = (size_t)nt / 2 + 1, img = (size_t)ne * n_samples;
+    if (!rc)
+        rc = h->fk_D.ensure((size_t)n_angles * nf * nk * sizeof(float2));
+    if (!rc)
+        rc = h->fk_spec.ensure((size_t)(nt / 2) * nk * sizeof(float2));
+    if (!rc && stage == BF_OUT_LOGDB)
+        rc = h->fk_img.ensure(img * sizeof(float));
+    if (!rc)
+        rc = h->fk_max.ensure(sizeof(unsigned));
+    if (!rc)
+        rc = h->fk_beta.ensure(beta.size() * sizeof(float));
+    if (!rc)
+        rc = h->fk_sc.ensure(sc.size() * sizeof(double));
+    if (rc)
+        return rc;
+    h->call.clear();  // the device tables above may have moved
+    cudaStream_t st = h->stream;
+    cudaError_t e = cudaMemcpyAsync(h->fk_beta.p, beta.data(), beta.size() * sizeof(float),
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->fk_sc.p, sc.data(), sc.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && stage == BF_OUT_LOGDB)
+        e = cudaMemsetAsync(h->fk_max.p, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "bf_fkmig setup");
+    FkJob J{};
+    J.rf = rf_dev;
+    J.D = (float2 *)h->fk_D.p;
+    J.spec = (float2 *)h->fk_spec.p;
+    J.img = stage == BF_OUT_LOGDB ? (float *)h->fk_img.p : out_dev;
+    J.maxbits = stage == BF_OUT_LOGDB ? (unsigned *)h->fk_max.p : nullptr;
+    J.beta = (const float *)h->fk_beta.p;
+    J.sc = (const double *)h->fk_sc.p;
+    J.tw_t = (const float2 *)tt->tw.p;
+    J.tw_k = (const float2 *)tk->tw.p;
+    J.r = (double)nt * dz / ((double)nk * pitch);
+    J.na = n_angles;
+    J.ne = ne;
+    J.ns = n_samples;
+    J.nt = nt;
+    J.lgt = lgt;
+    J.nk = nk;
+    J.lgk = lgk;
+    e = launch_fkmig(J, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "f-k migration launch");
+    if (stage == BF_OUT_LOGDB) {
+        // the log stage of the beamformer, one job over the native image
+        LogJob l{};
+        l.env = J.img;
+        l.out = out_dev;
+        l.maxbits = J.maxbits;
+        l.n = (int)img;
+        l.vec4 = (img % 4 == 0 && ((uintptr_t)l.env & 15) == 0 && ((uintptr_t)l.out & 15) == 0) ? 1 : 0;
+        rc = h->fk_log.upload(&l, sizeof l);
+        int zero = 0;
+        if (!rc)
+            rc = h->fk_logp.upload(&zero, sizeof zero);
+        if (rc)
+            return rc;
+        e = launch_log((const LogJob *)h->fk_log.p, (const int *)h->fk_logp.p, 1,
+                       log_blocks((long long)img), 70.0f, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "log launch");
+    }
+    return BF_OK;
+}
+
 BF_API int bf_beamform_plain(bf_handle *h, const int16_t *rf_dev, int32_t n_samples,
                              const double *angles_rad, int32_t n_angles, uint32_t flags,
                              float *out_dev)

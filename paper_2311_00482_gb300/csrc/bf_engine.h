@@ -189,6 +189,7 @@ struct bf_handle {
     bfi::FrameScratch scratch;     // bf_beamform
     bfi::DeviceLaunch launch;      // bf_beamform
     bfi::CallCache call;           // bf_beamform's last call
+    bfi::DevMem fk_D, fk_spec, fk_img, fk_beta, fk_sc, fk_max, fk_log, fk_logp;  // bf_fkmig scratch
     bool err_cleared = false;
     std::map<uint64_t, std::shared_ptr<bfi::Request>> tickets;
 };

@@ -112,6 +112,21 @@ struct DemodJob {
     const float2 *tw;     // [ns] exp(-2 pi i k / ns)
 };
 
+// Plane-wave f-k migration of one frame (all its angles): see bf_fkmig.
+struct FkJob {
+    const int16_t *rf;    // [na][ne][ns]
+    float2 *D;            // [na][nt/2 + 1][nk] per-angle spectra (time, then lateral transform)
+    float2 *spec;         // [nt/2][nk] migrated spectrum, rows Kz bin q = 1 .. nt/2
+    float *img;           // [ne][ns] magnitude image
+    unsigned *maxbits;    // image maximum (float bits) for the log stage, or null
+    const float *beta;    // [na][ne] pi x_i sin(theta_a) / (nt dz): lateral phase per time bin
+    const double *sc;     // [na][2] sin, cos of the angles
+    const float2 *tw_t;   // [nt] exp(-2 pi i k / nt)
+    const float2 *tw_k;   // [nk] exp(-2 pi i k / nk)
+    double r;             // nt dz / (nk pitch): lateral bin in units of temporal bins
+    int na, ne, ns, nt, lgt, nk, lgk;
+};
+
 // One (frame, mode) image through the analytic-signal envelope along z.
 struct EnvJob {
     const float *y;       // [nx][nz] beamformed image
@@ -148,6 +163,8 @@ cudaError_t launch_ingest(const IngestJob *jobs_dev, const int *row_prefix_dev, 
 cudaError_t launch_demod(const DemodJob *jobs_dev, const int *row_prefix_dev, int njobs,
                          int total_rows, int max_ns, cudaStream_t stream);
 size_t demod_smem_bytes(int ns);
+// f-k migration launches (bf_kernels.cu), in order on `stream`.
+cudaError_t launch_fkmig(const FkJob &job, cudaStream_t stream);
 cudaError_t launch_beamform(const BfJob *jobs_dev, const int *tile_prefix_dev, int njobs,
                             int total_tiles, size_t smem_bytes, int prec, int variant, int rows,
                             int *err_dev, cudaStream_t stream);

@@ -1178,6 +1178,135 @@ __global__ void __launch_bounds__(256) envelope_kernel(const EnvJob *__restrict_
     }
 }
 
+// ------------------------------------------------------------ f-k migration --
+
+// Per channel record: transform along time (zero-padded to nt), then the
+// transmit's lateral delay removed per bin, written to D[a][b][i].
+__global__ void __launch_bounds__(256) fk_time_kernel(const FkJob J)
+{
+    extern __shared__ __align__(16) float2 fbuf[];
+    const int row = blockIdx.x, a = row / J.ne, i = row - a * J.ne;
+    const int m = J.nt;
+    float2 *X = fbuf, *Y = fbuf + m, *tw = fbuf + 2 * (size_t)m;
+    const int16_t *__restrict__ u = J.rf + (size_t)row * J.ns;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        tw[k] = __ldg(J.tw_t + k);
+        X[k] = make_float2(k < J.ns ? (float)__ldg(u + k) : 0.f, 0.f);
+    }
+    __syncthreads();
+    const float2 *S = fft_r8(X, Y, m, J.lgt, 1, tw, false);
+    const float beta = __ldg(J.beta + row);
+    const int nf = m / 2 + 1;
+    float2 *__restrict__ D = J.D + (size_t)a * nf * J.nk + i;
+    for (int b = threadIdx.x; b < nf; b += blockDim.x) {
+        float sn, cs;
+        sincosf((float)b * beta, &sn, &cs);
+        D[(size_t)b * J.nk] = cmul(S[b], make_float2(cs, sn));
+    }
+}
+
+// Transforms of `rows` rows of length n held with stride n: entries from
+// len_in on are taken as zero; `per` rows per CTA.
+__global__ void __launch_bounds__(256) fk_rows_kernel(float2 *data, int rows, int len_in, int n,
+                                                      int lg, int per, const float2 *tw_g,
+                                                      int inverse)
+{
+    extern __shared__ __align__(16) float2 fbuf[];
+    float2 *X = fbuf, *Y = fbuf + (size_t)per * n, *tw = fbuf + 2 * (size_t)per * n;
+    const int r0 = blockIdx.x * per;
+    const int nr = min(per, rows - r0);
+    for (int k = threadIdx.x; k < n; k += blockDim.x)
+        tw[k] = __ldg(tw_g + k);
+    for (int t = threadIdx.x; t < per * n; t += blockDim.x) {
+        const int rr = t / n, k = t - rr * n;
+        X[t] = (rr < nr && k < len_in) ? data[(size_t)(r0 + rr) * n + k] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const float2 *S = fft_r8(X, Y, n, lg, per, tw, inverse != 0);
+    for (int t = threadIdx.x; t < nr * n; t += blockDim.x)
+        data[(size_t)r0 * n + t] = S[t];
+}
+
+// Migrated spectrum at (q = 1 .. nt/2, m): every angle's temporal bin
+// pos = (X^2 + Q^2) / (X sin + Q cos) of lateral bin m, interpolated and
+// weighted by dk/dKz, summed.  The mapping's decisions and the bin position
+// are formed in double precision without fused multiply-adds.
+__global__ void __launch_bounds__(256) fk_map_kernel(const FkJob J)
+{
+    const int nk = J.nk, half = J.nt / 2;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)half * nk)
+        return;
+    const int q = (int)(idx / nk) + 1, m = (int)(idx - (long long)(q - 1) * nk);
+    const double X = __dmul_rn((double)(m < nk / 2 ? m : m - nk), J.r);
+    const double Q = (double)q;
+    const double num = __dadd_rn(__dmul_rn(X, X), __dmul_rn(Q, Q));
+    const int nf = half + 1;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int a = 0; a < J.na; ++a) {
+        const double st = __ldg(J.sc + 2 * a), ct = __ldg(J.sc + 2 * a + 1);
+        const double den = __dadd_rn(__dmul_rn(X, st), __dmul_rn(Q, ct));
+        if (!(den > 0.0))
+            continue;
+        const double pos = __ddiv_rn(num, den);
+        if (!(fabs(__dsub_rn(__dmul_rn(2.0, X), __dmul_rn(pos, st))) <= pos) || !(pos >= 0.0) ||
+            !(pos < (double)half))
+            continue;
+        const double w = __ddiv_rn(__dsub_rn(__dmul_rn(Q, den), __dmul_rn(__dmul_rn(0.5, num), ct)),
+                                   __dmul_rn(den, den));
+        const double fl = floor(pos);
+        const int i0 = (int)fl, i1 = min(i0 + 1, half);
+        const float al = (float)(pos - fl);
+        const float2 *D = J.D + (size_t)a * nf * nk + m;
+        const float2 v0 = D[(size_t)i0 * nk], v1 = D[(size_t)i1 * nk];
+        const float wf = (float)w;
+        acc.x = fmaf(wf, fmaf(al, v1.x - v0.x, v0.x), acc.x);
+        acc.y = fmaf(wf, fmaf(al, v1.y - v0.y, v0.y), acc.y);
+    }
+    J.spec[idx] = acc;
+}
+
+// Per image column m < ne: inverse transform along depth of the migrated
+// spectrum's column (Kz bins 1 .. nt/2, zero elsewhere), magnitude of the
+// first ns samples (the 1 / (nt nk) of both inverse transforms applied here).
+__global__ void __launch_bounds__(256) fk_depth_kernel(const FkJob J)
+{
+    extern __shared__ __align__(16) float2 fbuf[];
+    __shared__ float red[32];
+    const int mcol = blockIdx.x, n = J.nt, half = n / 2;
+    float2 *X = fbuf, *Y = fbuf + n, *tw = fbuf + 2 * (size_t)n;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        tw[k] = __ldg(J.tw_t + k);
+        X[k] = (k >= 1 && k <= half) ? J.spec[(size_t)(k - 1) * J.nk + mcol] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const float2 *S = fft_r8(X, Y, n, J.lgt, 1, tw, true);
+    const float inv = 1.f / ((float)n * (float)J.nk);
+    float lmax = 0.f;
+    float *__restrict__ out = J.img + (size_t)mcol * J.ns;
+    for (int z = threadIdx.x; z < J.ns; z += blockDim.x) {
+        const float e = hypotf(S[z].x, S[z].y) * inv;
+        out[z] = e;
+        lmax = fmaxf(lmax, e);
+    }
+    if (J.maxbits) {
+#pragma unroll
+        for (int off = 16; off; off >>= 1)
+            lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, off));
+        if ((threadIdx.x & 31) == 0)
+            red[threadIdx.x >> 5] = lmax;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+#pragma unroll
+            for (int off = 16; off; off >>= 1)
+                v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+            if (threadIdx.x == 0)
+                atomicMax(J.maxbits, __float_as_uint(v));
+        }
+    }
+}
+
 // ------------------------------------------------------------------ log --
 
 constexpr int kLogPerBlock = 1024;
@@ -1410,5 +1539,41 @@ cudaError_t launch_log(const LogJob *jobs_dev, const int *blk_prefix_dev, int nj
 }
 
 int log_blocks(long long pixels) { return (int)((pixels + kLogPerBlock - 1) / kLogPerBlock); }
+
+static cudaError_t smem_attr(const void *k, size_t smem, size_t &configured)
+{
+    if (smem <= 48u * 1024u || smem <= configured)
+        return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        configured = smem;
+    return e;
+}
+
+cudaError_t launch_fkmig(const FkJob &J, cudaStream_t st)
+{
+    static size_t c_time = 0, c_rows = 0, c_depth = 0;
+    const size_t s_nt = (size_t)3 * J.nt * sizeof(float2);
+    cudaError_t e = smem_attr((const void *)fk_time_kernel, s_nt, c_time);
+    if (e == cudaSuccess)
+        e = smem_attr((const void *)fk_depth_kernel, s_nt, c_depth);
+    const int per = J.nk >= 2048 ? 1 : 2048 / J.nk;
+    const size_t s_rows = ((size_t)2 * per * J.nk + J.nk) * sizeof(float2);
+    if (e == cudaSuccess)
+        e = smem_attr((const void *)fk_rows_kernel, s_rows, c_rows);
+    if (e != cudaSuccess)
+        return e;
+    const int nf = J.nt / 2 + 1, half = J.nt / 2;
+    fk_time_kernel<<<J.na * J.ne, 256, s_nt, st>>>(J);
+    const int drows = J.na * nf;
+    fk_rows_kernel<<<(drows + per - 1) / per, 256, s_rows, st>>>(J.D, drows, J.ne, J.nk, J.lgk, per,
+                                                                   J.tw_k, 0);
+    const long long pts = (long long)half * J.nk;
+    fk_map_kernel<<<(int)((pts + 255) / 256), 256, 0, st>>>(J);
+    fk_rows_kernel<<<(half + per - 1) / per, 256, s_rows, st>>>(J.spec, half, J.nk, J.nk, J.lgk, per,
+                                                                  J.tw_k, 1);
+    fk_depth_kernel<<<J.ne, 256, s_nt, st>>>(J);
+    return cudaGetLastError();
+}
 
 }  // namespace bfi
