@@ -400,6 +400,71 @@ __host__ __device__ __forceinline__ int stage_bytes(int group, int wmax, int pb)
     return group * (kTileCols * 12 + wmax * pb);
 }
 
+// ---- packed FP32 pairs (Blackwell f32x2 arithmetic): two rows' delays at once
+typedef unsigned long long f32x2_t;
+
+__device__ __forceinline__ f32x2_t pk2(float lo, float hi)
+{
+    f32x2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void upk2(f32x2_t v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ f32x2_t fma2(f32x2_t a, f32x2_t b, f32x2_t c)
+{
+    f32x2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ f32x2_t add2(f32x2_t a, f32x2_t b)
+{
+    f32x2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f32x2_t sub2(f32x2_t a, f32x2_t b)
+{
+    f32x2_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f32x2_t mul2(f32x2_t a, f32x2_t b)
+{
+    f32x2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// Rounded delays of rows j and j + 1 for one channel (d2 packed twice): the
+// rx_excess arithmetic of both rows in paired instructions, each half with
+// exactly the scalar version's operations and roundings.  m holds the delay
+// plus the rounding constant (integer in its low bits), al the offset in
+// [-1/2, 1/2].
+__device__ __forceinline__ void delay2(f32x2_t D2, float Za, float Zb, float fa, float fb,
+                                       float &ma, float &mb, float &ala, float &alb)
+{
+    const f32x2_t Zp = pk2(Za, Zb);
+    const f32x2_t s = fma2(Zp, Zp, D2);
+    float sa, sb;
+    upk2(s, sa, sb);
+    const f32x2_t r = mul2(s, pk2(rsqrt_approx(sa), rsqrt_approx(sb)));
+    float da, db;
+    upk2(add2(r, Zp), da, db);
+    const f32x2_t x = fma2(D2, pk2(rcp_approx(da), rcp_approx(db)), pk2(fa, fb));
+    const f32x2_t MG = pk2(kRoundMagic, kRoundMagic);
+    const f32x2_t m = add2(x, MG);
+    upk2(m, ma, mb);
+    upk2(sub2(x, sub2(m, MG)), ala, alb);
+}
+
 // Accumulate one channel into the ROWS pixels of this thread.  CHECK: test
 // every pixel's row against the channel's counted rows (otherwise the whole
 // row band of the warp counts it).
@@ -410,25 +475,31 @@ __device__ __forceinline__ void accumulate(uint32_t win, int wmax, int w0, float
                                            float *Su2, float *P1, float inv_p, bool square)
 {
     constexpr int PB = PairIO<PREC>::kBytes;
+    static_assert(ROWS % 2 == 0, "rows are processed in pairs");
     const unsigned span = (unsigned)(vr.y - vr.x);
+    const f32x2_t D2 = pk2(d2, d2);
 #pragma unroll
-    for (int j = 0; j < ROWS; ++j) {
-        const float x = rx_excess(d2, Z[j]) + fp[j];
-        const float m = x + kRoundMagic;
-        const float al = x - (m - kRoundMagic);  // in [-1/2, 1/2]
-        const unsigned idx = min((unsigned)(__float_as_int(m) + Kc[j] - w0), (unsigned)(wmax - 1));
-        const float v = PairIO<PREC>::interp(win + idx * PB, al);
-        if (!CHECK || (unsigned)(r_first + j - vr.x) <= span) {
-            S1[j] += v;
-            if (DMAS) {
-                const float av = fabsf(v);
-                T1[j] += copysignf(sqrt_approx(av), v);
-                T2[j] += av;
+    for (int j = 0; j < ROWS; j += 2) {
+        float m[2], al[2];  // al in [-1/2, 1/2]
+        delay2(D2, Z[j], Z[j + 1], fp[j], fp[j + 1], m[0], m[1], al[0], al[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int jj = j + h;
+            const unsigned idx =
+                min((unsigned)(__float_as_int(m[h]) + Kc[jj] - w0), (unsigned)(wmax - 1));
+            const float v = PairIO<PREC>::interp(win + idx * PB, al[h]);
+            if (!CHECK || (unsigned)(r_first + jj - vr.x) <= span) {
+                S1[jj] += v;
+                if (DMAS) {
+                    const float av = fabsf(v);
+                    T1[jj] += copysignf(sqrt_approx(av), v);
+                    T2[jj] += av;
+                }
+                if (CF)
+                    Su2[jj] = fmaf(v, v, Su2[jj]);
+                if (PDAS)
+                    P1[jj] += pdas_root(v, inv_p, square);
             }
-            if (CF)
-                Su2[j] = fmaf(v, v, Su2[j]);
-            if (PDAS)
-                P1[j] += pdas_root(v, inv_p, square);
         }
     }
 }
@@ -444,26 +515,32 @@ __device__ __forceinline__ void accumulate2(uint32_t win0, int w00, float d20, u
                                             bool square)
 {
     constexpr int PB = PairIO<PREC>::kBytes;
+    const f32x2_t D20 = pk2(d20, d20), D21 = pk2(d21, d21);
 #pragma unroll
-    for (int j = 0; j < ROWS; ++j) {
-        const float x0 = rx_excess(d20, Z[j]) + fp[j];
-        const float x1 = rx_excess(d21, Z[j]) + fp[j];
-        const float m0 = x0 + kRoundMagic, m1 = x1 + kRoundMagic;
-        const float al0 = x0 - (m0 - kRoundMagic), al1 = x1 - (m1 - kRoundMagic);
-        const unsigned i0 = min((unsigned)(__float_as_int(m0) + Kc[j] - w00), (unsigned)(wmax - 1));
-        const unsigned i1 = min((unsigned)(__float_as_int(m1) + Kc[j] - w01), (unsigned)(wmax - 1));
-        const float v0 = PairIO<PREC>::interp(win0 + i0 * PB, al0);
-        const float v1 = PairIO<PREC>::interp(win1 + i1 * PB, al1);
-        S1[j] += v0 + v1;
-        if (DMAS) {
-            const float a0 = fabsf(v0), a1 = fabsf(v1);
-            T1[j] += copysignf(sqrt_approx(a0), v0) + copysignf(sqrt_approx(a1), v1);
-            T2[j] += a0 + a1;
+    for (int j = 0; j < ROWS; j += 2) {
+        float m0[2], al0[2], m1[2], al1[2];
+        delay2(D20, Z[j], Z[j + 1], fp[j], fp[j + 1], m0[0], m0[1], al0[0], al0[1]);
+        delay2(D21, Z[j], Z[j + 1], fp[j], fp[j + 1], m1[0], m1[1], al1[0], al1[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int jj = j + h;
+            const unsigned i0 =
+                min((unsigned)(__float_as_int(m0[h]) + Kc[jj] - w00), (unsigned)(wmax - 1));
+            const unsigned i1 =
+                min((unsigned)(__float_as_int(m1[h]) + Kc[jj] - w01), (unsigned)(wmax - 1));
+            const float v0 = PairIO<PREC>::interp(win0 + i0 * PB, al0[h]);
+            const float v1 = PairIO<PREC>::interp(win1 + i1 * PB, al1[h]);
+            S1[jj] += v0 + v1;
+            if (DMAS) {
+                const float a0 = fabsf(v0), a1 = fabsf(v1);
+                T1[jj] += copysignf(sqrt_approx(a0), v0) + copysignf(sqrt_approx(a1), v1);
+                T2[jj] += a0 + a1;
+            }
+            if (CF)
+                Su2[jj] = fmaf(v0, v0, fmaf(v1, v1, Su2[jj]));
+            if (PDAS)
+                P1[jj] += pdas_root(v0, inv_p, square) + pdas_root(v1, inv_p, square);
         }
-        if (CF)
-            Su2[j] = fmaf(v0, v0, fmaf(v1, v1, Su2[j]));
-        if (PDAS)
-            P1[j] += pdas_root(v0, inv_p, square) + pdas_root(v1, inv_p, square);
     }
 }
 
