@@ -134,12 +134,18 @@ static __device__ float2 *fft_r8(float2 *x, float2 *y, int m, int lgm, int cols,
             const int r = j & (ns - 1), k1 = r << sh;
             float2 v[8];
             v[0] = xc[j];
+            if (ns == 1) {  // first pass: every twiddle is 1
 #pragma unroll
-            for (int p = 1; p < 8; ++p) {
-                float2 w = tw[p * k1];
-                if (inverse)
-                    w.y = -w.y;
-                v[p] = cmul(xc[j + p * q], w);
+                for (int p = 1; p < 8; ++p)
+                    v[p] = xc[j + p * q];
+            } else {
+#pragma unroll
+                for (int p = 1; p < 8; ++p) {
+                    float2 w = tw[p * k1];
+                    if (inverse)
+                        w.y = -w.y;
+                    v[p] = cmul(xc[j + p * q], w);
+                }
             }
             dft8(v, inverse);
             const int o = ((j - r) << 3) + r;

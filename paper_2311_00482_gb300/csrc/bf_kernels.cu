@@ -567,25 +567,31 @@ __device__ __forceinline__ void accumulate_iq(uint32_t win, int wmax, int w0, fl
                                               float *Yi, float *Tr, float *Ti)
 {
     const unsigned span = (unsigned)(vr.y - vr.x);
+    const f32x2_t D2 = pk2(d2, d2);
 #pragma unroll
-    for (int j = 0; j < ROWS; ++j) {
-        const float x = rx_excess(d2, Z[j]) + fp[j];
-        const float m = x + kRoundMagic;
-        const float al = x - (m - kRoundMagic);  // alpha - 1/2
-        const unsigned idx = min((unsigned)(__float_as_int(m) + Kc[j] - w0), (unsigned)(wmax - 1));
-        const float4 p = lds_f32x4(win + idx * 16u);
-        const float br = fmaf(al, p.z, p.x), bi = fmaf(al, p.w, p.y);
-        float sn, cs;
-        __sincosf(fmaf(al, c1, c2), &sn, &cs);
-        const float sr = fmaf(br, cs, -bi * sn), si = fmaf(br, sn, bi * cs);
-        if (!CHECK || (unsigned)(r_first + j - vr.x) <= span) {
-            Yr[j] += sr;
-            Yi[j] += si;
-            if (BB) {
-                // |s|^(-1/2); the floor keeps s = 0 at 0 instead of 0 * inf
-                const float w = rsqrt_approx(sqrt_approx(fmaf(sr, sr, fmaf(si, si, 1e-30f))));
-                Tr[j] = fmaf(sr, w, Tr[j]);
-                Ti[j] = fmaf(si, w, Ti[j]);
+    for (int j = 0; j < ROWS; j += 2) {
+        float mm[2], aa[2];
+        delay2(D2, Z[j], Z[j + 1], fp[j], fp[j + 1], mm[0], mm[1], aa[0], aa[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int jj = j + h;
+            const float al = aa[h];  // alpha - 1/2
+            const unsigned idx =
+                min((unsigned)(__float_as_int(mm[h]) + Kc[jj] - w0), (unsigned)(wmax - 1));
+            const float4 p = lds_f32x4(win + idx * 16u);
+            const float br = fmaf(al, p.z, p.x), bi = fmaf(al, p.w, p.y);
+            float sn, cs;
+            __sincosf(fmaf(al, c1, c2), &sn, &cs);
+            const float sr = fmaf(br, cs, -bi * sn), si = fmaf(br, sn, bi * cs);
+            if (!CHECK || (unsigned)(r_first + jj - vr.x) <= span) {
+                Yr[jj] += sr;
+                Yi[jj] += si;
+                if (BB) {
+                    // |s|^(-1/2); the floor keeps s = 0 at 0 instead of 0 * inf
+                    const float w = rsqrt_approx(sqrt_approx(fmaf(sr, sr, fmaf(si, si, 1e-30f))));
+                    Tr[jj] = fmaf(sr, w, Tr[jj]);
+                    Ti[jj] = fmaf(si, w, Ti[jj]);
+                }
             }
         }
     }
