@@ -498,13 +498,15 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
                 ++d.lgn;
             d.rot = make_float2((float)std::cos(2.0 * kPi * r), (float)-std::sin(2.0 * kPi * r));
             d.tw = (const float2 *)f.dt->tw.p;
+            d.maxbits = f.stage != BF_OUT_RF ? f.maxbits : nullptr;
             hl.demod_prefix.push_back(hl.demod_rows);
             hl.demod_rows += d.rows;
             hl.demod_max_ns = std::max(hl.demod_max_ns, f.ns);
             hl.demod.push_back(d);
             continue;
         }
-        ig[f.prec].push_back(IngestJob{f.rf, f.pairs, f.na * f.h->g.ne, f.ns, f.plan->nsp});
+        ig[f.prec].push_back(IngestJob{f.rf, f.pairs, f.na * f.h->g.ne, f.ns, f.plan->nsp,
+                                       f.stage != BF_OUT_RF ? f.maxbits : nullptr});
     }
     for (auto &kv : ig) {
         HostLaunch::IGroup g;
@@ -673,13 +675,7 @@ int enqueue(const std::vector<FramePrep> &frames, const HostLaunch &hl, DeviceLa
         if (e != cudaSuccess)
             return cuda_fail(e, "demodulation launch");
     }
-    for (const FramePrep &f : frames) {
-        if (f.stage != BF_OUT_RF) {
-            e = cudaMemsetAsync(f.maxbits, 0, 4 * sizeof(unsigned), st);
-            if (e != cudaSuccess)
-                return cuda_fail(e, "cudaMemsetAsync");
-        }
-    }
+    // (the ingest / demodulation launches above zeroed each frame's image maxima)
     if (marks)
         cudaEventRecordWithFlags(marks[1], st, mark_flags);
     for (const HostLaunch::Group &g : hl.groups) {

@@ -97,6 +97,7 @@ struct IngestJob {
     const int16_t *rf;    // [rows][ns]
     void *pairs;          // [rows][nsp]
     int rows, ns, nsp;
+    unsigned *maxbits;    // the frame's 4 image maxima, zeroed by the job's first CTA (or null)
 };
 
 // One frame's int16 records to complex analytic-signal pairs for IQ
@@ -110,6 +111,7 @@ struct DemodJob {
     int rows, ns, nsp, lgn;
     float2 rot;           // exp(-j 2 pi f0 / fs)
     const float2 *tw;     // [ns] exp(-2 pi i k / ns)
+    unsigned *maxbits;    // the frame's image maxima, zeroed by the job's first CTA (or null)
 };
 
 // Plane-wave f-k migration of one frame (all its angles): see bf_fkmig.

@@ -235,6 +235,8 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestJob *__restrict
     const int jb = find_job(row_prefix, njobs, blockIdx.x);
     const IngestJob J = jobs[jb];
     const int row = blockIdx.x - __ldg(row_prefix + jb);
+    if (row == 0 && J.maxbits && threadIdx.x < 4)  // before any later kernel takes a maximum
+        J.maxbits[threadIdx.x] = 0u;
     const int16_t *__restrict__ u = J.rf + (size_t)row * J.ns;
     const int ns = J.ns;
     auto sample = [&](int k) -> int { return (k >= 0 && k < ns) ? (int)__ldg(u + k) : 0; };
@@ -290,6 +292,8 @@ __global__ void __launch_bounds__(256) demod_kernel(const DemodJob *__restrict__
     const int jb = find_job(row_prefix, njobs, blockIdx.x);
     const DemodJob J = jobs[jb];
     const int row = blockIdx.x - __ldg(row_prefix + jb);
+    if (row == 0 && J.maxbits && threadIdx.x < 4)  // before any later kernel takes a maximum
+        J.maxbits[threadIdx.x] = 0u;
     const int m = J.ns, lgm = J.lgn;
     float2 *X = dbuf, *Y = dbuf + m, *tw = dbuf + 2 * (size_t)m;
     const int16_t *__restrict__ u = J.rf + (size_t)row * m;
