@@ -190,6 +190,23 @@ BF_API int bf_submit(bf_handle *h, const int16_t *rf, int32_t n_samples,
 BF_API int bf_poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes,
                    int64_t timeout_us);
 
+/* Paper: as bf_submit.  n frames of one geometry, sample count, angle set and
+ * flags in one call: rf[k] (host or device) is frame k, tickets_out[k] its
+ * ticket.  Every source has been copied when the call returns (one wait for
+ * all the copies instead of one per frame).  *n_submitted (optional) receives
+ * how many frames got tickets: on BF_EAGAIN the rest can be submitted later. */
+BF_API int bf_submit_many(bf_handle *h, int32_t n, const int16_t *const *rf, int32_t n_samples,
+                          const double *angles_rad, int32_t n_angles, uint32_t mode_and_flags,
+                          uint64_t *tickets_out, int32_t *n_submitted);
+
+/* Paper: as bf_poll.  Waits up to timeout_us for all n tickets, then copies
+ * every result into outs[k] (host or device, out_bytes each; outs or outs[k]
+ * NULL discards) with one synchronisation at the end and releases every
+ * ticket; returns the first failure of any ticket (all are released).  On
+ * BF_PENDING / BF_ETIMEDOUT / BF_ENOTFOUND nothing is released. */
+BF_API int bf_poll_many(bf_handle *h, int32_t n, const uint64_t *tickets, float *const *outs,
+                        size_t out_bytes, int64_t timeout_us);
+
 /* Serving-engine introspection: the batch a launched ticket rides in and how
  * many frames that batch holds (BF_PENDING while still queued). */
 BF_API int bf_ticket_batch(bf_handle *h, uint64_t ticket, int32_t *batch_id,

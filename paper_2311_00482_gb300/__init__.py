@@ -33,7 +33,7 @@ _NAMES = {-1: "BF_EINVAL", -2: "BF_EAGAIN", -3: "BF_ENOMEM", -4: "BF_ECUDA", -5:
 EXPORTED = ("bf_create", "bf_destroy", "bf_set_stream", "bf_set_pdas_order", "bf_output_bytes",
             "bf_beamform",
             "bf_beamform_plain", "bf_fkmig",
-            "bf_submit", "bf_poll", "bf_ticket_batch", "bf_ticket_times", "bf_engine_pause",
+            "bf_submit", "bf_poll", "bf_submit_many", "bf_poll_many", "bf_ticket_batch", "bf_ticket_times", "bf_engine_pause",
             "bf_engine_configure", "bf_sync",
             "bf_batch_create", "bf_batch_launch", "bf_batch_status", "bf_batch_timing",
             "bf_batch_destroy",
@@ -93,6 +93,10 @@ def load(path: str | None = None):
         "bf_fkmig": ([vp, vp, i32, dp, i32, u32, vp], ctypes.c_int),
         "bf_submit": ([vp, vp, i32, dp, i32, u32, ctypes.POINTER(u64)], ctypes.c_int),
         "bf_poll": ([vp, u64, vp, ctypes.c_size_t, i64], ctypes.c_int),
+        "bf_submit_many": ([vp, i32, ctypes.POINTER(vp), i32, dp, i32, u32, ctypes.POINTER(u64),
+                            ctypes.POINTER(i32)], ctypes.c_int),
+        "bf_poll_many": ([vp, i32, ctypes.POINTER(u64), ctypes.POINTER(vp), ctypes.c_size_t, i64],
+                         ctypes.c_int),
         "bf_ticket_batch": ([vp, u64, ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
         "bf_engine_configure": ([i32, i32, u64], ctypes.c_int),
         "bf_engine_pause": ([i32], ctypes.c_int),
@@ -276,6 +280,37 @@ def bf_poll(h, ticket, out=None, timeout_us=-1) -> int:
     nbytes = 0 if out is None else (out.nbytes if isinstance(out, np.ndarray)
                                     else out.numel() * out.element_size())
     return _check(load().bf_poll(h, int(ticket), _ptr(out), nbytes, int(timeout_us)),
+                  allow=(BF_OK, BF_PENDING))
+
+
+def bf_submit_many(h, rfs, n_samples, angles_rad, flags):
+    """Submit several frames of one configuration; returns their tickets (raises
+    BFError; on BF_EAGAIN the error's .submitted holds the tickets that got in)."""
+    a, ap = _angles(angles_rad)
+    n = len(rfs)
+    ptrs = (ctypes.c_void_p * n)(*[_ptr(r) for r in rfs])
+    t = (ctypes.c_uint64 * n)()
+    done = ctypes.c_int32()
+    rc = load().bf_submit_many(h, n, ptrs, int(n_samples), ap, len(a), int(flags), t,
+                               ctypes.byref(done))
+    if rc != BF_OK:
+        err = BFError(rc, bf_last_error())
+        err.submitted = [t[k] for k in range(done.value)]
+        raise err
+    return [t[k] for k in range(n)]
+
+
+def bf_poll_many(h, tickets, outs=None, timeout_us=-1) -> int:
+    """Wait for every ticket and copy each result into outs[k]; BF_OK or BF_PENDING."""
+    n = len(tickets)
+    tk = (ctypes.c_uint64 * n)(*[int(x) for x in tickets])
+    nbytes = 0
+    optr = None
+    if outs is not None:
+        optr = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
+        nbytes = min((o.nbytes if isinstance(o, np.ndarray) else o.numel() * o.element_size())
+                     for o in outs)
+    return _check(load().bf_poll_many(h, n, tk, optr, nbytes, int(timeout_us)),
                   allow=(BF_OK, BF_PENDING))
 
 

@@ -287,8 +287,17 @@ public:
     }
 
     int submit(bf_handle *h, const int16_t *rf, int ns, const double *angles, int na,
-               uint32_t flags, uint64_t *ticket);
+               uint32_t flags, uint64_t *ticket, bool wait_copy = true);
     int poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes, int64_t timeout_us);
+    int poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const *outs, size_t out_bytes,
+                  int64_t timeout_us);
+    // the caller's sources of every submission so far have been copied
+    int wait_copies()
+    {
+        cudaSetDevice(device_);
+        cudaError_t e = cudaStreamSynchronize(copy_);
+        return e == cudaSuccess ? BF_OK : cuda_fail(e, "copying the requests' RF");
+    }
     int batch_of(bf_handle *h, uint64_t ticket, int *id, int *frames);
     int times_of(bf_handle *h, uint64_t ticket, double *start_ms, double *end_ms);
     void pause(bool p)
@@ -347,7 +356,7 @@ std::unique_ptr<Slot> Engine::take_slot()
 }
 
 int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles, int na,
-                   uint32_t flags, uint64_t *ticket)
+                   uint32_t flags, uint64_t *ticket, bool wait_copy)
 {
     int rc = check_frame_args(h, ns, angles, na, flags);
     if (rc)
@@ -438,7 +447,7 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
     }
     if (e == cudaSuccess)
         e = cudaEventRecord(s.h2d, copy_);
-    if (e == cudaSuccess && kind != kPageable)
+    if (e == cudaSuccess && kind != kPageable && wait_copy)
         e = cudaEventSynchronize(s.h2d);
     {
         std::lock_guard<std::mutex> lk(mu_);
@@ -631,6 +640,114 @@ int Engine::poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes, in
     return rc;
 }
 
+// Many tickets at once: wait for all their batches, copy every result with
+// one synchronisation at the end, release every ticket.  Nothing is released
+// when a wait times out (BF_ETIMEDOUT) or a ticket is unknown.
+int Engine::poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const *outs,
+                      size_t out_bytes, int64_t timeout_us)
+{
+    std::vector<std::shared_ptr<Request>> reqs((size_t)n);
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        for (int k = 0; k < n; ++k) {
+            auto it = h->tickets.find(tickets[k]);
+            if (it == h->tickets.end())
+                return fail(BF_ENOTFOUND, "unknown ticket %llu", (unsigned long long)tickets[k]);
+            reqs[k] = it->second;
+            if (outs && outs[k] && out_bytes < reqs[k]->out_bytes)
+                return fail(BF_EINVAL, "output buffer too small (%zu < %zu bytes)", out_bytes,
+                            reqs[k]->out_bytes);
+        }
+    }
+    using clk = std::chrono::steady_clock;
+    const auto deadline = clk::now() + std::chrono::microseconds(timeout_us > 0 ? timeout_us : 0);
+    for (auto &req : reqs) {  // launched and finished?
+        {
+            std::unique_lock<std::mutex> lk(mu_);
+            while (req->state == 0) {
+                if (timeout_us == 0)
+                    return BF_PENDING;
+                if (timeout_us < 0)
+                    cv_launched_.wait(lk);
+                else if (cv_launched_.wait_until(lk, deadline) == std::cv_status::timeout &&
+                         req->state == 0)
+                    return fail(BF_ETIMEDOUT, "a ticket was not launched within the timeout");
+            }
+        }
+        if (req->rc)
+            continue;
+        const auto spin_until = clk::now() + std::chrono::microseconds(500);
+        for (;;) {
+            cudaError_t q = cudaEventQuery(req->batch->res->done);
+            if (q == cudaSuccess || q != cudaErrorNotReady)
+                break;
+            if (timeout_us == 0)
+                return BF_PENDING;
+            const auto now = clk::now();
+            if (timeout_us > 0 && now >= deadline)
+                return fail(BF_ETIMEDOUT, "a ticket did not finish within the timeout");
+            if (now < spin_until)
+                std::this_thread::yield();
+            else
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+    }
+    cudaSetDevice(device_);
+    int rc = BF_OK;
+    std::vector<int> staged;
+    for (int k = 0; k < n; ++k) {
+        Request &r = *reqs[k];
+        int rk = r.rc ? fail(r.rc, "%s", r.err.c_str()) : BF_OK;
+        if (!rk) {
+            cudaError_t q = cudaEventQuery(r.batch->res->done);
+            if (q != cudaSuccess)
+                rk = cuda_fail(q, "batch execution");
+        }
+        if (!rk) {
+            const int v = *(volatile int *)r.batch->res->err_host;
+            if (v)
+                rk = fail(v & kErrTimeout ? BF_ETIMEDOUT : BF_ECUDA,
+                          "device-side failure in a batch (status 0x%x)", v);
+        }
+        float *out = outs ? outs[k] : nullptr;
+        if (!rk && out) {
+            Slot &s = *r.slot;
+            cudaError_t e;
+            if (pointer_kind(out) != kPageable) {
+                e = cudaMemcpyAsync(out, s.out.p, r.out_bytes, cudaMemcpyDefault, d2h_);
+            } else if (!s.pin_out.ensure(r.out_bytes)) {
+                e = cudaErrorMemoryAllocation;
+            } else {
+                e = cudaMemcpyAsync(s.pin_out.p, s.out.p, r.out_bytes, cudaMemcpyDeviceToHost, d2h_);
+                staged.push_back(k);
+            }
+            if (e != cudaSuccess)
+                rk = cuda_fail(e, "copying a result");
+        }
+        if (rk && !rc)
+            rc = rk;
+    }
+    cudaError_t e = cudaStreamSynchronize(d2h_);
+    if (e != cudaSuccess && !rc)
+        rc = cuda_fail(e, "copying the results");
+    if (e == cudaSuccess)
+        for (int k : staged)
+            CopyPool::get().copy(outs[k], reqs[k]->slot->pin_out.p, reqs[k]->out_bytes);
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        for (int k = 0; k < n; ++k)
+            h->tickets.erase(tickets[k]);
+    }
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        for (auto &req : reqs) {
+            free_.push_back(std::move(req->slot));
+            live_ -= 1;
+        }
+    }
+    return rc;
+}
+
 int Engine::batch_of(bf_handle *h, uint64_t ticket, int *id, int *frames)
 {
     std::shared_ptr<Request> req;
@@ -718,6 +835,42 @@ BF_API int bf_poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes, 
     if (!h)
         return fail(BF_EINVAL, "null handle");
     return engine_for(h->device)->poll(h, ticket, out, out_bytes, timeout_us);
+}
+
+BF_API int bf_submit_many(bf_handle *h, int32_t n, const int16_t *const *rf, int32_t n_samples,
+                          const double *angles_rad, int32_t n_angles, uint32_t flags,
+                          uint64_t *tickets_out, int32_t *n_submitted)
+{
+    if (!h || !rf || !tickets_out || n < 0)
+        return fail(BF_EINVAL, "null argument");
+    if (n_submitted)
+        *n_submitted = 0;
+    cudaSetDevice(h->device);
+    Engine *eng = engine_for(h->device);
+    int rc = BF_OK, k = 0;
+    for (; k < n; ++k) {
+        if (!rf[k]) {
+            rc = fail(BF_EINVAL, "null record pointer %d", k);
+            break;
+        }
+        rc = eng->submit(h, rf[k], n_samples, angles_rad, n_angles, flags, tickets_out + k, false);
+        if (rc)
+            break;
+    }
+    if (n_submitted)
+        *n_submitted = k;
+    const int rw = eng->wait_copies();  // every submitted source copied before returning
+    return rc ? rc : rw;
+}
+
+BF_API int bf_poll_many(bf_handle *h, int32_t n, const uint64_t *tickets, float *const *outs,
+                        size_t out_bytes, int64_t timeout_us)
+{
+    if (!h || !tickets || n < 0)
+        return fail(BF_EINVAL, "null argument");
+    if (n == 0)
+        return BF_OK;
+    return engine_for(h->device)->poll_many(h, n, tickets, outs, out_bytes, timeout_us);
 }
 
 BF_API int bf_ticket_batch(bf_handle *h, uint64_t ticket, int32_t *batch_id, int32_t *batch_frames)

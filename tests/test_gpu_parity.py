@@ -354,3 +354,30 @@ def test_envelope_into_an_unaligned_output_matches(torch):
                                              f0=acq.f0_hz), bf.BF_PREC_FP32, "dmas env")
     finally:
         bf.bf_destroy(h)
+
+
+def test_submit_many_and_poll_many(torch):
+    """Several frames in one submission and one collection: every result equals
+    the frame beamformed alone, from pinned, pageable and device sources into
+    pinned, pageable and device destinations."""
+    acq = synth.SPECKLE_POINTS_128.with_(nx=48, nz=80)
+    flags = bf.BF_DAS | bf.BF_DMAS | bf.BF_OUT_LOGDB
+    rfs = [synth.speckle_points_frame(acq, seed=synth.BASE_SEED + 300 + k)[0] for k in range(6)]
+    h = make_handle(acq)
+    try:
+        solo = [run_gpu(torch, acq, rf, flags, h=h) for rf in rfs]
+        srcs = [torch.from_numpy(rfs[0]).pin_memory(), rfs[1], torch.from_numpy(rfs[2]).cuda(),
+                torch.from_numpy(rfs[3]).pin_memory(), rfs[4], torch.from_numpy(rfs[5]).cuda()]
+        tickets = bf.bf_submit_many(h, srcs, acq.n_samples, acq.angles_rad, flags)
+        assert len(tickets) == 6 and len(set(tickets)) == 6
+        outs = [torch.zeros((2, acq.nx, acq.nz)).pin_memory(), np.zeros((2, acq.nx, acq.nz), np.float32),
+                torch.zeros((2, acq.nx, acq.nz), device="cuda"), torch.zeros((2, acq.nx, acq.nz)).pin_memory(),
+                np.zeros((2, acq.nx, acq.nz), np.float32), torch.zeros((2, acq.nx, acq.nz), device="cuda")]
+        assert bf.bf_poll_many(h, tickets, outs, timeout_us=30_000_000) == bf.BF_OK
+        for o, ref in zip(outs, solo):
+            got = o if isinstance(o, np.ndarray) else o.cpu().numpy()
+            np.testing.assert_allclose(got, ref, atol=1e-4)
+        with pytest.raises(bf.BFError):  # released
+            bf.bf_poll(h, tickets[0], None, timeout_us=0)
+    finally:
+        bf.bf_destroy(h)
