@@ -525,7 +525,6 @@ __device__ __forceinline__ void accumulate2(uint32_t win0, int w00, float d20, u
         float m0[2], al0[2], m1[2], al1[2];
         delay2(D20, Z[j], Z[j + 1], fp[j], fp[j + 1], m0[0], m0[1], al0[0], al0[1]);
         delay2(D21, Z[j], Z[j + 1], fp[j], fp[j + 1], m1[0], m1[1], al1[0], al1[1]);
-        float v0[2], v1[2], c0[2], c1[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int jj = j + h;
@@ -533,25 +532,18 @@ __device__ __forceinline__ void accumulate2(uint32_t win0, int w00, float d20, u
                 min((unsigned)(__float_as_int(m0[h]) + Kc[jj] - w00), (unsigned)(wmax - 1));
             const unsigned i1 =
                 min((unsigned)(__float_as_int(m1[h]) + Kc[jj] - w01), (unsigned)(wmax - 1));
-            v0[h] = PairIO<PREC>::interp(win0 + i0 * PB, al0[h]);
-            v1[h] = PairIO<PREC>::interp(win1 + i1 * PB, al1[h]);
+            const float v0 = PairIO<PREC>::interp(win0 + i0 * PB, al0[h]);
+            const float v1 = PairIO<PREC>::interp(win1 + i1 * PB, al1[h]);
+            S1[jj] += v0 + v1;
             if (DMAS) {
-                const float a0 = fabsf(v0[h]), a1 = fabsf(v1[h]);
-                c0[h] = copysignf(sqrt_approx(a0), v0[h]);
-                c1[h] = copysignf(sqrt_approx(a1), v1[h]);
+                const float a0 = fabsf(v0), a1 = fabsf(v1);
+                T1[jj] += copysignf(sqrt_approx(a0), v0) + copysignf(sqrt_approx(a1), v1);
                 T2[jj] += a0 + a1;
             }
             if (CF)
-                Su2[jj] = fmaf(v0[h], v0[h], fmaf(v1[h], v1[h], Su2[jj]));
+                Su2[jj] = fmaf(v0, v0, fmaf(v1, v1, Su2[jj]));
             if (PDAS)
-                P1[jj] += pdas_root(v0[h], inv_p, square) + pdas_root(v1[h], inv_p, square);
-        }
-        // rows j and j + 1 of the sums in paired instructions
-        const f32x2_t s1 = add2(pk2(S1[j], S1[j + 1]), add2(pk2(v0[0], v0[1]), pk2(v1[0], v1[1])));
-        upk2(s1, S1[j], S1[j + 1]);
-        if (DMAS) {
-            const f32x2_t t1 = add2(pk2(T1[j], T1[j + 1]), add2(pk2(c0[0], c0[1]), pk2(c1[0], c1[1])));
-            upk2(t1, T1[j], T1[j + 1]);
+                P1[jj] += pdas_root(v0, inv_p, square) + pdas_root(v1, inv_p, square);
         }
     }
 }
