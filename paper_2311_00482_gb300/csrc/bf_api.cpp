@@ -421,11 +421,35 @@ int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *ang
 }
 
 // Host-side launch description of a set of frames (job arrays + prefixes).
+// Two frames can share one beamforming job (and every delay) when they use the
+// same plan with the same combiners: DAS and / or DMAS of RF records.
+static bool pairable(const FramePrep &a, const FramePrep &b)
+{
+    const int m = a.modes & (BF_MODE_MASK | BF_IQ_MASK);
+    return a.plan == b.plan && a.h == b.h && m == (b.modes & (BF_MODE_MASK | BF_IQ_MASK)) &&
+           a.prec == b.prec && a.prec != kPrecIQ && (m & ~(BF_DAS | BF_DMAS)) == 0 &&
+           a.na == b.na && a.ns == b.ns && a.plan->rows == 4 &&
+           beamform_smem_bytes(a.plan->wmax, a.plan->group, a.prec, 2) <= (size_t)kMaxSmemPerCta;
+}
+
 void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
 {
     hl = HostLaunch{};
     std::map<int, std::vector<BfJob>> groups;
-    for (const FramePrep &f : frames) {
+    std::map<int, size_t> group_smem;
+    std::vector<char> taken(frames.size(), 0);
+    for (size_t fi = 0; fi < frames.size(); ++fi) {
+        if (taken[fi])
+            continue;
+        const FramePrep &f = frames[fi];
+        taken[fi] = 1;
+        // a partner frame of the same plan, if any: both ride in one job
+        const FramePrep *f2 = nullptr;
+        for (size_t gi = fi + 1; gi < frames.size() && !f2; ++gi)
+            if (!taken[gi] && pairable(f, frames[gi])) {
+                f2 = &frames[gi];
+                taken[gi] = 1;
+            }
         const bf_handle *h = f.h;
         const Plan *p = f.plan;
         BfJob j{};
@@ -462,15 +486,23 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
         j.iq_c1 = (float)(2.0 * kPi * r);
         j.iq_c2 = (float)(kPi * r);
         j.maxbits = (f.prec == kPrecIQ && f.stage == BF_OUT_LOGDB) ? f.maxbits : nullptr;
-        const int variant = (p->rows * 4 + f.prec) * 16 + (j.modes & (BF_DMAS | BF_CF | BF_PDAS));
+        j.rf_map2 = f2 ? f2->map_dev : nullptr;
+        j.y2 = f2 ? f2->y : nullptr;
+        const int nf = f2 ? 2 : 1;
+        const int variant =
+            ((nf * 16 + p->rows) * 4 + f.prec) * 16 + (j.modes & (BF_DMAS | BF_CF | BF_PDAS));
         groups[variant].push_back(j);
-        hl.smem = std::max(hl.smem, beamform_smem_bytes(p->wmax, p->group, f.prec));
+        const size_t sm = beamform_smem_bytes(p->wmax, p->group, f.prec, nf);
+        group_smem[variant] = std::max(group_smem[variant], sm);
+        hl.smem = std::max(hl.smem, sm);
     }
     for (auto &kv : groups) {
         HostLaunch::Group g;
-        g.rows = kv.first / 64;
+        g.nf = kv.first / (16 * 4 * 16);
+        g.rows = (kv.first / 64) % 16;
         g.prec = (kv.first / 16) % 4;
         g.variant = kv.first % 16;
+        g.smem = group_smem[kv.first];
         g.first = (int)hl.jobs.size();
         g.count = (int)kv.second.size();
         g.prefix_first = (int)hl.tile_prefix.size();
@@ -680,8 +712,8 @@ int enqueue(const std::vector<FramePrep> &frames, const HostLaunch &hl, DeviceLa
         cudaEventRecordWithFlags(marks[1], st, mark_flags);
     for (const HostLaunch::Group &g : hl.groups) {
         e = launch_beamform((const BfJob *)dl.jobs.p + g.first,
-                            (const int *)dl.tile_prefix.p + g.prefix_first, g.count, g.tiles, hl.smem,
-                            g.prec, g.variant, g.rows, (int *)dl.err.p, st);
+                            (const int *)dl.tile_prefix.p + g.prefix_first, g.count, g.tiles, g.smem,
+                            g.prec, g.variant, g.rows, g.nf, (int *)dl.err.p, st);
         if (e != cudaSuccess)
             return cuda_fail(e, "beamform launch");
     }

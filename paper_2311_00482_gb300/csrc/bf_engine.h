@@ -113,7 +113,8 @@ struct FramePrep {
 
 struct HostLaunch {
     struct Group {  // one beamforming launch
-        int prec, variant, rows, first, count, prefix_first, tiles;
+        int prec, variant, rows, nf, first, count, prefix_first, tiles;
+        size_t smem;
     };
     struct IGroup {  // one ingest launch
         int prec, first, count, prefix_first, rows;

@@ -60,6 +60,10 @@ struct BfJob {
     const CUtensorMap *valid_map;  // int2 [na * ne][nxp]: first / last counted row, (-1, -1) if none
     const CUtensorMap *dx2_map;    // float [ne][nxp]: max((kappa * (x_p - x_i))^2, 1e-30)
     float *y;             // [nmodes][nx][nz] beamformed output
+    // a second frame of the same plan sharing every delay (two-frame launches;
+    // null otherwise): its staged pairs and its output
+    const CUtensorMap *rf_map2;
+    float *y2;
     int nx, nz, na, ne;
     int wmax;             // window length (pairs) staged per channel and tile
     int box;              // TMA box width (pairs); wmax is a multiple of it
@@ -167,9 +171,11 @@ cudaError_t launch_demod(const DemodJob *jobs_dev, const int *row_prefix_dev, in
 size_t demod_smem_bytes(int ns);
 // f-k migration launches (bf_kernels.cu), in order on `stream`.
 cudaError_t launch_fkmig(const FkJob &job, cudaStream_t stream);
+// nf: frames per job (2: pairs of frames of one plan share the delays; DAS /
+// DMAS variants of the RF precisions only).
 cudaError_t launch_beamform(const BfJob *jobs_dev, const int *tile_prefix_dev, int njobs,
                             int total_tiles, size_t smem_bytes, int prec, int variant, int rows,
-                            int *err_dev, cudaStream_t stream);
+                            int nf, int *err_dev, cudaStream_t stream);
 cudaError_t launch_envelope(const EnvJob *jobs_dev, const int *blk_prefix_dev, int njobs,
                             int total_blocks, size_t smem_bytes, cudaStream_t stream);
 cudaError_t launch_log(const LogJob *jobs_dev, const int *blk_prefix_dev, int njobs,
@@ -178,7 +184,7 @@ cudaError_t launch_log(const LogJob *jobs_dev, const int *blk_prefix_dev, int nj
 // per pixel); job.y receives the beamformed modes.
 cudaError_t launch_plain(const BfJob &job, const int16_t *rf, const int2 *valid, const float *dx2,
                          int nxp, int ns, cudaStream_t stream);
-size_t beamform_smem_bytes(int wmax, int group, int prec);
+size_t beamform_smem_bytes(int wmax, int group, int prec, int nf = 1);
 int log_blocks(long long pixels);
 int envelope_cols_per_block(int fft_m);
 size_t envelope_smem_bytes(int fft_m, int bluestein);

@@ -399,9 +399,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 }
 
 // Bytes of one pipeline stage: tables (int2 rows + float dx^2) and windows.
-__host__ __device__ __forceinline__ int stage_bytes(int group, int wmax, int pb)
+// (nf frames' windows per channel in two-frame launches)
+__host__ __device__ __forceinline__ int stage_bytes(int group, int wmax, int pb, int nf = 1)
 {
-    return group * (kTileCols * 12 + wmax * pb);
+    return group * (kTileCols * 12 + nf * wmax * pb);
 }
 
 // ---- packed FP32 pairs (Blackwell f32x2 arithmetic): two rows' delays at once
@@ -508,6 +509,46 @@ __device__ __forceinline__ void accumulate(uint32_t win, int wmax, int w0, float
     }
 }
 
+// One channel into the ROWS pixels of this thread for two frames of one plan:
+// the delay of each pixel is formed once and read from both frames' windows
+// (the second frame's window follows the first at wmax pairs).
+template <int PREC, bool DMAS, int ROWS, bool CHECK>
+__device__ __forceinline__ void accumulate_f2(uint32_t win, int wmax, int w0, float d2, int2 vr,
+                                              int r_first, const float *Z, const float *fp,
+                                              const int *Kc, float *S1, float *T1, float *T2,
+                                              float *S1b, float *T1b, float *T2b)
+{
+    constexpr int PB = PairIO<PREC>::kBytes;
+    const uint32_t second = (uint32_t)(wmax * PB);
+    const unsigned span = (unsigned)(vr.y - vr.x);
+    const f32x2_t D2 = pk2(d2, d2);
+#pragma unroll
+    for (int j = 0; j < ROWS; j += 2) {
+        float m[2], al[2];
+        delay2(D2, Z[j], Z[j + 1], fp[j], fp[j + 1], m[0], m[1], al[0], al[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int jj = j + h;
+            const unsigned idx =
+                min((unsigned)(__float_as_int(m[h]) + Kc[jj] - w0), (unsigned)(wmax - 1));
+            const uint32_t a = win + idx * PB;
+            const float v0 = PairIO<PREC>::interp(a, al[h]);
+            const float v1 = PairIO<PREC>::interp(a + second, al[h]);
+            if (!CHECK || (unsigned)(r_first + jj - vr.x) <= span) {
+                S1[jj] += v0;
+                S1b[jj] += v1;
+                if (DMAS) {
+                    const float a0 = fabsf(v0), a1 = fabsf(v1);
+                    T1[jj] += copysignf(sqrt_approx(a0), v0);
+                    T1b[jj] += copysignf(sqrt_approx(a1), v1);
+                    T2[jj] += a0;
+                    T2b[jj] += a1;
+                }
+            }
+        }
+    }
+}
+
 // Two channels that every pixel of the band counts, interleaved: twice the
 // independent dependency chains per thread (square roots, reciprocal, shared
 // load) for the scheduler to overlap.
@@ -604,14 +645,16 @@ __device__ __forceinline__ void accumulate_iq(uint32_t win, int wmax, int w0, fl
 // Resident CTAs per SM the register budget is sized for: three 32-row tiles,
 // one 64-row tile (measured: capping 64-row tiles at two CTAs per SM costs
 // more in spills and lost overlap than the extra warps win).
-template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS>
+// Two-frame launches (NF = 2) hold twice the accumulators and twice the
+// windows per stage: two CTAs per SM.
+template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS, int NF>
 constexpr int beamform_min_blocks()
 {
-    return ROWS != 8 ? 3 : 1;
+    return ROWS != 8 ? (NF == 2 ? 2 : 3) : 1;
 }
 
-template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS>
-__global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS, CF, PDAS, ROWS>()))
+template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS, int NF>
+__global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS, CF, PDAS, ROWS, NF>()))
     beamform_kernel(const BfJob *__restrict__ jobs, const int *__restrict__ tile_prefix, int njobs,
                     int total_tiles, int stage_stride, int *__restrict__ err)
 {
@@ -654,6 +697,7 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
             const int *__restrict__ wtab = J->wtab;
             const int *__restrict__ btab = J->btab;
             const CUtensorMap *rf_map = J->rf_map;
+            const CUtensorMap *rf_map2 = J->rf_map2;
             const CUtensorMap *valid_map = J->valid_map;
             const CUtensorMap *dx2_map = J->dx2_map;
             const int box = J->box;
@@ -741,7 +785,7 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
                     }
                 }
                 const int w0 = wf.x;
-                const unsigned bytes = (mine && w0 != kNoWindow) ? (unsigned)(wmax * PB) : 0u;
+                const unsigned bytes = (mine && w0 != kNoWindow) ? (unsigned)(NF * wmax * PB) : 0u;
                 unsigned total = bytes;
 #pragma unroll
                 for (int off = 16; off; off >>= 1)
@@ -757,10 +801,15 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
                 }
                 __syncwarp();
                 if (bytes) {
-                    unsigned char *dst = base + (size_t)G * kTileCols * 12 + (size_t)lane * wmax * PB;
+                    unsigned char *dst =
+                        base + (size_t)G * kTileCols * 12 + (size_t)lane * NF * wmax * PB;
                     const int row = a * ne + i0 + lane;
                     for (int off = 0; off < wmax; off += box)
                         tma_2d(dst + (size_t)off * PB, rf_map, (w0 + off) * XS, row, &sh.full[st]);
+                    if (NF == 2)  // the second frame's window right after the first
+                        for (int off = 0; off < wmax; off += box)
+                            tma_2d(dst + (size_t)(wmax + off) * PB, rf_map2, (w0 + off) * XS, row,
+                                   &sh.full[st]);
                 }
                 wf = wf_next;
                 tb = tb_next;
@@ -789,9 +838,11 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
         int Kc[ROWS];
         float Z[ROWS], fp[ROWS];
         float S1[ROWS], T1[ROWS], T2[ROWS], Yd[ROWS], Su2[ROWS], P1[ROWS], Yp[ROWS];
+        float S1b[ROWS], T1b[ROWS], T2b[ROWS], Ydb[ROWS];  // second frame (NF = 2)
 #pragma unroll
         for (int j = 0; j < ROWS; ++j) {
             S1[j] = T1[j] = T2[j] = Yd[j] = Su2[j] = P1[j] = Yp[j] = 0.f;
+            S1b[j] = T1b[j] = T2b[j] = Ydb[j] = 0.f;
             Kc[j] = 0;
             fp[j] = Z[j] = 0.f;
         }
@@ -831,6 +882,7 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
                     fp[j] = cf + sh.tF[st][kTileCols + rr] - 0.5f;
                     Z[j] = sh.tZ[st][rr];
                     T1[j] = T2[j] = P1[j] = Ti[j] = 0.f;
+                    T1b[j] = T2b[j] = 0.f;
                 }
             }
             const uint32_t base = smem_u32(stage_base(st));
@@ -840,7 +892,7 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
             const uint32_t wfb = smem_u32(&sh.wf[st][0]);
             const int nf = sh.nfull[st][warp], nt = sh.ntot[st][warp];
             const uint8_t *L = sh.list[st][warp];
-            auto win_of = [&](int c) { return wins + (uint32_t)(c * wmax * PB); };
+            auto win_of = [&](int c) { return wins + (uint32_t)(c * NF * wmax * PB); };
             auto w0_of = [&](int c) { return lds_int2(wfb + (uint32_t)c * 8).x; };
             auto d2_of = [&](int c) { return lds_f32(d2b + (uint32_t)c * (kTileCols * 4)); };
             auto vr_of = [&](int c) { return lds_int2(vrb + (uint32_t)c * (kTileCols * 8)); };
@@ -858,6 +910,22 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
                     const int c = L[k];
                     accumulate_iq<DMAS, ROWS, true>(win_of(c), wmax, w0_of(c), d2_of(c), vr_of(c),
                                                     r_first, Z, fp, Kc, c1, c2, S1, Y1i, T1, Ti);
+                }
+            } else if constexpr (NF == 2) {
+                // every channel once, each delay serving both frames
+#pragma unroll 1
+                for (; k < nf; ++k) {
+                    const int c = L[k];
+                    accumulate_f2<PREC, DMAS, ROWS, false>(win_of(c), wmax, w0_of(c), d2_of(c),
+                                                           make_int2(0, 0), r_first, Z, fp, Kc, S1,
+                                                           T1, T2, S1b, T1b, T2b);
+                }
+#pragma unroll 1
+                for (; k < nt; ++k) {
+                    const int c = L[k];
+                    accumulate_f2<PREC, DMAS, ROWS, true>(win_of(c), wmax, w0_of(c), d2_of(c),
+                                                          vr_of(c), r_first, Z, fp, Kc, S1, T1, T2,
+                                                          S1b, T1b, T2b);
                 }
             } else {
                 // channels every pixel of the band counts, two at a time (twice the
@@ -892,8 +960,11 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
                 mbar_arrive(&sh.empty[st]);
             if (DMAS && !IQ && g == ngroups - 1) {
 #pragma unroll
-                for (int j = 0; j < ROWS; ++j)
+                for (int j = 0; j < ROWS; ++j) {
                     Yd[j] = fmaf(0.5f * T1[j], T1[j], fmaf(-0.5f, T2[j], Yd[j]));
+                    if (NF == 2)
+                        Ydb[j] = fmaf(0.5f * T1b[j], T1b[j], fmaf(-0.5f, T2b[j], Ydb[j]));
+                }
             }
             if (DMAS && IQ && g == ngroups - 1) {  // Eq. (4): ((1/M) sum s^)^2 per angle
 #pragma unroll
@@ -974,6 +1045,14 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
             }
             if (modes & BF_PDAS)
                 y[(size_t)(slot++) * plane + o] = Yp[j] * scale;
+            if (NF == 2) {  // the second frame (DAS / DMAS only)
+                float *__restrict__ y2 = J->y2;
+                int slot2 = 0;
+                if (modes & BF_DAS)
+                    y2[(size_t)(slot2++) * plane + o] = S1b[j] * scale;
+                if (modes & BF_DMAS)
+                    y2[(size_t)(slot2++) * plane + o] = Ydb[j] * scale;
+            }
         }
     }
 }
@@ -1431,11 +1510,11 @@ __global__ void __launch_bounds__(256) log_kernel(const LogJob *__restrict__ job
     }
 }
 
-template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS>
+template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS, int NF = 1>
 cudaError_t launch_bf_t(const BfJob *jobs, const int *prefix, int njobs, int tiles, size_t smem,
                         int *err, cudaStream_t st)
 {
-    auto k = beamform_kernel<PREC, DMAS, CF, PDAS, ROWS>;
+    auto k = beamform_kernel<PREC, DMAS, CF, PDAS, ROWS, NF>;
     static size_t configured = 0;
     static size_t occ_smem = 0;
     static int occ = 0, sms = 0;
@@ -1496,9 +1575,9 @@ cudaError_t launch_bf_p(const BfJob *jobs, const int *prefix, int njobs, int til
 
 }  // namespace
 
-size_t beamform_smem_bytes(int wmax, int group, int prec)
+size_t beamform_smem_bytes(int wmax, int group, int prec, int nf)
 {
-    return (size_t)kHeaderBytes + (size_t)kStages * stage_bytes(group, wmax, pair_bytes(prec));
+    return (size_t)kHeaderBytes + (size_t)kStages * stage_bytes(group, wmax, pair_bytes(prec), nf);
 }
 
 // Image columns per envelope CTA for a power-of-two transform: two per
@@ -1555,12 +1634,26 @@ cudaError_t launch_demod(const DemodJob *jobs_dev, const int *row_prefix_dev, in
 
 cudaError_t launch_beamform(const BfJob *jobs_dev, const int *tile_prefix_dev, int njobs,
                             int total_tiles, size_t smem_bytes, int prec, int variant, int rows,
-                            int *err_dev, cudaStream_t stream)
+                            int nf, int *err_dev, cudaStream_t stream)
 {
     if (njobs <= 0 || total_tiles <= 0)
         return cudaSuccess;
     const int dmas = (variant & BF_DMAS) ? 1 : 0, cf = (variant & BF_CF) ? 1 : 0;
     const int pdas = (variant & BF_PDAS) ? 1 : 0;
+    if (nf == 2) {  // pairs of frames sharing the delays: DAS / DMAS, 32-row tiles
+        if (cf || pdas || rows != 4 || prec == kPrecIQ)
+            return cudaErrorInvalidValue;
+        const BfJob *j = jobs_dev;
+        const int *pf = tile_prefix_dev;
+        if (prec == kPrecF32)
+            return dmas ? launch_bf_t<kPrecF32, true, false, false, 4, 2>(j, pf, njobs, total_tiles, smem_bytes, err_dev, stream)
+                        : launch_bf_t<kPrecF32, false, false, false, 4, 2>(j, pf, njobs, total_tiles, smem_bytes, err_dev, stream);
+        if (prec == kPrecF16)
+            return dmas ? launch_bf_t<kPrecF16, true, false, false, 4, 2>(j, pf, njobs, total_tiles, smem_bytes, err_dev, stream)
+                        : launch_bf_t<kPrecF16, false, false, false, 4, 2>(j, pf, njobs, total_tiles, smem_bytes, err_dev, stream);
+        return dmas ? launch_bf_t<kPrecBF16, true, false, false, 4, 2>(j, pf, njobs, total_tiles, smem_bytes, err_dev, stream)
+                    : launch_bf_t<kPrecBF16, false, false, false, 4, 2>(j, pf, njobs, total_tiles, smem_bytes, err_dev, stream);
+    }
     if (prec == kPrecIQ) {  // IQ-DAS always, BB-DMAS in the DMAS slot
         if (rows == 4)
             return dmas ? launch_bf_t<kPrecIQ, true, false, false, 4>(jobs_dev, tile_prefix_dev, njobs,

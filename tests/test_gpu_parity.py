@@ -381,3 +381,32 @@ def test_submit_many_and_poll_many(torch):
             bf.bf_poll(h, tickets[0], None, timeout_us=0)
     finally:
         bf.bf_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [bf.BF_PREC_FP32, bf.BF_PREC_FP16])
+def test_frames_of_one_plan_share_delays_in_pairs(torch, prec):
+    """Five frames of one handle and plan in a batch: two pairs share their delays
+    (two-frame jobs), the fifth runs alone; every frame matches the oracle and
+    its single-frame result."""
+    acq = synth.SPECKLE_POINTS_128.with_(nx=70, nz=90, angles_deg=(-4.0, 4.0))
+    flags = bf.BF_DAS | bf.BF_DMAS | prec
+    rfs = [synth.speckle_points_frame(acq, seed=synth.BASE_SEED + 500 + k)[0] for k in range(5)]
+    h = make_handle(acq)
+    try:
+        rf_d = [torch.from_numpy(r).cuda() for r in rfs]
+        outs = [torch.full((2, acq.nx, acq.nz), float("nan"), device="cuda") for _ in rfs]
+        batch = bf.Batch([(h, rf_d[k], acq.n_samples, acq.angles_rad, flags, outs[k])
+                          for k in range(5)])
+        batch.launch()
+        batch.status()
+        for k in range(5):
+            got = outs[k].cpu().numpy().astype(np.float64)
+            ref = oracle_all(acq, rfs[k])
+            assert_close(got[0], ref["das"], prec, "das %d" % k)
+            assert_close(got[1], ref["dmas"], prec, "dmas %d" % k)
+            single = run_gpu(torch, acq, rfs[k], flags, h=h)
+            np.testing.assert_allclose(got, single, rtol=0,
+                                       atol=2e-6 * np.max(np.abs(single)) + 1e-30)
+        batch.close()
+    finally:
+        bf.bf_destroy(h)
