@@ -241,12 +241,12 @@ def test_submit_poll_results_equal_solo_and_batches_overlap(torch):
         # all 16 queued while held: launched together (batches of up to 64)
         tickets, outs, info, _ = burst(64, 1)
         assert max(n for _, n in info) > 1, info
-        for out, ref in zip(outs, solo):
-            np.testing.assert_allclose(out, ref, atol=1e-4)
+        for out, ref in zip(outs, solo):  # (2e-3 dB: frames of one plan may share a job)
+            np.testing.assert_allclose(out, ref, atol=2e-3)
         # batches of 4, three in flight on different streams: some run at the same time
         _, outs, info, times = burst(4, 3)
         for out, ref in zip(outs, solo):
-            np.testing.assert_allclose(out, ref, atol=1e-4)
+            np.testing.assert_allclose(out, ref, atol=2e-3)
         spans = sorted({(bid, t) for (bid, _), t in zip(info, times)})
         overlap = any(spans[i][1][0] < spans[j][1][1] and spans[j][1][0] < spans[i][1][1]
                       for i in range(len(spans)) for j in range(i + 1, len(spans)))
