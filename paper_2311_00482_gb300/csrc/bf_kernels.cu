@@ -549,47 +549,6 @@ __device__ __forceinline__ void accumulate_f2(uint32_t win, int wmax, int w0, fl
     }
 }
 
-// Two fully counted channels for two frames of one plan: four independent
-// chains per row (two delays, each read from both frames' windows).
-template <int PREC, bool DMAS, int ROWS>
-__device__ __forceinline__ void accumulate2_f2(uint32_t win0, int w00, float d20, uint32_t win1,
-                                               int w01, float d21, int wmax, const float *Z,
-                                               const float *fp, const int *Kc, float *S1, float *T1,
-                                               float *T2, float *S1b, float *T1b, float *T2b)
-{
-    constexpr int PB = PairIO<PREC>::kBytes;
-    const uint32_t second = (uint32_t)(wmax * PB);
-    const f32x2_t D20 = pk2(d20, d20), D21 = pk2(d21, d21);
-#pragma unroll
-    for (int j = 0; j < ROWS; j += 2) {
-        float m0[2], al0[2], m1[2], al1[2];
-        delay2(D20, Z[j], Z[j + 1], fp[j], fp[j + 1], m0[0], m0[1], al0[0], al0[1]);
-        delay2(D21, Z[j], Z[j + 1], fp[j], fp[j + 1], m1[0], m1[1], al1[0], al1[1]);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int jj = j + h;
-            const unsigned i0 =
-                min((unsigned)(__float_as_int(m0[h]) + Kc[jj] - w00), (unsigned)(wmax - 1));
-            const unsigned i1 =
-                min((unsigned)(__float_as_int(m1[h]) + Kc[jj] - w01), (unsigned)(wmax - 1));
-            const uint32_t a0 = win0 + i0 * PB, a1 = win1 + i1 * PB;
-            const float u0 = PairIO<PREC>::interp(a0, al0[h]);           // channel 0, frame a
-            const float u1 = PairIO<PREC>::interp(a1, al1[h]);           // channel 1, frame a
-            const float w0 = PairIO<PREC>::interp(a0 + second, al0[h]);  // channel 0, frame b
-            const float w1 = PairIO<PREC>::interp(a1 + second, al1[h]);  // channel 1, frame b
-            S1[jj] += u0 + u1;
-            S1b[jj] += w0 + w1;
-            if (DMAS) {
-                const float au0 = fabsf(u0), au1 = fabsf(u1), aw0 = fabsf(w0), aw1 = fabsf(w1);
-                T1[jj] += copysignf(sqrt_approx(au0), u0) + copysignf(sqrt_approx(au1), u1);
-                T1b[jj] += copysignf(sqrt_approx(aw0), w0) + copysignf(sqrt_approx(aw1), w1);
-                T2[jj] += au0 + au1;
-                T2b[jj] += aw0 + aw1;
-            }
-        }
-    }
-}
-
 // Two channels that every pixel of the band counts, interleaved: twice the
 // independent dependency chains per thread (square roots, reciprocal, shared
 // load) for the scheduler to overlap.
@@ -953,14 +912,7 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
                                                     r_first, Z, fp, Kc, c1, c2, S1, Y1i, T1, Ti);
                 }
             } else if constexpr (NF == 2) {
-                // each delay serves both frames; fully counted channels two at a time
-#pragma unroll 1
-                for (; k + 1 < nf; k += 2) {
-                    const int c0 = L[k], c1 = L[k + 1];
-                    accumulate2_f2<PREC, DMAS, ROWS>(win_of(c0), w0_of(c0), d2_of(c0), win_of(c1),
-                                                     w0_of(c1), d2_of(c1), wmax, Z, fp, Kc, S1, T1,
-                                                     T2, S1b, T1b, T2b);
-                }
+                // every channel once, each delay serving both frames
 #pragma unroll 1
                 for (; k < nf; ++k) {
                     const int c = L[k];
