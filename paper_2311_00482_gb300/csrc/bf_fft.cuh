@@ -139,13 +139,21 @@ static __device__ float2 *fft_r8(float2 *x, float2 *y, int m, int lgm, int cols,
                 for (int p = 1; p < 8; ++p)
                     v[p] = xc[j + p * q];
             } else {
-#pragma unroll
-                for (int p = 1; p < 8; ++p) {
-                    float2 w = tw[p * k1];
-                    if (inverse)
-                        w.y = -w.y;
-                    v[p] = cmul(xc[j + p * q], w);
+                // w^1, w^2, w^4 from the table, the other powers by products: three
+                // table reads per butterfly instead of seven (the strided reads of
+                // w^3 .. w^7 collide in the shared-memory banks)
+                float2 w1 = tw[k1], w2 = tw[2 * k1], w4 = tw[4 * k1];
+                if (inverse) {
+                    w1.y = -w1.y;
+                    w2.y = -w2.y;
+                    w4.y = -w4.y;
                 }
+                const float2 w3 = cmul(w1, w2);
+                const float2 w[8] = {make_float2(1.f, 0.f), w1, w2, w3, w4, cmul(w1, w4),
+                                     cmul(w2, w4), cmul(w3, w4)};
+#pragma unroll
+                for (int p = 1; p < 8; ++p)
+                    v[p] = cmul(xc[j + p * q], w[p]);
             }
             dft8(v, inverse);
             const int o = ((j - r) << 3) + r;
