@@ -275,8 +275,6 @@ public:
             cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
         cudaStreamCreateWithFlags(&copy_, cudaStreamNonBlocking);
         cudaStreamCreateWithFlags(&d2h_, cudaStreamNonBlocking);
-        for (auto &s : d2h_many_)
-            cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
         size_t fr = 0, tot = 0;
         cudaMemGetInfo(&fr, &tot);
         budget_ = tot / 2;
@@ -341,9 +339,6 @@ private:
     int next_batch_ = 0;
     cudaStream_t streams_[kStreams]{};
     cudaStream_t copy_ = nullptr, d2h_ = nullptr;
-    // bf_poll_many spreads its copies over several streams (several copy engines)
-    static constexpr int kCopyStreams = 4;
-    cudaStream_t d2h_many_[kCopyStreams]{};
     std::thread worker_;
     ResPool res_pool_;
 };
@@ -718,13 +713,12 @@ int Engine::poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const
         if (!rk && out) {
             Slot &s = *r.slot;
             cudaError_t e;
-            cudaStream_t cs = d2h_many_[k % kCopyStreams];
             if (pointer_kind(out) != kPageable) {
-                e = cudaMemcpyAsync(out, s.out.p, r.out_bytes, cudaMemcpyDefault, cs);
+                e = cudaMemcpyAsync(out, s.out.p, r.out_bytes, cudaMemcpyDefault, d2h_);
             } else if (!s.pin_out.ensure(r.out_bytes)) {
                 e = cudaErrorMemoryAllocation;
             } else {
-                e = cudaMemcpyAsync(s.pin_out.p, s.out.p, r.out_bytes, cudaMemcpyDeviceToHost, cs);
+                e = cudaMemcpyAsync(s.pin_out.p, s.out.p, r.out_bytes, cudaMemcpyDeviceToHost, d2h_);
                 staged.push_back(k);
             }
             if (e != cudaSuccess)
@@ -733,12 +727,7 @@ int Engine::poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const
         if (rk && !rc)
             rc = rk;
     }
-    cudaError_t e = cudaSuccess;
-    for (cudaStream_t cs : d2h_many_) {
-        const cudaError_t ec = cudaStreamSynchronize(cs);
-        if (e == cudaSuccess)
-            e = ec;
-    }
+    cudaError_t e = cudaStreamSynchronize(d2h_);
     if (e != cudaSuccess && !rc)
         rc = cuda_fail(e, "copying the results");
     if (e == cudaSuccess)
