@@ -159,6 +159,15 @@ struct LogJob {
     int vec4;             // 1: env and out 16-byte aligned and n a multiple of 4
 };
 
+// Launch configuration of kernel `k` on the current device, cached per
+// (device, kernel) behind a mutex so that host threads and devices do not race:
+// raises its dynamic shared-memory limit to at least `smem` when that is above
+// the 48 KB default (with the largest shared-memory carveout when
+// `max_carveout`), and returns the device's SM count in *sms and, when occ is
+// not null, the resident CTAs per SM at `threads` threads and `smem` bytes.
+cudaError_t kernel_setup(const void *k, size_t smem, int threads, bool max_carveout, int *sms,
+                         int *occ);
+
 // Kernel launchers (bf_kernels.cu).  All enqueue on `stream` and return the
 // launch status.  `variant` holds the BF_DMAS / BF_CF bits the launch computes
 // (all its jobs must share them, the precision and the rows per thread);

@@ -26,6 +26,9 @@
 #include <limits.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "../../include/bf.h"
 #include "bf_fft.cuh"
@@ -1519,33 +1522,11 @@ cudaError_t launch_bf_t(const BfJob *jobs, const int *prefix, int njobs, int til
                         int *err, cudaStream_t st)
 {
     auto k = beamform_kernel<PREC, DMAS, CF, PDAS, ROWS, NF>;
-    static size_t configured = 0;
-    static size_t occ_smem = 0;
-    static int occ = 0, sms = 0;
-    cudaError_t e = cudaSuccess;
-    if (smem > configured) {
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)  // several CTAs per SM need the largest shared-memory carveout
-            e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     (int)cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess)
-            return e;
-        configured = smem;
-    }
-    if (sms == 0) {
-        int dev = 0;
-        e = cudaGetDevice(&dev);
-        if (e == cudaSuccess)
-            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess)
-            return e;
-    }
-    if (smem != occ_smem) {  // resident CTAs per SM at this shared-memory size
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kThreads + 32, smem);
-        if (e != cudaSuccess)
-            return e;
-        occ_smem = smem;
-    }
+    // several CTAs per SM need the largest shared-memory carveout
+    int sms = 0, occ = 0;
+    cudaError_t e = kernel_setup((const void *)k, smem, kThreads + 32, true, &sms, &occ);
+    if (e != cudaSuccess)
+        return e;
     // persistent grid: every CTA resident at once, each walking the tiles
     const int grid = std::max(1, std::min(tiles, std::max(occ, 1) * sms));
     const int stride = (int)((smem - kHeaderBytes) / kStages);
@@ -1624,14 +1605,10 @@ cudaError_t launch_demod(const DemodJob *jobs_dev, const int *row_prefix_dev, in
     if (njobs <= 0 || total_rows <= 0)
         return cudaSuccess;
     const size_t smem = demod_smem_bytes(max_ns);
-    static size_t configured = 0;
-    if (smem > 48u * 1024u && smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(demod_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        configured = smem;
-    }
+    int sms = 0;
+    cudaError_t e = kernel_setup((const void *)demod_kernel, smem, 256, false, &sms, nullptr);
+    if (e != cudaSuccess)
+        return e;
     demod_kernel<<<total_rows, 256, smem, stream>>>(jobs_dev, row_prefix_dev, njobs);
     return cudaGetLastError();
 }
@@ -1701,14 +1678,10 @@ cudaError_t launch_envelope(const EnvJob *jobs_dev, const int *blk_prefix_dev, i
 {
     if (njobs <= 0 || total_blocks <= 0)
         return cudaSuccess;
-    static size_t configured = 0;
-    if (smem > 48u * 1024u && smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(envelope_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        configured = smem;
-    }
+    int sms = 0;
+    cudaError_t e = kernel_setup((const void *)envelope_kernel, smem, 256, false, &sms, nullptr);
+    if (e != cudaSuccess)
+        return e;
     envelope_kernel<<<total_blocks, 256, smem, stream>>>(jobs_dev, blk_prefix_dev, njobs);
     return cudaGetLastError();
 }
@@ -1724,27 +1697,70 @@ cudaError_t launch_log(const LogJob *jobs_dev, const int *blk_prefix_dev, int nj
 
 int log_blocks(long long pixels) { return (int)((pixels + kLogPerBlock - 1) / kLogPerBlock); }
 
-static cudaError_t smem_attr(const void *k, size_t smem, size_t &configured)
+cudaError_t kernel_setup(const void *k, size_t smem, int threads, bool max_carveout, int *sms,
+                         int *occ)
 {
-    if (smem <= 48u * 1024u || smem <= configured)
-        return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        configured = smem;
-    return e;
+    struct State {
+        size_t configured = 48u * 1024u;  // dynamic shared memory allowed without an attribute
+        bool carveout = false;
+        std::map<std::pair<size_t, int>, int> occ;  // (smem, threads) -> resident CTAs per SM
+    };
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, State> state;
+    static std::map<int, int> sm_count;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    std::lock_guard<std::mutex> lock(mu);
+    auto sm = sm_count.find(dev);
+    if (sm == sm_count.end()) {
+        int n = 0;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess)
+            return e;
+        sm = sm_count.emplace(dev, n).first;
+    }
+    *sms = sm->second;
+    State &s = state[{dev, k}];
+    if (max_carveout && !s.carveout) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess)
+            return e;
+        s.carveout = true;
+    }
+    if (smem > s.configured) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        s.configured = smem;
+    }
+    if (occ) {
+        auto it = s.occ.find({smem, threads});
+        if (it == s.occ.end()) {
+            int n = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem);
+            if (e != cudaSuccess)
+                return e;
+            it = s.occ.emplace(std::make_pair(smem, threads), n).first;
+        }
+        *occ = it->second;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_fkmig(const FkJob &J, cudaStream_t st)
 {
-    static size_t c_time = 0, c_rows = 0, c_depth = 0;
+    int sms = 0;
     const size_t s_nt = (size_t)3 * J.nt * sizeof(float2);
-    cudaError_t e = smem_attr((const void *)fk_time_kernel, s_nt, c_time);
+    cudaError_t e = kernel_setup((const void *)fk_time_kernel, s_nt, 256, false, &sms, nullptr);
     if (e == cudaSuccess)
-        e = smem_attr((const void *)fk_depth_kernel, s_nt, c_depth);
+        e = kernel_setup((const void *)fk_depth_kernel, s_nt, 256, false, &sms, nullptr);
     const int per = J.nk >= 2048 ? 1 : 2048 / J.nk;
     const size_t s_rows = ((size_t)2 * per * J.nk + J.nk) * sizeof(float2);
     if (e == cudaSuccess)
-        e = smem_attr((const void *)fk_rows_kernel, s_rows, c_rows);
+        e = kernel_setup((const void *)fk_rows_kernel, s_rows, 256, false, &sms, nullptr);
     if (e != cudaSuccess)
         return e;
     const int nf = J.nt / 2 + 1, half = J.nt / 2;

@@ -177,16 +177,10 @@ extern "C" BF_API int bf_logdb_static(const float *y_dev, int32_t nx, int32_t nz
         return cuda_fail(e, "cudaMemsetAsync (static scratch)");
     const int C = nz >= 2048 ? 1 : 2048 / nz;
     const size_t smem = (3u * (size_t)C * nz + (size_t)nz) * sizeof(float2);
-    static bool configured[kMaxDevices] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (!configured[dev]) {
-        e = cudaFuncSetAttribute(static_envelope_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((3u * 2048u + 4096u) * sizeof(float2)));
-        if (e != cudaSuccess)
-            return cuda_fail(e, "cudaFuncSetAttribute");
-        configured[dev] = true;
-    }
+    int sms = 0;
+    e = kernel_setup((const void *)static_envelope_kernel, smem, 256, false, &sms, nullptr);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaFuncSetAttribute");
     const int blocks = (nx + 2 * C - 1) / (2 * C);
     static_envelope_kernel<<<blocks, 256, smem, st>>>(y_dev, nx, nz, bandpass ? 1 : 0, kb_lo, kb_hi,
                                                       env, maxbits);
