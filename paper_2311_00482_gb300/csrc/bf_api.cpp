@@ -174,7 +174,8 @@ static int env_tables(int nz, std::shared_ptr<EnvTablesDev> &out)
 
 // Tile configuration of a workload: what bf_autotune measured fastest for it,
 // else entry 0 (4 rows per thread, 32-row tiles, three CTAs per SM, measured
-// faster than 8 rows on every grid tried); BF_TILE_ROWS=8 forces entry 3.
+// faster than 8 rows on every grid tried); BF_TILE_ROWS=8 forces entry 3,
+// BF_TILE_ROWS=2 entry 4 (DAS / DMAS of RF records; others keep entry 0).
 static int choose_cfg(const bf_handle *h, const PlanKey &key)
 {
     if (const char *e = std::getenv("BF_TILE_ROWS")) {
@@ -182,16 +183,26 @@ static int choose_cfg(const bf_handle *h, const PlanKey &key)
             return 3;
         if (std::atoi(e) == 4)
             return 0;
+        if (std::atoi(e) == 2)
+            return 4;
     }
     auto it = h->tuned.find(key);
     return it == h->tuned.end() ? 0 : it->second;
 }
 
-int handle_plan(bf_handle *h, int ns, const double *angles, int na, int prec, Plan **out, int cfg)
+int handle_plan(bf_handle *h, int ns, const double *angles, int na, uint32_t flags, Plan **out,
+                int cfg)
 {
+    const int prec = frame_prec(flags);
+    const bool narrow_ok = prec != kPrecIQ && (flags & BF_MODE_MASK & ~(BF_DAS | BF_DMAS)) == 0;
     PlanKey key{ns, prec, std::vector<double>(angles, angles + na), 0};
     std::lock_guard<std::mutex> lk(h->mu);
     key.cfg = (cfg >= 0 && cfg < kNumTileConfigs) ? cfg : choose_cfg(h, key);
+    if (kTileConfigs[key.cfg].rows == 2 && !narrow_ok) {
+        if (cfg >= 0)
+            return fail(BF_EINVAL, "two-row tiles serve DAS / DMAS of RF records only");
+        key.cfg = 0;
+    }
     auto it = h->plans.find(key);
     if (it != h->plans.end()) {
         *out = it->second.get();
@@ -353,7 +364,7 @@ int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *ang
     const int prec = frame_prec(flags);
     const bool iq = prec == kPrecIQ;
     Plan *plan = nullptr;
-    rc = handle_plan(h, ns, angles, na, prec, &plan, cfg);
+    rc = handle_plan(h, ns, angles, na, flags, &plan, cfg);
     if (rc)
         return rc;
     const int modes = flags & (BF_MODE_MASK | BF_IQ_MASK), nm = frame_images(flags);
@@ -421,15 +432,25 @@ int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *ang
 }
 
 // Host-side launch description of a set of frames (job arrays + prefixes).
-// Two frames can share one beamforming job (and every delay) when they use the
-// same plan with the same combiners: DAS and / or DMAS of RF records.
-static bool pairable(const FramePrep &a, const FramePrep &b)
+// Frames can share one beamforming job (and every delay) when they use the
+// same plan with the same combiners: DAS and / or DMAS of RF records, up to
+// two frames on 32-row tiles and four on 16-row tiles.
+static int max_frames_per_job(const FramePrep &a)
+{
+    const int m = a.modes & (BF_MODE_MASK | BF_IQ_MASK);
+    if (a.prec == kPrecIQ || (m & ~(BF_DAS | BF_DMAS)) != 0)
+        return 1;
+    for (int nf = a.plan->rows == 2 ? 4 : a.plan->rows == 4 ? 2 : 1; nf > 1; nf /= 2)
+        if (beamform_smem_bytes(a.plan->wmax, a.plan->group, a.prec, nf) <= (size_t)kMaxSmemPerCta)
+            return nf;
+    return 1;
+}
+
+static bool shareable(const FramePrep &a, const FramePrep &b)
 {
     const int m = a.modes & (BF_MODE_MASK | BF_IQ_MASK);
     return a.plan == b.plan && a.h == b.h && m == (b.modes & (BF_MODE_MASK | BF_IQ_MASK)) &&
-           a.prec == b.prec && a.prec != kPrecIQ && (m & ~(BF_DAS | BF_DMAS)) == 0 &&
-           a.na == b.na && a.ns == b.ns && a.plan->rows == 4 &&
-           beamform_smem_bytes(a.plan->wmax, a.plan->group, a.prec, 2) <= (size_t)kMaxSmemPerCta;
+           a.prec == b.prec && a.na == b.na && a.ns == b.ns;
 }
 
 void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
@@ -443,13 +464,19 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
             continue;
         const FramePrep &f = frames[fi];
         taken[fi] = 1;
-        // a partner frame of the same plan, if any: both ride in one job
-        const FramePrep *f2 = nullptr;
-        for (size_t gi = fi + 1; gi < frames.size() && !f2; ++gi)
-            if (!taken[gi] && pairable(f, frames[gi])) {
-                f2 = &frames[gi];
-                taken[gi] = 1;
-            }
+        // partner frames of the same plan, if any: all ride in one job (1, 2 or 4 frames)
+        const FramePrep *more[kMaxFramesPerJob - 1] = {};
+        const int cap = max_frames_per_job(f);
+        std::vector<size_t> cand;
+        for (size_t gi = fi + 1; gi < frames.size() && (int)cand.size() + 1 < cap; ++gi)
+            if (!taken[gi] && shareable(f, frames[gi]))
+                cand.push_back(gi);
+        const int avail = (int)cand.size() + 1;
+        const int nf = avail >= 4 ? 4 : avail >= 2 ? 2 : 1;
+        for (int q = 0; q < nf - 1; ++q) {
+            more[q] = &frames[cand[q]];
+            taken[cand[q]] = 1;
+        }
         const bf_handle *h = f.h;
         const Plan *p = f.plan;
         BfJob j{};
@@ -486,9 +513,10 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
         j.iq_c1 = (float)(2.0 * kPi * r);
         j.iq_c2 = (float)(kPi * r);
         j.maxbits = (f.prec == kPrecIQ && f.stage == BF_OUT_LOGDB) ? f.maxbits : nullptr;
-        j.rf_map2 = f2 ? f2->map_dev : nullptr;
-        j.y2 = f2 ? f2->y : nullptr;
-        const int nf = f2 ? 2 : 1;
+        for (int q = 0; q < kMaxFramesPerJob - 1; ++q) {
+            j.rf_more[q] = more[q] ? more[q]->map_dev : nullptr;
+            j.y_more[q] = more[q] ? more[q]->y : nullptr;
+        }
         const int variant =
             ((nf * 16 + p->rows) * 4 + f.prec) * 16 + (j.modes & (BF_DMAS | BF_CF | BF_PDAS));
         groups[variant].push_back(j);
@@ -895,7 +923,7 @@ BF_API int bf_beamform(bf_handle *h, const int16_t *rf_dev, int32_t n_samples,
         if (rc)
             return rc;
         Plan *plan = nullptr;
-        rc = handle_plan(h, n_samples, angles_rad, n_angles, frame_prec(flags), &plan);
+        rc = handle_plan(h, n_samples, angles_rad, n_angles, flags, &plan);
         if (rc)
             return rc;
         if (plan == cc.plan && flags == cc.flags && rf_dev == cc.rf && out_dev == cc.out &&
@@ -1217,7 +1245,7 @@ BF_API int bf_plan_info(bf_handle *h, int32_t n_samples, const double *angles_ra
         return fail(BF_EINVAL, "null info");
     cudaSetDevice(h->device);
     Plan *p = nullptr;
-    rc = handle_plan(h, n_samples, angles_rad, n_angles, frame_prec(flags), &p);
+    rc = handle_plan(h, n_samples, angles_rad, n_angles, flags, &p);
     if (rc)
         return rc;
     const size_t n = (size_t)n_angles * p->tiles_x * p->tiles_z * h->g.ne;

@@ -378,7 +378,7 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
     // admission by device memory: the slot may have to grow
     const int prec = frame_prec(flags);
     Plan *plan = nullptr;
-    rc = handle_plan(h, ns, angles, na, prec, &plan);
+    rc = handle_plan(h, ns, angles, na, flags, &plan);
     size_t need = rf_bytes + out_bytes + (size_t)na * h->g.ne * (plan ? plan->nsp : 0) * pair_bytes(prec);
     if ((flags & BF_OUT_MASK) != BF_OUT_RF)
         need += out_bytes * ((flags & BF_OUT_MASK) == BF_OUT_LOGDB ? 2 : 1);

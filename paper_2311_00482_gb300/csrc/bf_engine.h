@@ -208,8 +208,11 @@ struct bf_batch {
 
 namespace bfi {
 
-// cfg < 0: the configuration bf_autotune chose for this workload, else the default
-int handle_plan(bf_handle *h, int ns, const double *angles, int na, int prec, Plan **out,
+// Plan of a frame with these arguments (`flags`: its mode and precision bits).
+// cfg < 0: the configuration bf_autotune chose for this workload, else the
+// default; a two-row configuration serves DAS / DMAS of RF records only (an
+// explicit one is refused for other frames, a tuned one replaced by the default).
+int handle_plan(bf_handle *h, int ns, const double *angles, int na, uint32_t flags, Plan **out,
                 int cfg = -1);
 int check_frame_args(bf_handle *h, int ns, const double *angles, int na, uint32_t flags);
 size_t frame_out_bytes(const bf_handle *h, uint32_t flags);

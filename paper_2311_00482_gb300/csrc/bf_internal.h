@@ -30,12 +30,16 @@ inline int tile_rows(int rows_per_thread) { return kWarps * rows_per_thread; }
 
 // Tile configurations the autotuner chooses from: rows per thread (tile
 // height 8 * rows) and the target bytes of one pipeline stage's sample
-// windows (channels per stage).  Entry 0 is the default.
+// windows (channels per stage).  Entry 0 is the default.  Two-row tiles serve
+// DAS / DMAS of RF records only, with up to four frames per job.
 struct TileConfig {
     int rows, stage_bytes;
 };
-constexpr TileConfig kTileConfigs[] = {{4, 24 << 10}, {4, 16 << 10}, {4, 32 << 10}, {8, 24 << 10}};
-constexpr int kNumTileConfigs = 4;
+constexpr TileConfig kTileConfigs[] = {{4, 24 << 10}, {4, 16 << 10}, {4, 32 << 10}, {8, 24 << 10},
+                                       {2, 12 << 10}};
+constexpr int kNumTileConfigs = 5;
+// Frames of one plan that one beamforming job may carry (sharing every delay).
+constexpr int kMaxFramesPerJob = 4;
 
 // Storage of the staged records: RF sample pairs in FP32 (mid, diff), FP16 or
 // BF16, or complex analytic-signal pairs for IQ beamforming (kPrecIQ, FP32).
@@ -60,10 +64,10 @@ struct BfJob {
     const CUtensorMap *valid_map;  // int2 [na * ne][nxp]: first / last counted row, (-1, -1) if none
     const CUtensorMap *dx2_map;    // float [ne][nxp]: max((kappa * (x_p - x_i))^2, 1e-30)
     float *y;             // [nmodes][nx][nz] beamformed output
-    // a second frame of the same plan sharing every delay (two-frame launches;
-    // null otherwise): its staged pairs and its output
-    const CUtensorMap *rf_map2;
-    float *y2;
+    // further frames of the same plan sharing every delay (multi-frame
+    // launches; null otherwise): their staged pairs and their outputs
+    const CUtensorMap *rf_more[kMaxFramesPerJob - 1];
+    float *y_more[kMaxFramesPerJob - 1];
     int nx, nz, na, ne;
     int wmax;             // window length (pairs) staged per channel and tile
     int box;              // TMA box width (pairs); wmax is a multiple of it
@@ -180,8 +184,9 @@ cudaError_t launch_demod(const DemodJob *jobs_dev, const int *row_prefix_dev, in
 size_t demod_smem_bytes(int ns);
 // f-k migration launches (bf_kernels.cu), in order on `stream`.
 cudaError_t launch_fkmig(const FkJob &job, cudaStream_t stream);
-// nf: frames per job (2: pairs of frames of one plan share the delays; DAS /
-// DMAS variants of the RF precisions only).
+// nf: frames per job (1, 2 or 4, with 4 on two-row tiles only; the frames of
+// one job share the delays; DAS / DMAS variants of the RF precisions only when
+// nf > 1 or rows == 2).
 cudaError_t launch_beamform(const BfJob *jobs_dev, const int *tile_prefix_dev, int njobs,
                             int total_tiles, size_t smem_bytes, int prec, int variant, int rows,
                             int nf, int *err_dev, cudaStream_t stream);

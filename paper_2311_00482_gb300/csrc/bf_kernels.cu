@@ -512,17 +512,17 @@ __device__ __forceinline__ void accumulate(uint32_t win, int wmax, int w0, float
     }
 }
 
-// One channel into the ROWS pixels of this thread for two frames of one plan:
-// the delay of each pixel is formed once and read from both frames' windows
-// (the second frame's window follows the first at wmax pairs).
-template <int PREC, bool DMAS, int ROWS, bool CHECK>
-__device__ __forceinline__ void accumulate_f2(uint32_t win, int wmax, int w0, float d2, int2 vr,
+// One channel into the ROWS pixels of this thread for NF frames of one plan:
+// the delay of each pixel is formed once and read from every frame's window
+// (frame f's window starts f * wmax pairs after the first).
+template <int PREC, bool DMAS, int ROWS, int NF, bool CHECK>
+__device__ __forceinline__ void accumulate_fn(uint32_t win, int wmax, int w0, float d2, int2 vr,
                                               int r_first, const float *Z, const float *fp,
-                                              const int *Kc, float *S1, float *T1, float *T2,
-                                              float *S1b, float *T1b, float *T2b)
+                                              const int *Kc, float (&S1)[NF][ROWS],
+                                              float (&T1)[NF][ROWS], float (&T2)[NF][ROWS])
 {
     constexpr int PB = PairIO<PREC>::kBytes;
-    const uint32_t second = (uint32_t)(wmax * PB);
+    const uint32_t fstride = (uint32_t)(wmax * PB);
     const unsigned span = (unsigned)(vr.y - vr.x);
     const f32x2_t D2 = pk2(d2, d2);
 #pragma unroll
@@ -535,17 +535,19 @@ __device__ __forceinline__ void accumulate_f2(uint32_t win, int wmax, int w0, fl
             const unsigned idx =
                 min((unsigned)(__float_as_int(m[h]) + Kc[jj] - w0), (unsigned)(wmax - 1));
             const uint32_t a = win + idx * PB;
-            const float v0 = PairIO<PREC>::interp(a, al[h]);
-            const float v1 = PairIO<PREC>::interp(a + second, al[h]);
+            float v[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+                v[f] = PairIO<PREC>::interp(a + (uint32_t)f * fstride, al[h]);
             if (!CHECK || (unsigned)(r_first + jj - vr.x) <= span) {
-                S1[jj] += v0;
-                S1b[jj] += v1;
-                if (DMAS) {
-                    const float a0 = fabsf(v0), a1 = fabsf(v1);
-                    T1[jj] += copysignf(sqrt_approx(a0), v0);
-                    T1b[jj] += copysignf(sqrt_approx(a1), v1);
-                    T2[jj] += a0;
-                    T2b[jj] += a1;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    S1[f][jj] += v[f];
+                    if (DMAS) {
+                        const float av = fabsf(v[f]);
+                        T1[f][jj] += copysignf(sqrt_approx(av), v[f]);
+                        T2[f][jj] += av;
+                    }
                 }
             }
         }
@@ -645,15 +647,16 @@ __device__ __forceinline__ void accumulate_iq(uint32_t win, int wmax, int w0, fl
     }
 }
 
-// Resident CTAs per SM the register budget is sized for: three 32-row tiles,
-// one 64-row tile (measured: capping 64-row tiles at two CTAs per SM costs
-// more in spills and lost overlap than the extra warps win).
-// Two-frame launches (NF = 2) hold twice the accumulators and twice the
-// windows per stage: two CTAs per SM.
+// Resident CTAs per SM the register budget is sized for: three 16- or 32-row
+// tiles, one 64-row tile (measured: capping 64-row tiles at two CTAs per SM
+// costs more in spills and lost overlap than the extra warps win).
+// Multi-frame jobs hold NF times the accumulators and NF windows per channel
+// and stage: two CTAs per SM when NF * ROWS = 8 (two frames of 4 rows, four
+// frames of 2 rows).
 template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS, int NF>
 constexpr int beamform_min_blocks()
 {
-    return ROWS != 8 ? (NF == 2 ? 2 : 3) : 1;
+    return ROWS == 8 ? 1 : (NF * ROWS >= 8 ? 2 : 3);
 }
 
 template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS, int NF>
@@ -700,7 +703,10 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
             const int *__restrict__ wtab = J->wtab;
             const int *__restrict__ btab = J->btab;
             const CUtensorMap *rf_map = J->rf_map;
-            const CUtensorMap *rf_map2 = J->rf_map2;
+            const CUtensorMap *rf_more[kMaxFramesPerJob - 1] = {};
+#pragma unroll
+            for (int f = 1; f < NF; ++f)
+                rf_more[f - 1] = J->rf_more[f - 1];
             const CUtensorMap *valid_map = J->valid_map;
             const CUtensorMap *dx2_map = J->dx2_map;
             const int box = J->box;
@@ -809,10 +815,11 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
                     const int row = a * ne + i0 + lane;
                     for (int off = 0; off < wmax; off += box)
                         tma_2d(dst + (size_t)off * PB, rf_map, (w0 + off) * XS, row, &sh.full[st]);
-                    if (NF == 2)  // the second frame's window right after the first
+#pragma unroll
+                    for (int f = 1; f < NF; ++f)  // the other frames' windows after the first
                         for (int off = 0; off < wmax; off += box)
-                            tma_2d(dst + (size_t)(wmax + off) * PB, rf_map2, (w0 + off) * XS, row,
-                                   &sh.full[st]);
+                            tma_2d(dst + (size_t)(f * wmax + off) * PB, rf_more[f - 1],
+                                   (w0 + off) * XS, row, &sh.full[st]);
                 }
                 wf = wf_next;
                 tb = tb_next;
@@ -841,11 +848,13 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
         int Kc[ROWS];
         float Z[ROWS], fp[ROWS];
         float S1[ROWS], T1[ROWS], T2[ROWS], Yd[ROWS], Su2[ROWS], P1[ROWS], Yp[ROWS];
-        float S1b[ROWS], T1b[ROWS], T2b[ROWS], Ydb[ROWS];  // second frame (NF = 2)
+        float FS1[NF][ROWS], FT1[NF][ROWS], FT2[NF][ROWS], FYd[NF][ROWS];  // NF > 1: per frame
 #pragma unroll
         for (int j = 0; j < ROWS; ++j) {
             S1[j] = T1[j] = T2[j] = Yd[j] = Su2[j] = P1[j] = Yp[j] = 0.f;
-            S1b[j] = T1b[j] = T2b[j] = Ydb[j] = 0.f;
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+                FS1[f][j] = FT1[f][j] = FT2[f][j] = FYd[f][j] = 0.f;
             Kc[j] = 0;
             fp[j] = Z[j] = 0.f;
         }
@@ -885,7 +894,9 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
                     fp[j] = cf + sh.tF[st][kTileCols + rr] - 0.5f;
                     Z[j] = sh.tZ[st][rr];
                     T1[j] = T2[j] = P1[j] = Ti[j] = 0.f;
-                    T1b[j] = T2b[j] = 0.f;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f)
+                        FT1[f][j] = FT2[f][j] = 0.f;
                 }
             }
             const uint32_t base = smem_u32(stage_base(st));
@@ -914,21 +925,21 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
                     accumulate_iq<DMAS, ROWS, true>(win_of(c), wmax, w0_of(c), d2_of(c), vr_of(c),
                                                     r_first, Z, fp, Kc, c1, c2, S1, Y1i, T1, Ti);
                 }
-            } else if constexpr (NF == 2) {
-                // every channel once, each delay serving both frames
+            } else if constexpr (NF > 1) {
+                // every channel once, each delay serving every frame
 #pragma unroll 1
                 for (; k < nf; ++k) {
                     const int c = L[k];
-                    accumulate_f2<PREC, DMAS, ROWS, false>(win_of(c), wmax, w0_of(c), d2_of(c),
-                                                           make_int2(0, 0), r_first, Z, fp, Kc, S1,
-                                                           T1, T2, S1b, T1b, T2b);
+                    accumulate_fn<PREC, DMAS, ROWS, NF, false>(win_of(c), wmax, w0_of(c),
+                                                               d2_of(c), make_int2(0, 0), r_first,
+                                                               Z, fp, Kc, FS1, FT1, FT2);
                 }
 #pragma unroll 1
                 for (; k < nt; ++k) {
                     const int c = L[k];
-                    accumulate_f2<PREC, DMAS, ROWS, true>(win_of(c), wmax, w0_of(c), d2_of(c),
-                                                          vr_of(c), r_first, Z, fp, Kc, S1, T1, T2,
-                                                          S1b, T1b, T2b);
+                    accumulate_fn<PREC, DMAS, ROWS, NF, true>(win_of(c), wmax, w0_of(c), d2_of(c),
+                                                              vr_of(c), r_first, Z, fp, Kc, FS1,
+                                                              FT1, FT2);
                 }
             } else {
                 // channels every pixel of the band counts, two at a time (twice the
@@ -965,8 +976,9 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
 #pragma unroll
                 for (int j = 0; j < ROWS; ++j) {
                     Yd[j] = fmaf(0.5f * T1[j], T1[j], fmaf(-0.5f, T2[j], Yd[j]));
-                    if (NF == 2)
-                        Ydb[j] = fmaf(0.5f * T1b[j], T1b[j], fmaf(-0.5f, T2b[j], Ydb[j]));
+#pragma unroll
+                    for (int f = 0; f < NF; ++f)
+                        FYd[f][j] = fmaf(0.5f * FT1[f][j], FT1[f][j], fmaf(-0.5f, FT2[f][j], FYd[f][j]));
                 }
             }
             if (DMAS && IQ && g == ngroups - 1) {  // Eq. (4): ((1/M) sum s^)^2 per angle
@@ -1030,6 +1042,29 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
         const float scale = J->out_scale;
         const size_t plane = (size_t)nx * nz;
         float *__restrict__ y = J->y;
+        if constexpr (NF > 1) {  // every frame of the job (DAS / DMAS only)
+            float *yf[NF];
+            yf[0] = y;
+#pragma unroll
+            for (int f = 1; f < NF; ++f)
+                yf[f] = J->y_more[f - 1];
+#pragma unroll
+            for (int j = 0; j < ROWS; ++j) {
+                const int iz = r_first + j;
+                if (iz >= nz)
+                    break;
+                const size_t o = (size_t)ix * nz + iz;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    int slot = 0;
+                    if (modes & BF_DAS)
+                        yf[f][(size_t)(slot++) * plane + o] = FS1[f][j] * scale;
+                    if (modes & BF_DMAS)
+                        yf[f][(size_t)(slot++) * plane + o] = FYd[f][j] * scale;
+                }
+            }
+            continue;
+        }
     #pragma unroll
         for (int j = 0; j < ROWS; ++j) {
             const int iz = r_first + j;
@@ -1048,14 +1083,6 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
             }
             if (modes & BF_PDAS)
                 y[(size_t)(slot++) * plane + o] = Yp[j] * scale;
-            if (NF == 2) {  // the second frame (DAS / DMAS only)
-                float *__restrict__ y2 = J->y2;
-                int slot2 = 0;
-                if (modes & BF_DAS)
-                    y2[(size_t)(slot2++) * plane + o] = S1b[j] * scale;
-                if (modes & BF_DMAS)
-                    y2[(size_t)(slot2++) * plane + o] = Ydb[j] * scale;
-            }
         }
     }
 }
@@ -1547,6 +1574,21 @@ cudaError_t launch_bf_pdr(const BfJob *jobs, const int *prefix, int njobs, int t
     return launch_bf_t<PREC, false, false, PDAS, ROWS>(jobs, prefix, njobs, tiles, smem, err, st);
 }
 
+// Jobs of NF frames each (DAS / DMAS of the RF precisions).
+template <int ROWS, int NF>
+cudaError_t launch_bf_frames(const BfJob *j, const int *pf, int njobs, int tiles, size_t smem,
+                             int prec, int dmas, int *err, cudaStream_t st)
+{
+    if (prec == kPrecF32)
+        return dmas ? launch_bf_t<kPrecF32, true, false, false, ROWS, NF>(j, pf, njobs, tiles, smem, err, st)
+                    : launch_bf_t<kPrecF32, false, false, false, ROWS, NF>(j, pf, njobs, tiles, smem, err, st);
+    if (prec == kPrecF16)
+        return dmas ? launch_bf_t<kPrecF16, true, false, false, ROWS, NF>(j, pf, njobs, tiles, smem, err, st)
+                    : launch_bf_t<kPrecF16, false, false, false, ROWS, NF>(j, pf, njobs, tiles, smem, err, st);
+    return dmas ? launch_bf_t<kPrecBF16, true, false, false, ROWS, NF>(j, pf, njobs, tiles, smem, err, st)
+                : launch_bf_t<kPrecBF16, false, false, false, ROWS, NF>(j, pf, njobs, tiles, smem, err, st);
+}
+
 template <int PREC>
 cudaError_t launch_bf_p(const BfJob *jobs, const int *prefix, int njobs, int tiles, size_t smem,
                         int dmas, int cf, int pdas, int rows, int *err, cudaStream_t st)
@@ -1621,19 +1663,21 @@ cudaError_t launch_beamform(const BfJob *jobs_dev, const int *tile_prefix_dev, i
         return cudaSuccess;
     const int dmas = (variant & BF_DMAS) ? 1 : 0, cf = (variant & BF_CF) ? 1 : 0;
     const int pdas = (variant & BF_PDAS) ? 1 : 0;
-    if (nf == 2) {  // pairs of frames sharing the delays: DAS / DMAS, 32-row tiles
-        if (cf || pdas || rows != 4 || prec == kPrecIQ)
+    if (nf > 1 || rows == 2) {
+        // frames sharing the delays, and every two-row tile: DAS / DMAS of RF records
+        if (cf || pdas || prec == kPrecIQ)
             return cudaErrorInvalidValue;
         const BfJob *j = jobs_dev;
         const int *pf = tile_prefix_dev;
-        if (prec == kPrecF32)
-            return dmas ? launch_bf_t<kPrecF32, true, false, false, 4, 2>(j, pf, njobs, total_tiles, smem_bytes, err_dev, stream)
-                        : launch_bf_t<kPrecF32, false, false, false, 4, 2>(j, pf, njobs, total_tiles, smem_bytes, err_dev, stream);
-        if (prec == kPrecF16)
-            return dmas ? launch_bf_t<kPrecF16, true, false, false, 4, 2>(j, pf, njobs, total_tiles, smem_bytes, err_dev, stream)
-                        : launch_bf_t<kPrecF16, false, false, false, 4, 2>(j, pf, njobs, total_tiles, smem_bytes, err_dev, stream);
-        return dmas ? launch_bf_t<kPrecBF16, true, false, false, 4, 2>(j, pf, njobs, total_tiles, smem_bytes, err_dev, stream)
-                    : launch_bf_t<kPrecBF16, false, false, false, 4, 2>(j, pf, njobs, total_tiles, smem_bytes, err_dev, stream);
+        if (rows == 4 && nf == 2)
+            return launch_bf_frames<4, 2>(j, pf, njobs, total_tiles, smem_bytes, prec, dmas, err_dev, stream);
+        if (rows == 2 && nf == 4)
+            return launch_bf_frames<2, 4>(j, pf, njobs, total_tiles, smem_bytes, prec, dmas, err_dev, stream);
+        if (rows == 2 && nf == 2)
+            return launch_bf_frames<2, 2>(j, pf, njobs, total_tiles, smem_bytes, prec, dmas, err_dev, stream);
+        if (rows == 2 && nf == 1)
+            return launch_bf_frames<2, 1>(j, pf, njobs, total_tiles, smem_bytes, prec, dmas, err_dev, stream);
+        return cudaErrorInvalidValue;
     }
     if (prec == kPrecIQ) {  // IQ-DAS always, BB-DMAS in the DMAS slot
         if (rows == 4)

@@ -45,8 +45,8 @@ def test_autotune_choice_is_kept_and_exact(torch, monkeypatch):
         bf.bf_destroy(h)
 
 
-@pytest.mark.parametrize("rows", ["4", "8"])
-def test_both_tile_heights_match_the_oracle(torch, monkeypatch, rows):
+@pytest.mark.parametrize("rows", ["2", "4", "8"])
+def test_every_tile_height_matches_the_oracle(torch, monkeypatch, rows):
     monkeypatch.setenv("BF_TILE_ROWS", rows)
     acq = synth.SPECKLE_POINTS_128.with_(nx=70, nz=101, angles_deg=(0.0, 7.0))
     rf, _ = synth.speckle_points_frame(acq)

@@ -412,3 +412,53 @@ def test_frames_of_one_plan_share_delays_in_pairs(torch, prec):
         batch.close()
     finally:
         bf.bf_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [bf.BF_PREC_FP32, bf.BF_PREC_BF16])
+def test_two_row_tiles_share_delays_in_fours(torch, monkeypatch, prec):
+    """Seven frames of one plan on 16-row tiles: one four-frame job, one
+    two-frame job and one frame alone; every frame matches the oracle and its
+    single-frame result on the same tiles."""
+    monkeypatch.setenv("BF_TILE_ROWS", "2")
+    acq = synth.SPECKLE_POINTS_128.with_(nx=70, nz=90, angles_deg=(-4.0, 4.0))
+    flags = bf.BF_DAS | bf.BF_DMAS | prec
+    rfs = [synth.speckle_points_frame(acq, seed=synth.BASE_SEED + 520 + k)[0] for k in range(7)]
+    h = make_handle(acq)
+    try:
+        assert bf.bf_plan_info(h, acq.n_samples, acq.angles_rad, flags)["rows"] == 2
+        rf_d = [torch.from_numpy(r).cuda() for r in rfs]
+        outs = [torch.full((2, acq.nx, acq.nz), float("nan"), device="cuda") for _ in rfs]
+        batch = bf.Batch([(h, rf_d[k], acq.n_samples, acq.angles_rad, flags, outs[k])
+                          for k in range(7)])
+        batch.launch()
+        batch.status()
+        for k in range(7):
+            got = outs[k].cpu().numpy().astype(np.float64)
+            ref = oracle_all(acq, rfs[k])
+            assert_close(got[0], ref["das"], prec, "das %d" % k)
+            assert_close(got[1], ref["dmas"], prec, "dmas %d" % k)
+            single = run_gpu(torch, acq, rfs[k], flags, h=h)
+            np.testing.assert_allclose(got, single, rtol=0,
+                                       atol=2e-6 * np.max(np.abs(single)) + 1e-30)
+        batch.close()
+    finally:
+        bf.bf_destroy(h)
+
+
+def test_two_row_tiles_leave_other_combiners_on_the_default(torch, monkeypatch):
+    """Two-row tiles carry DAS / DMAS only: a coherence-factor or pDAS frame on a
+    handle asked for them keeps the default 32-row tiles and still matches."""
+    monkeypatch.setenv("BF_TILE_ROWS", "2")
+    acq = synth.SPECKLE_POINTS_128.with_(nx=40, nz=60, angles_deg=(0.0,))
+    rf, _ = synth.speckle_points_frame(acq)
+    h = make_handle(acq)
+    try:
+        assert bf.bf_plan_info(h, acq.n_samples, acq.angles_rad, bf.BF_DAS)["rows"] == 2
+        flags = bf.BF_DAS | bf.BF_CF
+        assert bf.bf_plan_info(h, acq.n_samples, acq.angles_rad, flags)["rows"] == 4
+        ref = oracle_all(acq, rf)
+        got = run_gpu(torch, acq, rf, flags, h=h)
+        assert_close(got[0], ref["das"], bf.BF_PREC_FP32, "das")
+        assert_close(got[1], ref["cf"], bf.BF_PREC_FP32, "cf")
+    finally:
+        bf.bf_destroy(h)
