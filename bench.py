@@ -353,9 +353,13 @@ def run_ours(args):
             sm_max = float(json.load(open(peaks_path)).get("sm_max_mhz", sm_max))
         except (OSError, ValueError):
             pass
-    # Binding unit of DAS+DMAS: two square roots per active triple on the
-    # special-function units (16 per SM per clock).
-    peak_pch = sm_count * 16 * sm_max * 1e6 / 2.0
+    # Binding unit of DAS+DMAS: the special-function units (16 per SM per
+    # clock).  Each frame's active triple needs its own signed square root
+    # (DMAS); the receive distance's square root belongs to the (pixel,
+    # channel, angle) geometry, which the step's B frames share, so it costs
+    # at least 1 / B per frame's triple.
+    sfu_per_triple = 1.0 + 1.0 / B
+    peak_pch = sm_count * 16 * sm_max * 1e6 / sfu_per_triple
     beam_s = statistics.median(bf_ms) / 1e3 if bf_ms else beam_ms / 1e3
     achieved_pch = B * active / beam_s
     line = {
@@ -381,8 +385,9 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": "beamform_kernel",
                      "achieved": achieved_pch / 1e9, "peak": peak_pch / 1e9,
                      "unit": "G active pixel*ch/s", "frac": achieved_pch / peak_pch,
-                     "peak_basis": "%d SMs x 16 SFU/clk x %.0f MHz / 2 square roots per triple"
-                                   % (sm_count, sm_max),
+                     "peak_basis": "%d SMs x 16 SFU/clk x %.0f MHz / (1 signed root per frame's "
+                                   "triple + 1 receive-distance root per (pixel, channel, angle) "
+                                   "shared by the step's %d frames)" % (sm_count, sm_max, B),
                      "traffic": beamform_traffic(B),
                      "traffic_unit": "DRAM bytes per launch (ncu capture scaled by frames)"},
         "e2e": {"value": job_value(ws, units_step, e2e_steps, t_e2e), "unit": UNIT,

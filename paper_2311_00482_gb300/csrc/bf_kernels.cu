@@ -1063,26 +1063,27 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
                         yf[f][(size_t)(slot++) * plane + o] = FYd[f][j] * scale;
                 }
             }
-            continue;
-        }
-    #pragma unroll
-        for (int j = 0; j < ROWS; ++j) {
-            const int iz = r_first + j;
-            if (iz >= nz)
-                break;
-            const size_t o = (size_t)ix * nz + iz;
-            int slot = 0;
-            if (modes & BF_DAS)
-                y[(size_t)(slot++) * plane + o] = S1[j] * scale;
-            if (modes & BF_DMAS)
-                y[(size_t)(slot++) * plane + o] = Yd[j] * scale;
-            if (modes & BF_CF) {
-                const float mtot = (float)na * (float)__ldg(J->apcnt + o);
-                const float den = mtot * Su2[j];
-                y[(size_t)(slot++) * plane + o] = den > 0.f ? (S1[j] * S1[j] / den) * S1[j] * scale : 0.f;
+        } else {
+#pragma unroll
+            for (int j = 0; j < ROWS; ++j) {
+                const int iz = r_first + j;
+                if (iz >= nz)
+                    break;
+                const size_t o = (size_t)ix * nz + iz;
+                int slot = 0;
+                if (modes & BF_DAS)
+                    y[(size_t)(slot++) * plane + o] = S1[j] * scale;
+                if (modes & BF_DMAS)
+                    y[(size_t)(slot++) * plane + o] = Yd[j] * scale;
+                if (modes & BF_CF) {
+                    const float mtot = (float)na * (float)__ldg(J->apcnt + o);
+                    const float den = mtot * Su2[j];
+                    y[(size_t)(slot++) * plane + o] =
+                        den > 0.f ? (S1[j] * S1[j] / den) * S1[j] * scale : 0.f;
+                }
+                if (modes & BF_PDAS)
+                    y[(size_t)(slot++) * plane + o] = Yp[j] * scale;
             }
-            if (modes & BF_PDAS)
-                y[(size_t)(slot++) * plane + o] = Yp[j] * scale;
         }
     }
 }
