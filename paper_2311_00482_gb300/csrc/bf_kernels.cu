@@ -1048,6 +1048,29 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
 #pragma unroll
             for (int f = 1; f < NF; ++f)
                 yf[f] = J->y_more[f - 1];
+            unsigned long long align = 0;
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+                align |= reinterpret_cast<unsigned long long>(yf[f]);
+            if ((nz & 1) == 0 && (align & 7) == 0 && r_first + ROWS <= nz) {
+                // rows in pairs: one 8-byte store per pair (8-byte aligned images,
+                // nz even, r_first even)
+#pragma unroll
+                for (int j = 0; j < ROWS; j += 2) {
+                    const size_t o = (size_t)ix * nz + r_first + j;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        int slot = 0;
+                        if (modes & BF_DAS)
+                            *reinterpret_cast<float2 *>(yf[f] + (size_t)(slot++) * plane + o) =
+                                make_float2(FS1[f][j] * scale, FS1[f][j + 1] * scale);
+                        if (modes & BF_DMAS)
+                            *reinterpret_cast<float2 *>(yf[f] + (size_t)(slot++) * plane + o) =
+                                make_float2(FYd[f][j] * scale, FYd[f][j + 1] * scale);
+                    }
+                }
+                continue;
+            }
 #pragma unroll
             for (int j = 0; j < ROWS; ++j) {
                 const int iz = r_first + j;
