@@ -441,7 +441,8 @@ static int max_frames_per_job(const FramePrep &a)
     if (a.prec == kPrecIQ || (m & ~(BF_DAS | BF_DMAS)) != 0)
         return 1;
     for (int nf = a.plan->rows == 2 ? 4 : a.plan->rows == 4 ? 2 : 1; nf > 1; nf /= 2)
-        if (beamform_smem_bytes(a.plan->wmax, a.plan->group, a.prec, nf) <= (size_t)kMaxSmemPerCta)
+        if (beamform_smem_bytes(a.plan->wmax, a.plan->group, a.prec, nf, a.plan->rows) <=
+            (size_t)kMaxSmemPerCta)
             return nf;
     return 1;
 }
@@ -520,7 +521,7 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
         const int variant =
             ((nf * 16 + p->rows) * 4 + f.prec) * 16 + (j.modes & (BF_DMAS | BF_CF | BF_PDAS));
         groups[variant].push_back(j);
-        const size_t sm = beamform_smem_bytes(p->wmax, p->group, f.prec, nf);
+        const size_t sm = beamform_smem_bytes(p->wmax, p->group, f.prec, nf, p->rows);
         group_smem[variant] = std::max(group_smem[variant], sm);
         hl.smem = std::max(hl.smem, sm);
     }

@@ -36,8 +36,8 @@ struct TileConfig {
     int rows, stage_bytes;
 };
 constexpr TileConfig kTileConfigs[] = {{4, 24 << 10}, {4, 16 << 10}, {4, 32 << 10}, {8, 24 << 10},
-                                       {2, 12 << 10}};
-constexpr int kNumTileConfigs = 5;
+                                       {2, 10 << 10}, {2, 11 << 10}};
+constexpr int kNumTileConfigs = 6;
 // Frames of one plan that one beamforming job may carry (sharing every delay).
 constexpr int kMaxFramesPerJob = 4;
 
@@ -198,7 +198,9 @@ cudaError_t launch_log(const LogJob *jobs_dev, const int *blk_prefix_dev, int nj
 // per pixel); job.y receives the beamformed modes.
 cudaError_t launch_plain(const BfJob &job, const int16_t *rf, const int2 *valid, const float *dx2,
                          int nxp, int ns, cudaStream_t stream);
-size_t beamform_smem_bytes(int wmax, int group, int prec, int nf = 1);
+// Dynamic shared memory of a beamforming CTA: header, the multi-frame
+// staging area (nf > 1) and the pipeline stages.
+size_t beamform_smem_bytes(int wmax, int group, int prec, int nf = 1, int rows = 4);
 int log_blocks(long long pixels);
 int envelope_cols_per_block(int fft_m);
 size_t envelope_smem_bytes(int fft_m, int bluestein);

@@ -338,6 +338,9 @@ struct SmemHeader {
     int tK[kStages][kTileCols + 64];
     float tF[kStages][kTileCols + 64];
     float tZ[kStages][64];
+    // multi-frame jobs: consumers -> storer (the tile's images are staged),
+    // storer -> consumers (the staging area is free again)
+    uint64_t epi_full, epi_empty;
 };
 constexpr int kHeaderBytes = 4096;
 static_assert(sizeof(SmemHeader) <= kHeaderBytes, "header");
@@ -401,11 +404,61 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+__device__ __forceinline__ void sts_f32x2(uint32_t addr, float a, float b)
+{
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(a), "f"(b) : "memory");
+}
+
+// This thread's shared-memory writes, visible to the async proxy (bulk copies).
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Bulk copy shared -> global (16-byte aligned addresses, size a multiple of 16),
+// tracked in this thread's bulk groups.
+__device__ __forceinline__ void bulk_store(void *gdst, uint32_t ssrc, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+                 "r"(ssrc), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// Every committed bulk copy of this thread has read its shared-memory source.
+__device__ __forceinline__ void bulk_wait_read()
+{
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// Every committed bulk copy of this thread is complete.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // Bytes of one pipeline stage: tables (int2 rows + float dx^2) and windows.
 // (nf frames' windows per channel in two-frame launches)
 __host__ __device__ __forceinline__ int stage_bytes(int group, int wmax, int pb, int nf = 1)
 {
     return group * (kTileCols * 12 + nf * wmax * pb);
+}
+
+// Multi-frame jobs stage their images in shared memory for the storer warp:
+// per image plane (frame, combiner) and tile column the tile's rows, then
+// kEpiPad floats (16-byte aligned runs for the bulk copies, at most 4-way bank
+// conflicts for the consumers' writes).  It sits between the header and the
+// pipeline stages.
+constexpr int kEpiPad = 4;
+__host__ __device__ constexpr int epi_col_floats(int rows) { return kWarps * rows + kEpiPad; }
+__host__ __device__ constexpr int epi_bytes(int nf, int rows)
+{
+    return nf > 1 ? nf * 2 * kTileCols * epi_col_floats(rows) * (int)sizeof(float) : 0;
+}
+// Threads of a beamforming CTA: the consumer warps, the producer warp and, in
+// multi-frame jobs, the storer warp.
+template <int NF>
+constexpr int beamform_threads()
+{
+    return kThreads + 32 + (NF > 1 ? 32 : 0);
 }
 
 // ---- packed FP32 pairs (Blackwell f32x2 arithmetic): two rows' delays at once
@@ -660,7 +713,8 @@ constexpr int beamform_min_blocks()
 }
 
 template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS, int NF>
-__global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS, CF, PDAS, ROWS, NF>()))
+__global__ void __launch_bounds__(beamform_threads<NF>(),
+                                  (beamform_min_blocks<PREC, DMAS, CF, PDAS, ROWS, NF>()))
     beamform_kernel(const BfJob *__restrict__ jobs, const int *__restrict__ tile_prefix, int njobs,
                     int total_tiles, int stage_stride, int *__restrict__ err)
 {
@@ -677,16 +731,79 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
     // it finishes the current one.  Every stage has the launch's largest
     // stage size; inside a stage the layout is the job's: int2 rows [G][32],
     // float dx^2 [G][32], windows [G][wmax].
-    auto stage_base = [&](int st) { return smem + kHeaderBytes + (size_t)st * stage_stride; };
+    constexpr int EPI = epi_bytes(NF, ROWS);
+    constexpr int CFL = epi_col_floats(ROWS);
+    auto stage_base = [&](int st) {
+        return smem + kHeaderBytes + EPI + (size_t)st * stage_stride;
+    };
+    // multi-frame jobs whose images take the bulk-copy epilogue: 16-byte aligned
+    // images and columns (nz a multiple of 4), uniform over the job
+    auto staged_job = [&](const BfJob *J) {
+        if (NF == 1)
+            return false;
+        unsigned long long a = reinterpret_cast<unsigned long long>(J->y);
+#pragma unroll
+        for (int f = 1; f < NF; ++f)
+            a |= reinterpret_cast<unsigned long long>(J->y_more[f - 1]);
+        return (J->nz & 3) == 0 && (a & 15) == 0;
+    };
 
     if (threadIdx.x == 0) {
         for (int st = 0; st < kStages; ++st) {
             mbar_init(&sh.full[st], 1);
             mbar_init(&sh.empty[st], kWarps);
         }
+        mbar_init(&sh.epi_full, kWarps);
+        mbar_init(&sh.epi_empty, 1);
         mbar_fence_init();
     }
     __syncthreads();
+
+    if (NF > 1 && warp == kWarps + 1) {
+        // ================= storer warp (multi-frame jobs): the consumers' staged
+        // images out to global memory, per column and image one bulk copy of
+        // the tile's rows (lane = column)
+        const uint32_t eb = smem_u32(smem + kHeaderBytes) + (uint32_t)(lane * CFL) * 4u;
+        unsigned u = 0;
+        for (int tg = blockIdx.x; tg < total_tiles; tg += gridDim.x) {
+            const int jb = find_job(tile_prefix, njobs, tg);
+            const BfJob *J = jobs + jb;
+            if (!staged_job(J))
+                continue;
+            const int tile = tg - __ldg(tile_prefix + jb);
+            const int nx = J->nx, nz = J->nz, modes = J->modes;
+            const int tx = tile % J->tiles_x, tz = tile / J->tiles_x;
+            const unsigned long long deadline = global_ns() + kWaitNs;
+            if (!__all_sync(0xffffffffu, mbar_wait(&sh.epi_full, u & 1u, deadline, err)))
+                break;
+            const int ix = tx * kTileCols + lane, r0 = tz * TR;
+            const unsigned bytes = (unsigned)min(TR, nz - r0) * 4u;
+            const size_t plane = (size_t)nx * nz;
+            if (ix < nx) {
+                int p = 0;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    float *yf = f == 0 ? J->y : J->y_more[f - 1];
+                    float *col = yf + (size_t)ix * nz + r0;
+                    int slot = 0;
+                    if (modes & BF_DAS)
+                        bulk_store(col + (size_t)(slot++) * plane,
+                                   eb + (uint32_t)(p++ * kTileCols * CFL) * 4u, bytes);
+                    if (modes & BF_DMAS)
+                        bulk_store(col + (size_t)(slot++) * plane,
+                                   eb + (uint32_t)(p++ * kTileCols * CFL) * 4u, bytes);
+                }
+            }
+            bulk_commit();
+            bulk_wait_read();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&sh.epi_empty);
+            ++u;
+        }
+        bulk_wait_all();
+        return;
+    }
 
     if (warp == kWarps) {
         // ================= producer warp: TMA copies of every step's stage
@@ -832,6 +949,7 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
 
     // ================= consumer warps: one column per lane, ROWS rows per thread
     unsigned r = 0;
+    unsigned epi_use = 0;  // staged tiles so far (multi-frame jobs)
     for (int tg = blockIdx.x; tg < total_tiles; tg += gridDim.x) {
         const unsigned long long deadline = global_ns() + kWaitNs;
         const int jb = find_job(tile_prefix, njobs, tg);
@@ -1036,13 +1154,47 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
             }
             continue;
         }
-        if (!col_ok)
-            continue;
         const int modes = J->modes;
         const float scale = J->out_scale;
         const size_t plane = (size_t)nx * nz;
         float *__restrict__ y = J->y;
         if constexpr (NF > 1) {  // every frame of the job (DAS / DMAS only)
+            if (staged_job(J)) {
+                // the tile's images into the staging area (plane p = frame, then
+                // combiner; column = lane), then the storer warp writes them out
+                if (epi_use > 0 &&
+                    !__all_sync(0xffffffffu,
+                                mbar_wait(&sh.epi_empty, (epi_use - 1) & 1u, deadline, err)))
+                    return;  // warp-uniform: a bounded wait ran out (error bit set)
+                const uint32_t eb =
+                    smem_u32(smem + kHeaderBytes) + (uint32_t)(lane * CFL + warp * ROWS) * 4u;
+                int p = 0;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    if (modes & BF_DAS) {
+#pragma unroll
+                        for (int j = 0; j < ROWS; j += 2)
+                            sts_f32x2(eb + (uint32_t)(p * kTileCols * CFL + j) * 4u,
+                                      FS1[f][j] * scale, FS1[f][j + 1] * scale);
+                        ++p;
+                    }
+                    if (modes & BF_DMAS) {
+#pragma unroll
+                        for (int j = 0; j < ROWS; j += 2)
+                            sts_f32x2(eb + (uint32_t)(p * kTileCols * CFL + j) * 4u,
+                                      FYd[f][j] * scale, FYd[f][j + 1] * scale);
+                        ++p;
+                    }
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(&sh.epi_full);
+                ++epi_use;
+                continue;
+            }
+            if (!col_ok)
+                continue;
             float *yf[NF];
             yf[0] = y;
 #pragma unroll
@@ -1087,6 +1239,8 @@ __global__ void __launch_bounds__(kThreads + 32, (beamform_min_blocks<PREC, DMAS
                 }
             }
         } else {
+            if (!col_ok)
+                continue;
 #pragma unroll
             for (int j = 0; j < ROWS; ++j) {
                 const int iz = r_first + j;
@@ -1574,14 +1728,15 @@ cudaError_t launch_bf_t(const BfJob *jobs, const int *prefix, int njobs, int til
 {
     auto k = beamform_kernel<PREC, DMAS, CF, PDAS, ROWS, NF>;
     // several CTAs per SM need the largest shared-memory carveout
+    constexpr int threads = beamform_threads<NF>();
     int sms = 0, occ = 0;
-    cudaError_t e = kernel_setup((const void *)k, smem, kThreads + 32, true, &sms, &occ);
+    cudaError_t e = kernel_setup((const void *)k, smem, threads, true, &sms, &occ);
     if (e != cudaSuccess)
         return e;
     // persistent grid: every CTA resident at once, each walking the tiles
     const int grid = std::max(1, std::min(tiles, std::max(occ, 1) * sms));
-    const int stride = (int)((smem - kHeaderBytes) / kStages);
-    k<<<grid, kThreads + 32, smem, st>>>(jobs, prefix, njobs, tiles, stride, err);
+    const int stride = (int)((smem - kHeaderBytes - epi_bytes(NF, ROWS)) / kStages);
+    k<<<grid, threads, smem, st>>>(jobs, prefix, njobs, tiles, stride, err);
     return cudaGetLastError();
 }
 
@@ -1626,9 +1781,10 @@ cudaError_t launch_bf_p(const BfJob *jobs, const int *prefix, int njobs, int til
 
 }  // namespace
 
-size_t beamform_smem_bytes(int wmax, int group, int prec, int nf)
+size_t beamform_smem_bytes(int wmax, int group, int prec, int nf, int rows)
 {
-    return (size_t)kHeaderBytes + (size_t)kStages * stage_bytes(group, wmax, pair_bytes(prec), nf);
+    return (size_t)kHeaderBytes + (size_t)epi_bytes(nf, rows) +
+           (size_t)kStages * stage_bytes(group, wmax, pair_bytes(prec), nf);
 }
 
 // Image columns per envelope CTA for a power-of-two transform: two per
