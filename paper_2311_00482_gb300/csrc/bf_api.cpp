@@ -137,6 +137,20 @@ static int encode_pairs_map(CUtensorMap *map, void *base, int rows, int nsp, int
     return encode_map(map, base, rows, nsp * k, pair_bytes(prec) / k, box * k, 1);
 }
 
+// Pairs per frame of one tensor copy of an nf-frame job's interleaved window
+// ([pair][frame], wmax pairs): the largest divisor of wmax whose copy spans at
+// most kMaxBox elements and a multiple of 16 bytes (0: none).
+static int interleaved_box(int wmax, int nf, int prec)
+{
+    const int pb = pair_bytes(prec);
+    if ((wmax * nf * pb) % 16 != 0)
+        return 0;
+    for (int d = std::min(wmax, kMaxBox / nf); d >= 1; --d)
+        if (wmax % d == 0 && (d * nf * pb) % 16 == 0)
+            return d;
+    return 0;
+}
+
 // -------------------------------------------------------- envelope tables --
 
 static std::mutex g_env_mu;
@@ -355,8 +369,11 @@ size_t frame_out_bytes(const bf_handle *h, uint32_t flags)
     return (size_t)frame_images(flags) * (size_t)h->g.nx * (size_t)h->g.nz * sizeof(float);
 }
 
+static int plan_frames_per_job(const Plan *p, int modes, int prec, int cap);
+
 int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *angles, int na,
-                  uint32_t flags, float *out_dev, FrameScratch &s, FramePrep &fp, int cfg)
+                  uint32_t flags, float *out_dev, FrameScratch &s, FramePrep &fp, int cfg,
+                  int nf_cap)
 {
     int rc = check_frame_args(h, ns, angles, na, flags);
     if (rc)
@@ -371,7 +388,11 @@ int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *ang
     const int stage = flags & BF_OUT_MASK;
     const size_t img = (size_t)h->g.nx * h->g.nz;
     const int rows = na * h->g.ne;
-    rc = s.pairs.ensure((size_t)rows * plan->nsp * pair_bytes(prec));
+    // room for the frames of a job this frame may lead (interleaved pairs)
+    const int cap = plan_frames_per_job(plan, modes, prec, nf_cap);
+    rc = s.pairs.ensure((size_t)cap * rows * plan->nsp * pair_bytes(prec));
+    if (!rc && cap > 1)
+        rc = s.map_nf.ensure(sizeof(CUtensorMap));
     if (!rc && stage != BF_OUT_RF && !iq)  // IQ images are magnitudes already
         rc = s.y.ensure(nm * img * sizeof(float));
     if (!rc && stage == BF_OUT_LOGDB)
@@ -403,6 +424,7 @@ int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *ang
     }
     fp.maxbits = (unsigned *)s.maxbits.p;
     fp.map_dev = (CUtensorMap *)s.map.p;
+    fp.nf_cap = cap;
     if (s.map_base != s.pairs.p || s.map_rows != rows || s.map_nsp != plan->nsp ||
         s.map_box != plan->box || s.map_prec != prec) {
         rc = encode_pairs_map(&s.map_host, s.pairs.p, rows, plan->nsp, plan->box, prec);
@@ -435,16 +457,51 @@ int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *ang
 // Frames can share one beamforming job (and every delay) when they use the
 // same plan with the same combiners: DAS and / or DMAS of RF records, up to
 // two frames on 32-row tiles and four on 16-row tiles.
-static int max_frames_per_job(const FramePrep &a)
+static int plan_frames_per_job(const Plan *p, int modes, int prec, int cap)
 {
-    const int m = a.modes & (BF_MODE_MASK | BF_IQ_MASK);
-    if (a.prec == kPrecIQ || (m & ~(BF_DAS | BF_DMAS)) != 0)
+    const int m = modes & (BF_MODE_MASK | BF_IQ_MASK);
+    if (prec == kPrecIQ || (m & ~(BF_DAS | BF_DMAS)) != 0)
         return 1;
-    for (int nf = a.plan->rows == 2 ? 4 : a.plan->rows == 4 ? 2 : 1; nf > 1; nf /= 2)
-        if (beamform_smem_bytes(a.plan->wmax, a.plan->group, a.prec, nf, a.plan->rows) <=
-            (size_t)kMaxSmemPerCta)
+    for (int nf = p->rows == 2 ? 4 : p->rows == 4 ? 2 : 1; nf > 1; nf /= 2)
+        if (nf <= cap &&
+            beamform_smem_bytes(p->wmax, p->group, prec, nf, p->rows) <= (size_t)kMaxSmemPerCta &&
+            interleaved_box(p->wmax, nf, prec) > 0)
             return nf;
     return 1;
+}
+
+int job_frames_cap(const Plan *p, uint32_t flags, int cap)
+{
+    return plan_frames_per_job(p, (int)(flags & (BF_MODE_MASK | BF_IQ_MASK)), frame_prec(flags), cap);
+}
+
+static int max_frames_per_job(const FramePrep &a)
+{
+    return plan_frames_per_job(a.plan, a.modes, a.prec, a.nf_cap);
+}
+
+// The lead frame's tensor map of its job's interleaved pairs, encoded when the
+// layout changed (uploaded by upload_maps).
+static int lead_map(const FramePrep &f, int nf, int box)
+{
+    FrameScratch &S = *f.scratch;
+    const int rows = f.na * f.h->g.ne, nsp = f.plan->nsp;
+    if (!S.map_nf.p)
+        return fail(BF_EINVAL, "frame scratch has no multi-frame map");
+    if (S.mapnf_base == f.pairs && S.mapnf_rows == rows && S.mapnf_nsp == nsp &&
+        S.mapnf_box == box && S.mapnf_prec == f.prec && S.mapnf_nf == nf)
+        return BF_OK;
+    int rc = encode_map(&S.map_nf_host, f.pairs, rows, nsp * nf, pair_bytes(f.prec), box * nf, 1);
+    if (rc)
+        return rc;
+    S.mapnf_base = f.pairs;
+    S.mapnf_rows = rows;
+    S.mapnf_nsp = nsp;
+    S.mapnf_box = box;
+    S.mapnf_prec = f.prec;
+    S.mapnf_nf = nf;
+    S.mapnf_dirty = true;
+    return BF_OK;
 }
 
 static bool shareable(const FramePrep &a, const FramePrep &b)
@@ -460,6 +517,10 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
     std::map<int, std::vector<BfJob>> groups;
     std::map<int, size_t> group_smem;
     std::vector<char> taken(frames.size(), 0);
+    // frames riding in another frame's job (the lead, the first of them, carries
+    // the job's ingest)
+    std::vector<char> member(frames.size(), 0);
+    std::vector<std::vector<size_t>> partners(frames.size());
     for (size_t fi = 0; fi < frames.size(); ++fi) {
         if (taken[fi])
             continue;
@@ -473,10 +534,15 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
             if (!taken[gi] && shareable(f, frames[gi]))
                 cand.push_back(gi);
         const int avail = (int)cand.size() + 1;
-        const int nf = avail >= 4 ? 4 : avail >= 2 ? 2 : 1;
+        int nf = avail >= 4 ? 4 : avail >= 2 ? 2 : 1;
+        const int box_nf = nf > 1 ? interleaved_box(f.plan->wmax, nf, f.prec) : 0;
+        if (nf > 1 && lead_map(f, nf, box_nf) != BF_OK)
+            nf = 1;  // no interleaved map: every frame alone
         for (int q = 0; q < nf - 1; ++q) {
             more[q] = &frames[cand[q]];
             taken[cand[q]] = 1;
+            member[cand[q]] = 1;
+            partners[fi].push_back(cand[q]);
         }
         const bf_handle *h = f.h;
         const Plan *p = f.plan;
@@ -514,9 +580,11 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
         j.iq_c1 = (float)(2.0 * kPi * r);
         j.iq_c2 = (float)(kPi * r);
         j.maxbits = (f.prec == kPrecIQ && f.stage == BF_OUT_LOGDB) ? f.maxbits : nullptr;
-        for (int q = 0; q < kMaxFramesPerJob - 1; ++q) {
-            j.rf_more[q] = more[q] ? more[q]->map_dev : nullptr;
+        for (int q = 0; q < kMaxFramesPerJob - 1; ++q)
             j.y_more[q] = more[q] ? more[q]->y : nullptr;
+        if (nf > 1) {  // the frames' pairs interleaved in the lead's scratch
+            j.rf_map = (const CUtensorMap *)f.scratch->map_nf.p;
+            j.box = box_nf;
         }
         const int variant =
             ((nf * 16 + p->rows) * 4 + f.prec) * 16 + (j.modes & (BF_DMAS | BF_CF | BF_PDAS));
@@ -566,8 +634,28 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
             hl.demod.push_back(d);
             continue;
         }
-        ig[f.prec].push_back(IngestJob{f.rf, f.pairs, f.na * f.h->g.ne, f.ns, f.plan->nsp,
-                                       f.stage != BF_OUT_RF ? f.maxbits : nullptr});
+    }
+    for (size_t fi = 0; fi < frames.size(); ++fi) {
+        const FramePrep &f = frames[fi];
+        if (f.prec == kPrecIQ || member[fi])
+            continue;  // IQ frames demodulate; members of a job come with its lead
+        IngestJob ij{};
+        ij.rf = f.rf;
+        ij.pairs = f.pairs;
+        ij.rows = f.na * f.h->g.ne;
+        ij.ns = f.ns;
+        ij.nsp = f.plan->nsp;
+        ij.maxbits = f.stage != BF_OUT_RF ? f.maxbits : nullptr;
+        ij.nf = 1 + (int)partners[fi].size();
+        if (ij.nf > 1) {  // the whole job, interleaved into the lead's pairs
+            for (size_t q = 0; q < partners[fi].size(); ++q) {
+                const FramePrep &g = frames[partners[fi][q]];
+                ij.rf_more[q] = g.rf;
+                ij.maxbits_more[q] = g.stage != BF_OUT_RF ? g.maxbits : nullptr;
+            }
+        }
+        ij.chunks = (ij.nf * ((ij.nsp + 7) / 8) + 255) / 256;
+        ig[f.prec].push_back(ij);
     }
     for (auto &kv : ig) {
         HostLaunch::IGroup g;
@@ -577,8 +665,8 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
         g.prefix_first = (int)hl.ingest_prefix.size();
         int acc = 0;
         for (const IngestJob &j : kv.second) {
-            hl.ingest_prefix.push_back(acc);
-            acc += j.rows;
+            hl.ingest_prefix.push_back(acc);  // first CTA of the job
+            acc += j.rows * j.chunks;
             hl.ingest.push_back(j);
         }
         g.rows = acc;
@@ -687,17 +775,27 @@ int DeviceLaunch::upload(const HostLaunch &hl, cudaStream_t st, bool async)
 // kernel reads them).
 int upload_maps(std::vector<FramePrep> &frames, cudaStream_t st, bool async)
 {
-    for (FramePrep &f : frames) {
-        if (!f.map_dirty)
-            continue;
-        cudaError_t e = async ? cudaMemcpyAsync(f.map_dev, &f.scratch->map_host, sizeof(CUtensorMap),
+    auto copy = [&](void *dst, const CUtensorMap *src) -> int {
+        cudaError_t e = async ? cudaMemcpyAsync(dst, src, sizeof(CUtensorMap),
                                                 cudaMemcpyHostToDevice, st)
-                              : cudaMemcpy(f.map_dev, &f.scratch->map_host, sizeof(CUtensorMap),
-                                           cudaMemcpyHostToDevice);
-        if (e != cudaSuccess)
-            return cuda_fail(e, "cudaMemcpy (tensor map)");
-        f.scratch->map_dirty = false;
-        f.map_dirty = false;
+                              : cudaMemcpy(dst, src, sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+        return e == cudaSuccess ? BF_OK : cuda_fail(e, "cudaMemcpy (tensor map)");
+    };
+    for (FramePrep &f : frames) {
+        FrameScratch &S = *f.scratch;
+        if (f.map_dirty) {
+            int rc = copy(f.map_dev, &S.map_host);
+            if (rc)
+                return rc;
+            S.map_dirty = false;
+            f.map_dirty = false;
+        }
+        if (S.mapnf_dirty) {  // the frame leads a multi-frame job
+            int rc = copy(S.map_nf.p, &S.map_nf_host);
+            if (rc)
+                return rc;
+            S.mapnf_dirty = false;
+        }
     }
     return BF_OK;
 }
@@ -1305,7 +1403,7 @@ BF_API int bf_autotune(bf_handle *h, int32_t n_samples, const double *angles_rad
         for (int i = 0; i < frames && !prc; ++i)
             prc = prepare_frame(h, (const int16_t *)rf.p, n_samples, angles_rad, n_angles, fl,
                                 (float *)out.p + (size_t)i * (out_bytes / sizeof(float)),
-                                scratch[i], fr[i], c);
+                                scratch[i], fr[i], c, kMaxFramesPerJob);
         if (prc)
             continue;  // this configuration does not fit the workload
         HostLaunch hl;
@@ -1384,7 +1482,8 @@ BF_API int bf_batch_create(const bf_frame *frames, int32_t n, bf_batch **out)
         if (!is_device_pointer(f.rf_dev) || !is_device_pointer(f.out_dev))
             return fail(BF_EINVAL, "frame %d: batches need device pointers", i);
         int rc = prepare_frame(f.h, f.rf_dev, f.n_samples, f.angles_rad, f.n_angles,
-                               f.mode_and_flags, f.out_dev, b->scratch[i], b->frames[i]);
+                               f.mode_and_flags, f.out_dev, b->scratch[i], b->frames[i], -1,
+                               kMaxFramesPerJob);
         if (rc)
             return fail(rc, "frame %d: %s", i, g_err.c_str());
     }

@@ -379,7 +379,10 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
     const int prec = frame_prec(flags);
     Plan *plan = nullptr;
     rc = handle_plan(h, ns, angles, na, flags, &plan);
-    size_t need = rf_bytes + out_bytes + (size_t)na * h->g.ne * (plan ? plan->nsp : 0) * pair_bytes(prec);
+    // staged pairs: room for the frames of a multi-frame job this frame may lead
+    const int cap = plan ? job_frames_cap(plan, flags, kMaxFramesPerJob) : 1;
+    size_t need = rf_bytes + out_bytes +
+                  (size_t)cap * na * h->g.ne * (plan ? plan->nsp : 0) * pair_bytes(prec);
     if ((flags & BF_OUT_MASK) != BF_OUT_RF)
         need += out_bytes * ((flags & BF_OUT_MASK) == BF_OUT_LOGDB ? 2 : 1);
     auto give_back = [&](int code) {
@@ -421,7 +424,7 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
         rc = fail(BF_ECUDA, "cudaEventCreate");
     if (!rc)
         rc = prepare_frame(h, (const int16_t *)s.rf.p, ns, angles, na, flags, (float *)s.out.p,
-                           s.scratch, req->fp);
+                           s.scratch, req->fp, -1, kMaxFramesPerJob);
     if (rc) {
         std::lock_guard<std::mutex> lk(mu_);
         const size_t grow = need > before ? need - before : 0;

@@ -91,6 +91,13 @@ struct FrameScratch {
     void *map_base = nullptr;
     int map_rows = 0, map_nsp = 0, map_box = 0, map_prec = -1;
     bool map_dirty = false;
+    // as the lead of a multi-frame job: pairs holds the job's frames interleaved
+    // ([row][pair][frame]) and map_nf describes that layout
+    DevMem map_nf;
+    CUtensorMap map_nf_host{};
+    void *mapnf_base = nullptr;
+    int mapnf_rows = 0, mapnf_nsp = 0, mapnf_box = 0, mapnf_prec = -1, mapnf_nf = 0;
+    bool mapnf_dirty = false;
 };
 
 struct FramePrep {
@@ -109,6 +116,7 @@ struct FramePrep {
     CUtensorMap map_host{};
     bool map_dirty = false;
     FrameScratch *scratch = nullptr;
+    int nf_cap = 1;  // frames of a job this frame may lead (its pairs buffer holds that many)
 };
 
 struct HostLaunch {
@@ -117,7 +125,7 @@ struct HostLaunch {
         size_t smem;
     };
     struct IGroup {  // one ingest launch
-        int prec, first, count, prefix_first, rows;
+        int prec, first, count, prefix_first, rows;  // rows: the launch's CTAs
     };
     std::vector<BfJob> jobs;
     std::vector<int> tile_prefix;
@@ -218,8 +226,15 @@ int check_frame_args(bf_handle *h, int ns, const double *angles, int na, uint32_
 size_t frame_out_bytes(const bf_handle *h, uint32_t flags);
 // Storage code of a frame's staged records (kPrecIQ for the IQ combiners).
 int frame_prec(uint32_t flags);
+// nf_cap: frames of one plan a later build_launch may put in one job with
+// this frame (1: alone, as a single bf_beamform call); the frame's scratch
+// is sized for the multi-frame jobs its plan and combiners allow up to that.
 int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *angles, int na,
-                  uint32_t flags, float *out_dev, FrameScratch &s, FramePrep &fp, int cfg = -1);
+                  uint32_t flags, float *out_dev, FrameScratch &s, FramePrep &fp, int cfg = -1,
+                  int nf_cap = 1);
+// Frames (at most cap) of one plan that can share a beamforming job with a
+// frame of these flags (1: DAS / DMAS of RF records only share).
+int job_frames_cap(const Plan *p, uint32_t flags, int cap);
 void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl);
 int upload_maps(std::vector<FramePrep> &frames, cudaStream_t st, bool async);
 // marks (optional, 4 events): recorded before the ingest, before and after the

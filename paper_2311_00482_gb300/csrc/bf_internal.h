@@ -64,9 +64,10 @@ struct BfJob {
     const CUtensorMap *valid_map;  // int2 [na * ne][nxp]: first / last counted row, (-1, -1) if none
     const CUtensorMap *dx2_map;    // float [ne][nxp]: max((kappa * (x_p - x_i))^2, 1e-30)
     float *y;             // [nmodes][nx][nz] beamformed output
-    // further frames of the same plan sharing every delay (multi-frame
-    // launches; null otherwise): their staged pairs and their outputs
-    const CUtensorMap *rf_more[kMaxFramesPerJob - 1];
+    // further frames of the same plan sharing every delay (multi-frame jobs;
+    // null otherwise): their outputs.  rf_map then covers all the job's
+    // frames, interleaved by frame ([row][pair][frame]), and box counts pairs
+    // per frame of one copy.
     float *y_more[kMaxFramesPerJob - 1];
     int nx, nz, na, ne;
     int wmax;             // window length (pairs) staged per channel and tile
@@ -103,9 +104,15 @@ struct PlanJob {
 // One frame's int16 records to staged sample pairs.
 struct IngestJob {
     const int16_t *rf;    // [rows][ns]
-    void *pairs;          // [rows][nsp]
+    void *pairs;          // [rows][nsp], or [rows][nsp][nf] for nf > 1 (frames interleaved)
     int rows, ns, nsp;
     unsigned *maxbits;    // the frame's 4 image maxima, zeroed by the job's first CTA (or null)
+    // the other frames of a multi-frame beamforming job (nf > 1): their records
+    // and maxima; pair j of frame f lands at [row][j][f]
+    int nf;
+    int chunks;           // CTAs per record row: nf * nsp / 8 threads of 256 per CTA
+    const int16_t *rf_more[kMaxFramesPerJob - 1];
+    unsigned *maxbits_more[kMaxFramesPerJob - 1];
 };
 
 // One frame's int16 records to complex analytic-signal pairs for IQ
@@ -177,8 +184,9 @@ cudaError_t kernel_setup(const void *k, size_t smem, int threads, bool max_carve
 // (all its jobs must share them, the precision and the rows per thread);
 // BF_PDAS adds the p-th-root combiner.
 cudaError_t launch_plan(const PlanJob &job, int *err_dev, cudaStream_t stream);
-cudaError_t launch_ingest(const IngestJob *jobs_dev, const int *row_prefix_dev, int njobs,
-                          int total_rows, int prec, cudaStream_t stream);
+// total_blocks: the jobs' rows x chunks (blk_prefix_dev: each job's first CTA).
+cudaError_t launch_ingest(const IngestJob *jobs_dev, const int *blk_prefix_dev, int njobs,
+                          int total_blocks, int prec, cudaStream_t stream);
 cudaError_t launch_demod(const DemodJob *jobs_dev, const int *row_prefix_dev, int njobs,
                          int total_rows, int max_ns, cudaStream_t stream);
 size_t demod_smem_bytes(int ns);

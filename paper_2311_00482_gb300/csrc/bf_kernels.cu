@@ -231,49 +231,91 @@ __global__ void __launch_bounds__(128) plan_kernel(const PlanJob J, int *__restr
 
 // ---------------------------------------------------------------- ingest --
 
+// Pairs j0 .. j0 + 7 of one record row: mid point and difference of samples
+// k = j - kPadL and k + 1 (zero outside the record), FP32 or scaled by 2^-15 to
+// FP16 / BF16 (two 16-bit halves: sample k low, k + 1 high).
+template <int PREC>
+__device__ __forceinline__ void row_pairs(const int16_t *__restrict__ u, int ns, int j0, float2 *f,
+                                          unsigned *h)
+{
+    int s[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const int k = j0 - kPadL + q;
+        s[q] = (k >= 0 && k < ns) ? (int)__ldg(u + k) : 0;
+    }
+    if (PREC == kPrecF32) {
+        // v = mid + (alpha - 1/2) * diff (exact for int16)
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            f[q] = make_float2(0.5f * (float)(s[q] + s[q + 1]), (float)(s[q + 1] - s[q]));
+    } else {
+        const float sc = 1.0f / 32768.0f;
+        unsigned b[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            if (PREC == kPrecF16)
+                b[q] = __half_as_ushort(__float2half_rn((float)s[q] * sc));
+            else
+                b[q] = __bfloat16_as_ushort(__float2bfloat16_rn((float)s[q] * sc));
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            h[q] = b[q] | (b[q + 1] << 16);
+    }
+}
+
+// Record rows to sample pairs.  A job's CTAs take its rows in order, `chunks`
+// CTAs per row; thread g of a row handles pairs 8 (g / nf) .. + 7 of frame
+// g % nf.  nf = 1 writes [row][nsp]; a multi-frame job (nf = 2, 4) writes its
+// frames interleaved, pair j of frame f at [row][j][f], so that the frame
+// lanes of a warp fill adjacent slots.
 template <int PREC>
 __global__ void __launch_bounds__(256) ingest_kernel(const IngestJob *__restrict__ jobs,
-                                                     const int *__restrict__ row_prefix, int njobs)
+                                                     const int *__restrict__ blk_prefix, int njobs)
 {
-    const int jb = find_job(row_prefix, njobs, blockIdx.x);
+    const int jb = find_job(blk_prefix, njobs, blockIdx.x);
     const IngestJob J = jobs[jb];
-    const int row = blockIdx.x - __ldg(row_prefix + jb);
-    if (row == 0 && J.maxbits && threadIdx.x < 4)  // before any later kernel takes a maximum
-        J.maxbits[threadIdx.x] = 0u;
-    const int16_t *__restrict__ u = J.rf + (size_t)row * J.ns;
-    const int ns = J.ns;
-    auto sample = [&](int k) -> int { return (k >= 0 && k < ns) ? (int)__ldg(u + k) : 0; };
-    for (int j0 = threadIdx.x * 8; j0 < J.nsp; j0 += blockDim.x * 8) {
-        int s[9];
+    const int local = blockIdx.x - __ldg(blk_prefix + jb);
+    const int row = local / J.chunks, chunk = local - row * J.chunks;
+    if (row == 0 && chunk == 0 && threadIdx.x < 4) {  // before any later kernel takes a maximum
+        if (J.maxbits)
+            J.maxbits[threadIdx.x] = 0u;
+        for (int f = 1; f < J.nf; ++f)
+            if (J.maxbits_more[f - 1])
+                J.maxbits_more[f - 1][threadIdx.x] = 0u;
+    }
+    const int nf = J.nf;  // 1, 2 or 4
+    const int g = chunk * blockDim.x + threadIdx.x;
+    const int f = g & (nf - 1), j0 = (g / nf) * 8;
+    if (j0 >= J.nsp)
+        return;
+    const int16_t *__restrict__ u = (f == 0 ? J.rf : J.rf_more[f - 1]) + (size_t)row * J.ns;
+    float2 fp[8];
+    unsigned hp[8];
+    row_pairs<PREC>(u, J.ns, j0, fp, hp);
+    const size_t at = ((size_t)row * J.nsp + j0) * nf + f;  // slot of pair j0
+    if (PREC == kPrecF32) {
+        float2 *o = reinterpret_cast<float2 *>(J.pairs) + at;
+        if (nf == 1) {  // 16-byte stores of two pairs
 #pragma unroll
-        for (int q = 0; q < 9; ++q)
-            s[q] = sample(j0 - kPadL + q);
-        if (PREC == kPrecF32) {
-            // mid point and difference: v = mid + (alpha - 1/2) * diff (exact for int16)
-            float4 *o = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(J.pairs) +
-                                                   (size_t)row * J.nsp + j0);
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                o[q] = make_float4(0.5f * (float)(s[2 * q] + s[2 * q + 1]),
-                                   (float)(s[2 * q + 1] - s[2 * q]),
-                                   0.5f * (float)(s[2 * q + 1] + s[2 * q + 2]),
-                                   (float)(s[2 * q + 2] - s[2 * q + 1]));
+            for (int q = 0; q < 8; q += 2)
+                reinterpret_cast<float4 *>(o)[q / 2] =
+                    make_float4(fp[q].x, fp[q].y, fp[q + 1].x, fp[q + 1].y);
         } else {
-            const float sc = 1.0f / 32768.0f;
-            unsigned h[9];
 #pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                if (PREC == kPrecF16)
-                    h[q] = __half_as_ushort(__float2half_rn((float)s[q] * sc));
-                else
-                    h[q] = __bfloat16_as_ushort(__float2bfloat16_rn((float)s[q] * sc));
-            }
-            uint4 *o = reinterpret_cast<uint4 *>(reinterpret_cast<unsigned *>(J.pairs) +
-                                                 (size_t)row * J.nsp + j0);
-            o[0] = make_uint4(h[0] | (h[1] << 16), h[1] | (h[2] << 16), h[2] | (h[3] << 16),
-                              h[3] | (h[4] << 16));
-            o[1] = make_uint4(h[4] | (h[5] << 16), h[5] | (h[6] << 16), h[6] | (h[7] << 16),
-                              h[7] | (h[8] << 16));
+            for (int q = 0; q < 8; ++q)
+                o[(size_t)q * nf] = fp[q];
+        }
+    } else {
+        unsigned *o = reinterpret_cast<unsigned *>(J.pairs) + at;
+        if (nf == 1) {
+            reinterpret_cast<uint4 *>(o)[0] = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+            reinterpret_cast<uint4 *>(o)[1] = make_uint4(hp[4], hp[5], hp[6], hp[7]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                o[(size_t)q * nf] = hp[q];
         }
     }
 }
@@ -385,6 +427,15 @@ struct PairIO<kPrecBF16> {
 };
 
 // Loads through 32-bit shared-window addresses (the consumer loop's tables).
+__device__ __forceinline__ float4 lds_f32x4(uint32_t addr)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr));
+    return v;
+}
+
 __device__ __forceinline__ int2 lds_int2(uint32_t addr)
 {
     int2 v;
@@ -565,9 +616,48 @@ __device__ __forceinline__ void accumulate(uint32_t win, int wmax, int w0, float
     }
 }
 
+// The NF frames' staged pairs at one window index of a multi-frame job
+// (interleaved by frame, [pair][frame]): v[f] = the frame's sample at offset
+// al, read with 16-byte loads (two FP32 pairs, four FP16 / BF16 pairs each).
+template <int PREC, int NF>
+__device__ __forceinline__ void interp_frames(uint32_t a, float al, float *v)
+{
+    if constexpr (PREC == kPrecF32) {
+#pragma unroll
+        for (int f = 0; f < NF; f += 2) {
+            const float4 q = lds_f32x4(a + (uint32_t)f * 8u);
+            v[f] = fmaf(al, q.y, q.x);
+            v[f + 1] = fmaf(al, q.w, q.z);
+        }
+    } else {
+        unsigned w[NF];
+        if constexpr (NF == 4) {
+            asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+                         : "r"(a));
+        } else {
+            asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(w[0]), "=r"(w[1]) : "r"(a));
+        }
+        const float t = al + 0.5f;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            float lo, hi;
+            if constexpr (PREC == kPrecF16) {
+                const float2 h = __half22float2(*reinterpret_cast<const __half2 *>(&w[f]));
+                lo = h.x;
+                hi = h.y;
+            } else {
+                lo = __uint_as_float(w[f] << 16);
+                hi = __uint_as_float(w[f] & 0xffff0000u);
+            }
+            v[f] = fmaf(t, hi - lo, lo);
+        }
+    }
+}
+
 // One channel into the ROWS pixels of this thread for NF frames of one plan:
-// the delay of each pixel is formed once and read from every frame's window
-// (frame f's window starts f * wmax pairs after the first).
+// the delay of each pixel is formed once and read from every frame's pairs
+// (interleaved by frame in the window).
 template <int PREC, bool DMAS, int ROWS, int NF, bool CHECK>
 __device__ __forceinline__ void accumulate_fn(uint32_t win, int wmax, int w0, float d2, int2 vr,
                                               int r_first, const float *Z, const float *fp,
@@ -575,7 +665,6 @@ __device__ __forceinline__ void accumulate_fn(uint32_t win, int wmax, int w0, fl
                                               float (&T1)[NF][ROWS], float (&T2)[NF][ROWS])
 {
     constexpr int PB = PairIO<PREC>::kBytes;
-    const uint32_t fstride = (uint32_t)(wmax * PB);
     const unsigned span = (unsigned)(vr.y - vr.x);
     const f32x2_t D2 = pk2(d2, d2);
 #pragma unroll
@@ -587,11 +676,8 @@ __device__ __forceinline__ void accumulate_fn(uint32_t win, int wmax, int w0, fl
             const int jj = j + h;
             const unsigned idx =
                 min((unsigned)(__float_as_int(m[h]) + Kc[jj] - w0), (unsigned)(wmax - 1));
-            const uint32_t a = win + idx * PB;
             float v[NF];
-#pragma unroll
-            for (int f = 0; f < NF; ++f)
-                v[f] = PairIO<PREC>::interp(a + (uint32_t)f * fstride, al[h]);
+            interp_frames<PREC, NF>(win + idx * (NF * PB), al[h], v);
             if (!CHECK || (unsigned)(r_first + jj - vr.x) <= span) {
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
@@ -645,15 +731,6 @@ __device__ __forceinline__ void accumulate2(uint32_t win0, int w00, float d20, u
                 P1[jj] += pdas_root(v0, inv_p, square) + pdas_root(v1, inv_p, square);
         }
     }
-}
-
-__device__ __forceinline__ float4 lds_f32x4(uint32_t addr)
-{
-    float4 v;
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "r"(addr));
-    return v;
 }
 
 // One channel of IQ beamforming into the ROWS pixels of this thread.  The
@@ -820,10 +897,6 @@ __global__ void __launch_bounds__(beamform_threads<NF>(),
             const int *__restrict__ wtab = J->wtab;
             const int *__restrict__ btab = J->btab;
             const CUtensorMap *rf_map = J->rf_map;
-            const CUtensorMap *rf_more[kMaxFramesPerJob - 1] = {};
-#pragma unroll
-            for (int f = 1; f < NF; ++f)
-                rf_more[f - 1] = J->rf_more[f - 1];
             const CUtensorMap *valid_map = J->valid_map;
             const CUtensorMap *dx2_map = J->dx2_map;
             const int box = J->box;
@@ -930,13 +1003,11 @@ __global__ void __launch_bounds__(beamform_threads<NF>(),
                     unsigned char *dst =
                         base + (size_t)G * kTileCols * 12 + (size_t)lane * NF * wmax * PB;
                     const int row = a * ne + i0 + lane;
+                    // multi-frame jobs: the frames' pairs interleaved ([pair][frame]),
+                    // box pairs of every frame per copy
                     for (int off = 0; off < wmax; off += box)
-                        tma_2d(dst + (size_t)off * PB, rf_map, (w0 + off) * XS, row, &sh.full[st]);
-#pragma unroll
-                    for (int f = 1; f < NF; ++f)  // the other frames' windows after the first
-                        for (int off = 0; off < wmax; off += box)
-                            tma_2d(dst + (size_t)(f * wmax + off) * PB, rf_more[f - 1],
-                                   (w0 + off) * XS, row, &sh.full[st]);
+                        tma_2d(dst + (size_t)off * NF * PB, rf_map, (w0 + off) * NF * XS, row,
+                               &sh.full[st]);
                 }
                 wf = wf_next;
                 tb = tb_next;
@@ -1805,17 +1876,17 @@ cudaError_t launch_plan(const PlanJob &job, int *err_dev, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-cudaError_t launch_ingest(const IngestJob *jobs_dev, const int *row_prefix_dev, int njobs,
-                          int total_rows, int prec, cudaStream_t stream)
+cudaError_t launch_ingest(const IngestJob *jobs_dev, const int *blk_prefix_dev, int njobs,
+                          int total_blocks, int prec, cudaStream_t stream)
 {
-    if (njobs <= 0 || total_rows <= 0)
+    if (njobs <= 0 || total_blocks <= 0)
         return cudaSuccess;
     if (prec == kPrecF32)
-        ingest_kernel<kPrecF32><<<total_rows, 256, 0, stream>>>(jobs_dev, row_prefix_dev, njobs);
+        ingest_kernel<kPrecF32><<<total_blocks, 256, 0, stream>>>(jobs_dev, blk_prefix_dev, njobs);
     else if (prec == kPrecF16)
-        ingest_kernel<kPrecF16><<<total_rows, 256, 0, stream>>>(jobs_dev, row_prefix_dev, njobs);
+        ingest_kernel<kPrecF16><<<total_blocks, 256, 0, stream>>>(jobs_dev, blk_prefix_dev, njobs);
     else
-        ingest_kernel<kPrecBF16><<<total_rows, 256, 0, stream>>>(jobs_dev, row_prefix_dev, njobs);
+        ingest_kernel<kPrecBF16><<<total_blocks, 256, 0, stream>>>(jobs_dev, blk_prefix_dev, njobs);
     return cudaGetLastError();
 }
 
