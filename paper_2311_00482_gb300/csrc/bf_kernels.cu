@@ -1412,6 +1412,14 @@ __device__ __forceinline__ float spectral_weight(int k, int L, int band, int kb_
     return h;
 }
 
+// Envelope transform buffers: plain, or in the swz layout.  Measured on the
+// 512 x 512 workload: the swizzle removes the strided passes' bank conflicts
+// (shared wavefronts 7.9 M -> 3.2 M per 8 frames) but its index arithmetic
+// adds half again the instructions, and the kernel ends no faster; the
+// per-pass twiddle table alone takes the envelope + log stages from 0.285 to
+// 0.260 ms per 64 frames.
+constexpr bool kEnvSwizzle = false;
+
 // Analytic-signal envelope of an image's columns.  The one-sided spectrum
 // X * H (H = 1 at 0 and L/2, 2 between, 0 for negative frequencies), times
 // the band-pass B for the DMAS image, has as inverse transform r + i h: r is
@@ -1438,9 +1446,14 @@ __global__ void __launch_bounds__(256) envelope_kernel(const EnvJob *__restrict_
         const int c0 = (blockIdx.x - __ldg(blk_prefix + jb)) * J.cols_per_block;
         float2 *Zb = sbuf, *Pb = sbuf + (size_t)C * m, *Qb = sbuf + (size_t)2 * C * m;
         float2 *tw = sbuf + (size_t)3 * C * m;
+        float2 *ptw = tw + m;  // per-pass twiddles of the radix-8 passes
         for (int k = threadIdx.x; k < m; k += blockDim.x)
             tw[k] = __ldg(J.tw + k);
-        // columns in: four depths per thread and 16-byte accesses (m >= 4: nz = m)
+        __syncthreads();
+        fill_pass_twiddles(ptw, tw, lgm);
+        // Buffers in the swizzled layout (element t at swz(t)): columns in, four
+        // depths per thread with 16-byte global loads (m >= 4: nz = m)
+        auto at = [](int t) { return swz<kEnvSwizzle>(t); };
         const int vec = J.vec4 ? 4 : 1;
         for (int t = threadIdx.x * vec; t < C * m; t += blockDim.x * vec) {
             const int c = t >> lgm, n = t & (m - 1);
@@ -1449,56 +1462,59 @@ __global__ void __launch_bounds__(256) envelope_kernel(const EnvJob *__restrict_
                 const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
                 const float4 a = ca < J.nx ? __ldg(reinterpret_cast<const float4 *>(J.y + (size_t)ca * nz + n)) : z4;
                 const float4 b = cb < J.nx ? __ldg(reinterpret_cast<const float4 *>(J.y + (size_t)cb * nz + n)) : z4;
-                float4 *z = reinterpret_cast<float4 *>(Zb + t);
-                z[0] = make_float4(a.x, b.x, a.y, b.y);
-                z[1] = make_float4(a.z, b.z, a.w, b.w);
+                Zb[at(t)] = make_float2(a.x, b.x);
+                Zb[at(t + 1)] = make_float2(a.y, b.y);
+                Zb[at(t + 2)] = make_float2(a.z, b.z);
+                Zb[at(t + 3)] = make_float2(a.w, b.w);
             } else {
                 const float ya = ca < J.nx ? __ldg(J.y + (size_t)ca * nz + n) : 0.f;
                 const float yb = cb < J.nx ? __ldg(J.y + (size_t)cb * nz + n) : 0.f;
-                Zb[t] = make_float2(ya, yb);
+                Zb[at(t)] = make_float2(ya, yb);
             }
         }
         __syncthreads();
-        float2 *S = fft_r8(Zb, Pb, m, lgm, C, tw, false);  // spectrum of a + i b
-        float2 *F1 = S == Zb ? Pb : Zb;                    // free buffer
+        float2 *S = fft_r8<kEnvSwizzle>(Zb, Pb, m, lgm, C, tw, false, ptw);  // spectrum of a + i b
+        float2 *F1 = S == Zb ? Pb : Zb;                                 // free buffer
         const float inv = 1.f / (float)m;
         if (!J.band) {
             for (int t = threadIdx.x; t < C * m; t += blockDim.x) {
                 const int k = t & (m - 1);
                 const float sg = (k == 0 || 2 * k == m) ? 0.f : (2 * k < m ? 1.f : -1.f);
-                F1[t] = make_float2(S[t].y * sg, -S[t].x * sg);  // -i sgn(k) S
+                const float2 sv = S[at(t)];
+                F1[at(t)] = make_float2(sv.y * sg, -sv.x * sg);  // -i sgn(k) S
             }
             __syncthreads();
-            const float2 *Hh = fft_r8(F1, S, m, lgm, C, tw, true);
+            const float2 *Hh = fft_r8<kEnvSwizzle>(F1, S, m, lgm, C, tw, true, ptw);
             for (int t = threadIdx.x * vec; t < C * m; t += blockDim.x * vec) {
                 const int c = t >> lgm, n = t & (m - 1);
                 const int ca = c0 + 2 * c, cb = ca + 1;
                 if (vec == 4) {
-                    const float4 h01 = *reinterpret_cast<const float4 *>(Hh + t);
-                    const float4 h23 = *reinterpret_cast<const float4 *>(Hh + t + 2);
+                    const float2 h0 = Hh[at(t)], h1 = Hh[at(t + 1)], h2 = Hh[at(t + 2)],
+                                 h3 = Hh[at(t + 3)];
                     if (ca < J.nx) {
                         const float4 a = __ldg(reinterpret_cast<const float4 *>(J.y + (size_t)ca * nz + n));
-                        const float4 e = make_float4(hypotf(a.x, h01.x * inv), hypotf(a.y, h01.z * inv),
-                                                     hypotf(a.z, h23.x * inv), hypotf(a.w, h23.z * inv));
+                        const float4 e = make_float4(hypotf(a.x, h0.x * inv), hypotf(a.y, h1.x * inv),
+                                                     hypotf(a.z, h2.x * inv), hypotf(a.w, h3.x * inv));
                         *reinterpret_cast<float4 *>(J.env + (size_t)ca * nz + n) = e;
                         lmax = fmaxf(lmax, fmaxf(fmaxf(e.x, e.y), fmaxf(e.z, e.w)));
                     }
                     if (cb < J.nx) {
                         const float4 b = __ldg(reinterpret_cast<const float4 *>(J.y + (size_t)cb * nz + n));
-                        const float4 e = make_float4(hypotf(b.x, h01.y * inv), hypotf(b.y, h01.w * inv),
-                                                     hypotf(b.z, h23.y * inv), hypotf(b.w, h23.w * inv));
+                        const float4 e = make_float4(hypotf(b.x, h0.y * inv), hypotf(b.y, h1.y * inv),
+                                                     hypotf(b.z, h2.y * inv), hypotf(b.w, h3.y * inv));
                         *reinterpret_cast<float4 *>(J.env + (size_t)cb * nz + n) = e;
                         lmax = fmaxf(lmax, fmaxf(fmaxf(e.x, e.y), fmaxf(e.z, e.w)));
                     }
                     continue;
                 }
+                const float2 h = Hh[at(t)];
                 if (ca < J.nx) {
-                    const float e = hypotf(__ldg(J.y + (size_t)ca * nz + n), Hh[t].x * inv);
+                    const float e = hypotf(__ldg(J.y + (size_t)ca * nz + n), h.x * inv);
                     J.env[(size_t)ca * nz + n] = e;
                     lmax = fmaxf(lmax, e);
                 }
                 if (cb < J.nx) {
-                    const float e = hypotf(__ldg(J.y + (size_t)cb * nz + n), Hh[t].y * inv);
+                    const float e = hypotf(__ldg(J.y + (size_t)cb * nz + n), h.y * inv);
                     J.env[(size_t)cb * nz + n] = e;
                     lmax = fmaxf(lmax, e);
                 }
@@ -1509,43 +1525,47 @@ __global__ void __launch_bounds__(256) envelope_kernel(const EnvJob *__restrict_
                 const int kk = 2 * k <= m ? k : m - k;  // |k|
                 const float bp = (kk >= J.kb_lo && kk <= J.kb_hi) ? 1.f : 0.f;
                 const float sg = (k == 0 || 2 * k == m) ? 0.f : (2 * k < m ? 1.f : -1.f);
-                const float2 r = make_float2(S[t].x * bp, S[t].y * bp);
-                S[t] = r;
-                Qb[t] = make_float2(r.y * sg, -r.x * sg);
+                const float2 sv = S[at(t)];
+                const float2 r = make_float2(sv.x * bp, sv.y * bp);
+                S[at(t)] = r;
+                Qb[at(t)] = make_float2(r.y * sg, -r.x * sg);
             }
             __syncthreads();
-            float2 *R = fft_r8(S, F1, m, lgm, C, tw, true);
+            float2 *R = fft_r8<kEnvSwizzle>(S, F1, m, lgm, C, tw, true, ptw);
             float2 *F2 = R == S ? F1 : S;
-            const float2 *Hh = fft_r8(Qb, F2, m, lgm, C, tw, true);
+            const float2 *Hh = fft_r8<kEnvSwizzle>(Qb, F2, m, lgm, C, tw, true, ptw);
             for (int t = threadIdx.x * vec; t < C * m; t += blockDim.x * vec) {
                 const int c = t >> lgm, n = t & (m - 1);
                 const int ca = c0 + 2 * c, cb = ca + 1;
                 if (vec == 4) {
-                    const float4 r01 = *reinterpret_cast<const float4 *>(R + t);
-                    const float4 r23 = *reinterpret_cast<const float4 *>(R + t + 2);
-                    const float4 h01 = *reinterpret_cast<const float4 *>(Hh + t);
-                    const float4 h23 = *reinterpret_cast<const float4 *>(Hh + t + 2);
+                    float2 rr[4], hh[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        rr[u] = R[at(t + u)];
+                        hh[u] = Hh[at(t + u)];
+                    }
                     if (ca < J.nx) {
-                        const float4 e = make_float4(hypotf(r01.x, h01.x) * inv, hypotf(r01.z, h01.z) * inv,
-                                                     hypotf(r23.x, h23.x) * inv, hypotf(r23.z, h23.z) * inv);
+                        const float4 e = make_float4(hypotf(rr[0].x, hh[0].x) * inv, hypotf(rr[1].x, hh[1].x) * inv,
+                                                     hypotf(rr[2].x, hh[2].x) * inv, hypotf(rr[3].x, hh[3].x) * inv);
                         *reinterpret_cast<float4 *>(J.env + (size_t)ca * nz + n) = e;
                         lmax = fmaxf(lmax, fmaxf(fmaxf(e.x, e.y), fmaxf(e.z, e.w)));
                     }
                     if (cb < J.nx) {
-                        const float4 e = make_float4(hypotf(r01.y, h01.y) * inv, hypotf(r01.w, h01.w) * inv,
-                                                     hypotf(r23.y, h23.y) * inv, hypotf(r23.w, h23.w) * inv);
+                        const float4 e = make_float4(hypotf(rr[0].y, hh[0].y) * inv, hypotf(rr[1].y, hh[1].y) * inv,
+                                                     hypotf(rr[2].y, hh[2].y) * inv, hypotf(rr[3].y, hh[3].y) * inv);
                         *reinterpret_cast<float4 *>(J.env + (size_t)cb * nz + n) = e;
                         lmax = fmaxf(lmax, fmaxf(fmaxf(e.x, e.y), fmaxf(e.z, e.w)));
                     }
                     continue;
                 }
+                const float2 rv = R[at(t)], hv = Hh[at(t)];
                 if (ca < J.nx) {
-                    const float e = hypotf(R[t].x, Hh[t].x) * inv;
+                    const float e = hypotf(rv.x, hv.x) * inv;
                     J.env[(size_t)ca * nz + n] = e;
                     lmax = fmaxf(lmax, e);
                 }
                 if (cb < J.nx) {
-                    const float e = hypotf(R[t].y, Hh[t].y) * inv;
+                    const float e = hypotf(rv.y, hv.y) * inv;
                     J.env[(size_t)cb * nz + n] = e;
                     lmax = fmaxf(lmax, e);
                 }
@@ -1866,7 +1886,11 @@ int envelope_cols_per_block(int fft_m) { return 2 * (fft_m >= 2048 ? 1 : 2048 / 
 size_t envelope_smem_bytes(int fft_m, int bluestein)
 {
     const int c = bluestein ? 1 : envelope_cols_per_block(fft_m) / 2;
-    return (3u * (size_t)c * fft_m + (size_t)fft_m) * sizeof(float2);
+    int lgm = 0;
+    while ((1 << lgm) < fft_m)
+        ++lgm;
+    const size_t passes = bluestein ? 0 : (size_t)pass_twiddle_count(lgm);
+    return (3u * (size_t)c * fft_m + (size_t)fft_m + passes) * sizeof(float2);
 }
 
 cudaError_t launch_plan(const PlanJob &job, int *err_dev, cudaStream_t stream)
