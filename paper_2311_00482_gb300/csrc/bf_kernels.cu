@@ -234,15 +234,29 @@ __global__ void __launch_bounds__(128) plan_kernel(const PlanJob J, int *__restr
 // Pairs j0 .. j0 + 7 of one record row: mid point and difference of samples
 // k = j - kPadL and k + 1 (zero outside the record), FP32 or scaled by 2^-15 to
 // FP16 / BF16 (two 16-bit halves: sample k low, k + 1 high).
+// vec: the row starts 16-byte aligned (samples j0 .. j0 + 7 in one 16-byte
+// load, j0 - 2 and j0 - 1 in one 4-byte load when all lie inside the record).
 template <int PREC>
-__device__ __forceinline__ void row_pairs(const int16_t *__restrict__ u, int ns, int j0, float2 *f,
-                                          unsigned *h)
+__device__ __forceinline__ void row_pairs(const int16_t *__restrict__ u, int ns, int j0, bool vec,
+                                          float2 *f, unsigned *h)
 {
+    static_assert(kPadL == 2, "the vector path loads two samples before j0");
     int s[9];
+    if (vec && j0 >= kPadL && j0 + 8 <= ns) {
+        const unsigned lo = __ldg(reinterpret_cast<const unsigned *>(u + j0 - kPadL));
+        const int4 hi = __ldg(reinterpret_cast<const int4 *>(u + j0));
+        const unsigned w[4] = {(unsigned)hi.x, (unsigned)hi.y, (unsigned)hi.z, (unsigned)hi.w};
+        s[0] = (int)(int16_t)(lo & 0xffffu);
+        s[1] = (int)(int16_t)(lo >> 16);
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        const int k = j0 - kPadL + q;
-        s[q] = (k >= 0 && k < ns) ? (int)__ldg(u + k) : 0;
+        for (int q = 0; q < 7; ++q)  // samples j0 .. j0 + 6 (little-endian halves)
+            s[2 + q] = (int)(int16_t)((w[q >> 1] >> (16 * (q & 1))) & 0xffffu);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const int k = j0 - kPadL + q;
+            s[q] = (k >= 0 && k < ns) ? (int)__ldg(u + k) : 0;
+        }
     }
     if (PREC == kPrecF32) {
         // v = mid + (alpha - 1/2) * diff (exact for int16)
@@ -290,10 +304,12 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestJob *__restrict
     const int f = g & (nf - 1), j0 = (g / nf) * 8;
     if (j0 >= J.nsp)
         return;
-    const int16_t *__restrict__ u = (f == 0 ? J.rf : J.rf_more[f - 1]) + (size_t)row * J.ns;
+    const int16_t *__restrict__ rf = f == 0 ? J.rf : J.rf_more[f - 1];
+    const int16_t *__restrict__ u = rf + (size_t)row * J.ns;
+    const bool vec = (J.ns & 7) == 0 && (reinterpret_cast<unsigned long long>(rf) & 15) == 0;
     float2 fp[8];
     unsigned hp[8];
-    row_pairs<PREC>(u, J.ns, j0, fp, hp);
+    row_pairs<PREC>(u, J.ns, j0, vec, fp, hp);
     const size_t at = ((size_t)row * J.nsp + j0) * nf + f;  // slot of pair j0
     if (PREC == kPrecF32) {
         float2 *o = reinterpret_cast<float2 *>(J.pairs) + at;
