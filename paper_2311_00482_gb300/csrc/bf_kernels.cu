@@ -6,16 +6,20 @@
 //   ingest_kernel    int16 channel records of a batch of frames -> staged
 //                    sample pairs (FP32 (mid, diff) pairs, or raw FP16 / BF16
 //                    pairs), one launch for the whole batch
-//   beamform_kernel  per CTA a tile of 32 columns (one per lane) x 8 row bands
-//                    (one per warp, `ROWS` contiguous rows per thread).  Per
-//                    angle and channel group the tensor memory accelerator
-//                    (cp.async.bulk.tensor) copies, into a double-buffered
-//                    shared-memory stage tracked by an mbarrier, the group's
-//                    window of every channel's record plus the tile's
+//   beamform_kernel  persistent CTAs walking the launch's (job, tile) list; a
+//                    tile is 32 columns (one per lane) x 8 row bands (one per
+//                    consumer warp, `ROWS` contiguous rows per thread).  Per
+//                    angle and channel group a producer warp has the tensor
+//                    memory accelerator (cp.async.bulk.tensor) copy, into a
+//                    3-stage shared-memory ring tracked by mbarriers, the
+//                    group's window of every channel's record plus the tile's
 //                    per-(channel, column) tables; delays are formed in
 //                    registers, samples interpolated linearly and combined
-//                    (DAS, signed-sqrt DMAS, coherence factor, pDAS), compounded over
-//                    angles (Eq. (1), Sec. II-B)
+//                    (DAS, signed-sqrt DMAS, coherence factor, pDAS), compounded
+//                    over angles (Eq. (1), Sec. II-B).  A job may carry 2 or 4
+//                    frames of one plan (their pairs interleaved by frame):
+//                    every delay serves all of them, and a storer warp writes
+//                    the staged tile images with bulk copies
 //   envelope_kernel  per image column the analytic signal along depth via a
 //                    shared-memory radix-8 Stockham FFT (Bluestein for other
 //                    lengths), one-sided mask and optional [f0, 3 f0]
@@ -503,7 +507,7 @@ __device__ __forceinline__ void bulk_wait_read()
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Bytes of one pipeline stage: tables (int2 rows + float dx^2) and windows.
-// (nf frames' windows per channel in two-frame launches)
+// (nf frames' windows per channel in multi-frame jobs)
 __host__ __device__ __forceinline__ int stage_bytes(int group, int wmax, int pb, int nf = 1)
 {
     return group * (kTileCols * 12 + nf * wmax * pb);

@@ -376,7 +376,7 @@ def test_submit_many_and_poll_many(torch):
         assert bf.bf_poll_many(h, tickets, outs, timeout_us=30_000_000) == bf.BF_OK
         for o, ref in zip(outs, solo):
             got = o if isinstance(o, np.ndarray) else o.cpu().numpy()
-            # frames of one plan may ride in a shared two-frame job (another summation
+            # frames of one plan may ride in a shared multi-frame job (another summation
             # order): 2e-3 dB bounds the rounding difference, 25x below the oracle bound
             np.testing.assert_allclose(got, ref, atol=2e-3)
         with pytest.raises(bf.BFError):  # released

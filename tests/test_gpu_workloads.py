@@ -180,7 +180,7 @@ def test_poisson_serving_trace_fp16(torch):
         for (a, r, f, h), t, ref in zip(reqs, tickets, solo):
             out = np.empty((1, a.nx, a.nz), np.float32)
             assert bf.bf_poll(h, t, out, timeout_us=30_000_000) == bf.BF_OK
-            # requests of one plan may share a two-frame job (another summation order)
+            # requests of one plan may share a multi-frame job (another summation order)
             np.testing.assert_allclose(out, ref, atol=2e-3)
     finally:
         for h in handles.values():
