@@ -70,8 +70,8 @@ def dist_info():
 # (profiles/beamform_kernel_cyst512_8frames.md: 8 frames per launch; the
 # traffic grows with the frames).  Valid only for the kernel source the
 # capture was taken on: any other source reports null.
-TRAFFIC_CAPTURE = {"sources_sha256": "ac9216d4749bb6271de8d2aeb8cb66d8fa8316005f92dabb9ea3d3466549377b",
-                   "frames": 8, "bytes": 4558848 + 512}
+TRAFFIC_CAPTURE = {"sources_sha256": "125130ff0af8738700236621f624fd8c76aa0b64c7f02bf06b7bf8652ae77458",
+                   "frames": 8, "bytes": 4684288 + 0}
 
 
 def beamform_traffic(frames):
