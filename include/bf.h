@@ -308,6 +308,17 @@ BF_API int bf_autotune(bf_handle *h, int32_t n_samples, const double *angles_rad
                        int32_t *rows_out, int32_t *stage_bytes_out, float *candidate_us,
                        int32_t n_candidates);
 
+/* Paper: no counterpart (safety of this implementation).
+ * Self-test of the device-side bounded waits every beamforming kernel uses:
+ * launches one warp that waits on a barrier phase nothing completes, for
+ * timeout_us microseconds (1 .. 1000000) of the device's global timer, on a
+ * private stream of the current device, and waits for it.  Returns
+ * BF_ETIMEDOUT when the wait ran out and the kernel reported it (the expected
+ * outcome: the path a CTA whose copies never land takes; the CUDA context
+ * stays usable), BF_EINVAL for a timeout out of range, BF_ECUDA on a CUDA
+ * error. */
+BF_API int bf_selftest_wait(int64_t timeout_us);
+
 /* Allocation-free envelope + log compression, for callers that cannot
  * allocate device memory while running (a real-time acquisition loop that
  * must not enter cudaMalloc, an application whose device memory belongs to

@@ -37,8 +37,8 @@ EXPORTED = ("bf_create", "bf_destroy", "bf_set_stream", "bf_set_pdas_order", "bf
             "bf_engine_configure", "bf_sync",
             "bf_batch_create", "bf_batch_launch", "bf_batch_status", "bf_batch_timing",
             "bf_batch_destroy",
-            "bf_host_tables", "bf_plan_info", "bf_autotune", "bf_logdb_static", "bf_last_error",
-            "bf_version")
+            "bf_host_tables", "bf_plan_info", "bf_autotune", "bf_logdb_static", "bf_selftest_wait",
+            "bf_last_error", "bf_version")
 
 
 class BFError(RuntimeError):
@@ -115,6 +115,7 @@ def load(path: str | None = None):
                          ctypes.POINTER(ctypes.c_float), i32], ctypes.c_int),
         "bf_logdb_static": ([vp, i32, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                              ctypes.c_double, i32, vp, vp], ctypes.c_int),
+        "bf_selftest_wait": ([i64], ctypes.c_int),
         "bf_last_error": ([], ctypes.c_char_p),
         "bf_version": ([], ctypes.c_int),
     }
@@ -253,6 +254,12 @@ def bf_autotune(h, n_samples, angles_rad, flags, frames=8):
                               ctypes.byref(rows), ctypes.byref(stage), cand, 8))
     return {"rows": rows.value, "stage_bytes": stage.value,
             "candidates_us": [round(float(c), 2) for c in cand if c != 0.0]}
+
+
+def bf_selftest_wait(timeout_us):
+    """Device-side bounded-wait self-test (see include/bf.h): raises BFError with
+    code BF_ETIMEDOUT when the wait ran out as designed."""
+    return _check(load().bf_selftest_wait(ctypes.c_int64(int(timeout_us))))
 
 
 def bf_logdb_static(y_dev, nx, nz, z0_m, z1_m, f0_hz, c_mps, bandpass, db_dev, stream=None):

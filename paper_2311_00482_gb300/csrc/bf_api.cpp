@@ -48,6 +48,23 @@ int cuda_fail(cudaError_t e, const char *what)
 
 // ------------------------------------------------------------- device mem --
 
+bool fault_injected(const char *kind)
+{
+    const char *e = std::getenv("BF_FAULT");
+    if (!e || !*e)
+        return false;
+    const size_t n = std::strlen(kind);
+    for (const char *p = e;;) {
+        const char *q = std::strchr(p, ',');
+        const size_t len = q ? (size_t)(q - p) : std::strlen(p);
+        if (len == n && std::strncmp(p, kind, n) == 0)
+            return true;
+        if (!q)
+            return false;
+        p = q + 1;
+    }
+}
+
 int DevMem::ensure(size_t n)
 {
     if (n <= bytes && p)
@@ -55,6 +72,8 @@ int DevMem::ensure(size_t n)
     release();
     if (n == 0)
         return BF_OK;
+    if (fault_injected("alloc"))
+        return fail(BF_ENOMEM, "injected allocation failure (BF_FAULT=alloc)");
     cudaError_t e = cudaMalloc(&p, n);
     if (e != cudaSuccess) {
         p = nullptr;

@@ -361,6 +361,8 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
     int rc = check_frame_args(h, ns, angles, na, flags);
     if (rc)
         return rc;
+    if (fault_injected("submit"))
+        return fail(BF_EAGAIN, "injected admission refusal (BF_FAULT=submit)");
     const size_t rf_bytes = (size_t)na * h->g.ne * ns * sizeof(int16_t);
     const size_t out_bytes = frame_out_bytes(h, flags);
     auto req = std::make_shared<Request>();
@@ -440,7 +442,10 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
     // pageable host data through the slot's pinned staging.
     cudaError_t e;
     const PtrKind kind = pointer_kind(rf);
-    if (kind != kPageable) {
+    const bool inject = fault_injected("copy");
+    if (inject) {
+        e = cudaErrorUnknown;  // stands for a failed copy; no CUDA call is made
+    } else if (kind != kPageable) {
         e = cudaMemcpyAsync(s.rf.p, rf, rf_bytes, cudaMemcpyDefault, copy_);
     } else if (!s.pin_in.ensure(rf_bytes)) {
         e = cudaErrorMemoryAllocation;
@@ -461,7 +466,8 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
         if (e != cudaSuccess) {
             free_.push_back(std::move(req->slot));
             live_ -= 1;
-            return cuda_fail(e, "copying the request's RF");
+            return inject ? fail(BF_ECUDA, "injected RF copy failure (BF_FAULT=copy)")
+                          : cuda_fail(e, "copying the request's RF");
         }
         req->ticket = next_ticket_++;
         pending_.push_back(req);

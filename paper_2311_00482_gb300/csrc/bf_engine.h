@@ -23,6 +23,13 @@ int fail(int code, const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);
 
 // Owning device allocation (freed on destruction).
+// Host-side fault injection for tests of the error paths: true when the
+// environment variable BF_FAULT, a comma-separated list, names `kind`.
+// Kinds: alloc (device allocations fail with BF_ENOMEM), submit (admission
+// refuses every request with BF_EAGAIN), copy (a request's RF copy fails
+// with BF_ECUDA).  Read on every use, so a test can switch it on and off.
+bool fault_injected(const char *kind);
+
 struct DevMem {
     void *p = nullptr;
     size_t bytes = 0;

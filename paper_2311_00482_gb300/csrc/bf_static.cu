@@ -144,10 +144,78 @@ int static_scratch(float **out)
     return BF_OK;
 }
 
+// Self-test of the device-side bounded waits: one warp waits on an mbarrier
+// phase that nothing completes (no thread arrives) until timeout_ns pass on the
+// global timer, then records the timeout in *err, as a beamforming CTA whose
+// copies never land does, and returns.
+__global__ void __launch_bounds__(32) wait_selftest_kernel(unsigned long long timeout_ns, int *err)
+{
+    __shared__ unsigned long long bar;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(1u) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    const unsigned long long deadline = t + timeout_ns;
+    for (;;) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(0u)
+            : "memory");
+        if (__all_sync(0xffffffffu, done != 0))
+            return;  // the phase completed (it cannot: nothing arrives)
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (__any_sync(0xffffffffu, t >= deadline)) {
+            if (threadIdx.x == 0)
+                atomicOr(err, 1);
+            return;
+        }
+    }
+}
+
 }  // namespace
 }  // namespace bfi
 
 using namespace bfi;
+
+extern "C" BF_API int bf_selftest_wait(int64_t timeout_us)
+{
+    if (timeout_us < 1 || timeout_us > 1000000)
+        return fail(BF_EINVAL, "timeout_us must be in [1, 1000000], got %lld", (long long)timeout_us);
+    int *err_dev = nullptr;
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaMalloc(&err_dev, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(err_dev, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        wait_selftest_kernel<<<1, 32, 0, st>>>((unsigned long long)timeout_us * 1000ull, err_dev);
+        e = cudaGetLastError();
+    }
+    int err_host = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&err_host, err_dev, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (st)
+        cudaStreamDestroy(st);
+    if (err_dev)
+        cudaFree(err_dev);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "bounded-wait self-test");
+    if (err_host & 1)
+        return fail(BF_ETIMEDOUT, "bounded-wait self-test: the wait ran out after %lld us (expected)",
+                    (long long)timeout_us);
+    return BF_OK;
+}
 
 extern "C" BF_API int bf_logdb_static(const float *y_dev, int32_t nx, int32_t nz, double z0_m,
                                       double z1_m, double f0_hz, double c_mps, int32_t bandpass,

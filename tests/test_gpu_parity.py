@@ -414,20 +414,27 @@ def test_frames_of_one_plan_share_delays_in_pairs(torch, prec):
         bf.bf_destroy(h)
 
 
-@pytest.mark.parametrize("prec", [bf.BF_PREC_FP32, bf.BF_PREC_BF16])
-def test_two_row_tiles_share_delays_in_fours(torch, monkeypatch, prec):
+# (precision, depth, output offset in floats): depth 92 with aligned images
+# takes the bulk-copy epilogue (ragged last tile), 90 the 8-byte row-pair
+# stores, 91 and images offset by one float the per-pixel stores
+@pytest.mark.parametrize("prec,nz,offset", [(bf.BF_PREC_FP32, 90, 0), (bf.BF_PREC_FP32, 92, 0),
+                                            (bf.BF_PREC_FP32, 91, 0), (bf.BF_PREC_FP32, 92, 1),
+                                            (bf.BF_PREC_BF16, 90, 0), (bf.BF_PREC_BF16, 92, 0)])
+def test_two_row_tiles_share_delays_in_fours(torch, monkeypatch, prec, nz, offset):
     """Seven frames of one plan on 16-row tiles: one four-frame job, one
     two-frame job and one frame alone; every frame matches the oracle and its
     single-frame result on the same tiles."""
     monkeypatch.setenv("BF_TILE_ROWS", "2")
-    acq = synth.SPECKLE_POINTS_128.with_(nx=70, nz=90, angles_deg=(-4.0, 4.0))
+    acq = synth.SPECKLE_POINTS_128.with_(nx=70, nz=nz, angles_deg=(-4.0, 4.0))
     flags = bf.BF_DAS | bf.BF_DMAS | prec
     rfs = [synth.speckle_points_frame(acq, seed=synth.BASE_SEED + 520 + k)[0] for k in range(7)]
     h = make_handle(acq)
     try:
         assert bf.bf_plan_info(h, acq.n_samples, acq.angles_rad, flags)["rows"] == 2
         rf_d = [torch.from_numpy(r).cuda() for r in rfs]
-        outs = [torch.full((2, acq.nx, acq.nz), float("nan"), device="cuda") for _ in rfs]
+        n = 2 * acq.nx * acq.nz
+        bufs = [torch.full((n + offset,), float("nan"), device="cuda") for _ in rfs]
+        outs = [b[offset:].view(2, acq.nx, acq.nz) for b in bufs]
         batch = bf.Batch([(h, rf_d[k], acq.n_samples, acq.angles_rad, flags, outs[k])
                           for k in range(7)])
         batch.launch()
