@@ -193,8 +193,11 @@ BF_API int bf_poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes,
 /* Paper: as bf_submit.  n frames of one geometry, sample count, angle set and
  * flags in one call: rf[k] (host or device) is frame k, tickets_out[k] its
  * ticket.  Every source has been copied when the call returns (one wait for
- * all the copies instead of one per frame).  *n_submitted (optional) receives
- * how many frames got tickets: on BF_EAGAIN the rest can be submitted later. */
+ * all the copies instead of one per frame).  The engine forms no batch from
+ * pending work while the call admits its frames (unless a full batch is
+ * pending), so the call's frames ride together.  *n_submitted (optional)
+ * receives how many frames got tickets: on BF_EAGAIN the rest can be
+ * submitted later. */
 BF_API int bf_submit_many(bf_handle *h, int32_t n, const int16_t *const *rf, int32_t n_samples,
                           const double *angles_rad, int32_t n_angles, uint32_t mode_and_flags,
                           uint64_t *tickets_out, int32_t *n_submitted);

@@ -308,6 +308,18 @@ public:
         }
         cv_work_.notify_one();
     }
+    // A multi-frame submission in progress: the scheduler forms no batch from
+    // what is pending (unless a full batch is) until it ends, so that the
+    // call's frames ride together instead of in fragments.
+    void hold(bool on)
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            holding_ += on ? 1 : -1;
+        }
+        if (!on)
+            cv_work_.notify_one();
+    }
     void configure(int max_batch, int max_inflight, size_t budget)
     {
         std::lock_guard<std::mutex> lk(mu_);
@@ -334,6 +346,7 @@ private:
     int live_ = 0;
     int max_batch_ = 64, max_inflight_ = 3, max_live_ = 512;
     bool paused_ = false;
+    int holding_ = 0;  // submit_many calls in progress
     cudaEvent_t epoch_ = nullptr;
     uint64_t next_ticket_ = 1;
     int next_batch_ = 0;
@@ -538,7 +551,10 @@ void Engine::loop()
         std::vector<std::shared_ptr<Request>> take;
         {
             std::unique_lock<std::mutex> lk(mu_);
-            cv_work_.wait(lk, [&] { return !pending_.empty() && !paused_; });
+            cv_work_.wait(lk, [&] {
+                return !pending_.empty() && !paused_ &&
+                       (holding_ == 0 || (int)pending_.size() >= max_batch_);
+            });
             while (!inflight_.empty() &&
                    cudaEventQuery(inflight_.front()->res->done) != cudaErrorNotReady)
                 inflight_.pop_front();
@@ -856,15 +872,24 @@ BF_API int bf_submit_many(bf_handle *h, int32_t n, const int16_t *const *rf, int
         *n_submitted = 0;
     cudaSetDevice(h->device);
     Engine *eng = engine_for(h->device);
+    struct Hold {  // the call's frames form their batches together
+        Engine *e;
+        explicit Hold(Engine *x) : e(x) { e->hold(true); }
+        ~Hold() { e->hold(false); }
+    };
     int rc = BF_OK, k = 0;
-    for (; k < n; ++k) {
-        if (!rf[k]) {
-            rc = fail(BF_EINVAL, "null record pointer %d", k);
-            break;
+    {
+        Hold hold(eng);  // released once every frame is admitted (copies may still run)
+        for (; k < n; ++k) {
+            if (!rf[k]) {
+                rc = fail(BF_EINVAL, "null record pointer %d", k);
+                break;
+            }
+            rc = eng->submit(h, rf[k], n_samples, angles_rad, n_angles, flags, tickets_out + k,
+                             false);
+            if (rc)
+                break;
         }
-        rc = eng->submit(h, rf[k], n_samples, angles_rad, n_angles, flags, tickets_out + k, false);
-        if (rc)
-            break;
     }
     if (n_submitted)
         *n_submitted = k;
