@@ -134,16 +134,31 @@ private:
 
 enum PtrKind { kPageable = 0, kPinned = 1, kDevice = 2 };
 
-PtrKind pointer_kind(const void *p)
+// CTAs per frame of the batched copy kernels (records in, images out).
+constexpr int kCopyBlocksIn = 2, kCopyBlocksOut = 1;
+
+// dev (optional): an address of the memory a kernel may use (device memory
+// itself, or the device-mapped address of pinned host memory), else null.
+PtrKind pointer_kind(const void *p, void **dev = nullptr)
 {
+    if (dev)
+        *dev = nullptr;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return kPageable;
     }
-    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+        if (dev && a.type == cudaMemoryTypeDevice)
+            *dev = const_cast<void *>(p);
         return kDevice;
-    return a.type == cudaMemoryTypeHost ? kPinned : kPageable;
+    }
+    if (a.type == cudaMemoryTypeHost) {
+        if (dev)
+            *dev = a.devicePointer;
+        return kPinned;
+    }
+    return kPageable;
 }
 
 // Page-locked host buffer that grows on demand (contents not kept).
@@ -286,8 +301,18 @@ public:
         worker_.detach();  // lives for the process
     }
 
+    // A request whose RF copy bf_submit_many batches into one kernel.
+    struct Deferred {
+        std::shared_ptr<Request> req;
+        CopySeg seg;
+    };
+    // defer (bf_submit_many): a device or pinned source is not copied here; the
+    // request gets its ticket but is queued by flush() once the batched copy is
+    // enqueued.  Other sources are copied (and queued) at once.
     int submit(bf_handle *h, const int16_t *rf, int ns, const double *angles, int na,
-               uint32_t flags, uint64_t *ticket, bool wait_copy = true);
+               uint32_t flags, uint64_t *ticket, bool wait_copy = true,
+               std::vector<Deferred> *defer = nullptr);
+    int flush(std::vector<Deferred> &defer);
     int poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes, int64_t timeout_us);
     int poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const *outs, size_t out_bytes,
                   int64_t timeout_us);
@@ -369,7 +394,7 @@ std::unique_ptr<Slot> Engine::take_slot()
 }
 
 int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles, int na,
-                   uint32_t flags, uint64_t *ticket, bool wait_copy)
+                   uint32_t flags, uint64_t *ticket, bool wait_copy, std::vector<Deferred> *defer)
 {
     int rc = check_frame_args(h, ns, angles, na, flags);
     if (rc)
@@ -454,8 +479,27 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
     // caller's buffer (waited for: the caller may reuse it on return),
     // pageable host data through the slot's pinned staging.
     cudaError_t e;
-    const PtrKind kind = pointer_kind(rf);
+    void *rf_dev = nullptr;
+    const PtrKind kind = pointer_kind(rf, &rf_dev);
     const bool inject = fault_injected("copy");
+    if (defer && !inject && rf_dev && copy_segment_ok(rf_dev, s.rf.p, rf_bytes)) {
+        // batched with the call's other frames: registered now, queued by flush()
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            const size_t grow = need > before ? need - before : 0;
+            used_ -= grow;
+            used_ -= before;
+            used_ += s.device_bytes();
+            req->ticket = next_ticket_++;
+        }
+        {
+            std::lock_guard<std::mutex> lk(h->mu);
+            h->tickets[req->ticket] = req;
+        }
+        defer->push_back(Deferred{req, CopySeg{rf_dev, s.rf.p, (unsigned long long)rf_bytes}});
+        *ticket = req->ticket;
+        return BF_OK;
+    }
     if (inject) {
         e = cudaErrorUnknown;  // stands for a failed copy; no CUDA call is made
     } else if (kind != kPageable) {
@@ -492,6 +536,45 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
     *ticket = req->ticket;
     cv_work_.notify_one();
     return BF_OK;
+}
+
+int Engine::flush(std::vector<Deferred> &defer)
+{
+    if (defer.empty())
+        return BF_OK;
+    cudaSetDevice(device_);
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < defer.size() && e == cudaSuccess; i += kMaxCopySegs) {
+        CopyList l{};
+        l.n = (int)std::min<size_t>(kMaxCopySegs, defer.size() - i);
+        for (int k = 0; k < l.n; ++k)
+            l.seg[k] = defer[i + k].seg;
+        e = launch_copy_segments(l, kCopyBlocksIn, copy_);
+    }
+    for (auto &d : defer)  // each slot's copy is done when the batched copies are
+        if (e == cudaSuccess)
+            e = cudaEventRecord(d.req->slot->h2d, copy_);
+    std::string msg;
+    int rc = BF_OK;
+    if (e != cudaSuccess) {
+        rc = cuda_fail(e, "batched RF copy");
+        msg = bf_last_error();
+    }
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        for (auto &d : defer) {
+            if (rc) {  // never launched: bf_poll reports the failure and releases it
+                d.req->state = 2;
+                d.req->rc = rc;
+                d.req->err = msg;
+            } else {
+                pending_.push_back(d.req);
+            }
+        }
+    }
+    defer.clear();
+    cv_work_.notify_one();
+    return rc;
 }
 
 void Engine::launch(std::vector<std::shared_ptr<Request>> &reqs)
@@ -720,6 +803,24 @@ int Engine::poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const
     cudaSetDevice(device_);
     int rc = BF_OK;
     std::vector<int> staged;
+    // device and pinned destinations: the images leave in batched copy kernels
+    // (falling back to one copy per image if a launch fails)
+    CopyList list{};
+    std::vector<std::pair<float *, int>> listed;  // (destination, request) of list's segments
+    auto launch_list = [&]() -> cudaError_t {
+        cudaError_t le = launch_copy_segments(list, kCopyBlocksOut, d2h_);
+        if (le != cudaSuccess) {
+            cudaGetLastError();
+            le = cudaSuccess;
+            for (auto &dk : listed)
+                if (le == cudaSuccess)
+                    le = cudaMemcpyAsync(dk.first, reqs[dk.second]->slot->out.p,
+                                         reqs[dk.second]->out_bytes, cudaMemcpyDefault, d2h_);
+        }
+        list.n = 0;
+        listed.clear();
+        return le;
+    };
     for (int k = 0; k < n; ++k) {
         Request &r = *reqs[k];
         int rk = r.rc ? fail(r.rc, "%s", r.err.c_str()) : BF_OK;
@@ -737,8 +838,15 @@ int Engine::poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const
         float *out = outs ? outs[k] : nullptr;
         if (!rk && out) {
             Slot &s = *r.slot;
-            cudaError_t e;
-            if (pointer_kind(out) != kPageable) {
+            cudaError_t e = cudaSuccess;
+            void *out_dev = nullptr;
+            const PtrKind kind = pointer_kind(out, &out_dev);
+            if (out_dev && copy_segment_ok(s.out.p, out_dev, r.out_bytes)) {
+                list.seg[list.n++] = CopySeg{s.out.p, out_dev, (unsigned long long)r.out_bytes};
+                listed.emplace_back(out, k);
+                if (list.n == kMaxCopySegs)
+                    e = launch_list();
+            } else if (kind != kPageable) {
                 e = cudaMemcpyAsync(out, s.out.p, r.out_bytes, cudaMemcpyDefault, d2h_);
             } else if (!s.pin_out.ensure(r.out_bytes)) {
                 e = cudaErrorMemoryAllocation;
@@ -752,7 +860,10 @@ int Engine::poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const
         if (rk && !rc)
             rc = rk;
     }
-    cudaError_t e = cudaStreamSynchronize(d2h_);
+    cudaError_t e = list.n ? launch_list() : cudaSuccess;
+    if (e != cudaSuccess && !rc)
+        rc = cuda_fail(e, "copying the results");
+    e = cudaStreamSynchronize(d2h_);
     if (e != cudaSuccess && !rc)
         rc = cuda_fail(e, "copying the results");
     if (e == cudaSuccess)
@@ -880,16 +991,20 @@ BF_API int bf_submit_many(bf_handle *h, int32_t n, const int16_t *const *rf, int
     int rc = BF_OK, k = 0;
     {
         Hold hold(eng);  // released once every frame is admitted (copies may still run)
+        std::vector<Engine::Deferred> defer;  // device and pinned sources: one batched copy
         for (; k < n; ++k) {
             if (!rf[k]) {
                 rc = fail(BF_EINVAL, "null record pointer %d", k);
                 break;
             }
             rc = eng->submit(h, rf[k], n_samples, angles_rad, n_angles, flags, tickets_out + k,
-                             false);
+                             false, &defer);
             if (rc)
                 break;
         }
+        const int rf_copy = eng->flush(defer);
+        if (!rc)
+            rc = rf_copy;
     }
     if (n_submitted)
         *n_submitted = k;

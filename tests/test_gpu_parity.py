@@ -385,6 +385,31 @@ def test_submit_many_and_poll_many(torch):
         bf.bf_destroy(h)
 
 
+def test_submit_many_and_poll_many_batched_copies(torch):
+    """Seventy frames from pinned host records into pinned host images: the
+    records and images move in batched copy kernels of at most 64 frames, an
+    image whose destination is not 16-byte aligned by plain copy; every result
+    equals its frame beamformed alone."""
+    acq = synth.SPECKLE_POINTS_128.with_(nx=40, nz=64)
+    flags = bf.BF_DAS | bf.BF_DMAS
+    rfs = [synth.speckle_points_frame(acq, seed=synth.BASE_SEED + 330 + k)[0] for k in range(4)]
+    h = make_handle(acq)
+    try:
+        solo = [run_gpu(torch, acq, rf, flags, h=h) for rf in rfs]
+        n = 70
+        srcs = [torch.from_numpy(rfs[k % 4]).pin_memory() for k in range(n)]
+        size = 2 * acq.nx * acq.nz
+        bufs = [torch.full((size + 1,), float("nan")).pin_memory() for _ in range(n)]
+        outs = [b[(1 if k == 5 else 0):][:size].view(2, acq.nx, acq.nz) for k, b in enumerate(bufs)]
+        tickets = bf.bf_submit_many(h, srcs, acq.n_samples, acq.angles_rad, flags)
+        assert bf.bf_poll_many(h, tickets, outs, timeout_us=30_000_000) == bf.BF_OK
+        for k, o in enumerate(outs):
+            np.testing.assert_allclose(o.numpy(), solo[k % 4], rtol=0,
+                                       atol=2e-6 * np.max(np.abs(solo[k % 4])))
+    finally:
+        bf.bf_destroy(h)
+
+
 @pytest.mark.parametrize("prec", [bf.BF_PREC_FP32, bf.BF_PREC_FP16])
 def test_frames_of_one_plan_share_delays_in_pairs(torch, prec):
     """Five frames of one handle and plan in a batch: two pairs share their delays
