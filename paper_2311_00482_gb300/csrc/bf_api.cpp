@@ -244,7 +244,7 @@ int handle_plan(bf_handle *h, int ns, const double *angles, int na, uint32_t fla
     PlanHost ph;
     const TileConfig tc = kTileConfigs[key.cfg];
     angle_tables(h->g, h->geo, ns, key.angles, prec, tc.rows, tc.stage_bytes, ph);
-    if (beamform_smem_bytes(ph.wmax, ph.group, prec) > (size_t)kMaxSmemPerCta)
+    if (beamform_smem_bytes(ph.wmax, ph.group, prec, 1, ph.rows) > (size_t)kMaxSmemPerCta)
         return fail(BF_EINVAL,
                     "pixel spacing too coarse for the sample rate: one tile needs %d samples per channel",
                     ph.wmax);

@@ -19,7 +19,7 @@ constexpr int kTileCols = 32;
 constexpr int kWarps = 8;
 constexpr int kThreads = 32 * kWarps;
 constexpr int kMaxGroup = 16;         // channels staged per pipeline stage (upper bound)
-constexpr int kStages = 3;            // pipeline stages in shared memory
+constexpr int kMaxStages = 3;         // pipeline stages in shared memory (at most)
 constexpr int kMaxBox = 256;          // TMA box extent limit per dimension
 constexpr int kMaxSmemPerCta = 227 << 10;  // dynamic shared memory one CTA may use
 constexpr int kNoWindow = (int)0x80000000;  // window table: no sample of this channel counts
@@ -36,7 +36,10 @@ struct TileConfig {
     int rows, stage_bytes;
 };
 constexpr TileConfig kTileConfigs[] = {{4, 24 << 10}, {4, 16 << 10}, {4, 32 << 10}, {8, 24 << 10},
-                                       {2, 10 << 10}, {2, 11 << 10}};
+                                       {2, 14 << 10}, {2, 12 << 10}};
+// Pipeline stages of a beamforming CTA: two deep stages (up to 16 channels of
+// four frames) for two-row tiles, three otherwise (measured fastest for each).
+__host__ __device__ constexpr int stages_for_rows(int rows) { return rows == 2 ? 2 : 3; }
 constexpr int kNumTileConfigs = 6;
 // Frames of one plan that one beamforming job may carry (sharing every delay).
 constexpr int kMaxFramesPerJob = 4;

@@ -342,9 +342,12 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestJob *__restrict
 
 // ------------------------------------------------------------- beamform --
 
-// Shared memory of one CTA: the mbarrier ring and window starts, then
-// kStages stages, each holding the tile's per-(channel, column) tables of one
-// channel group and the channels' record windows.
+// Shared memory of one beamforming CTA: the header (mbarrier ring, window
+// starts, channel lists, delay tables), the image staging area of multi-frame
+// jobs, then stages_for_rows(ROWS) stages, each holding the tile's
+// per-(channel, column) tables of one channel group and the channels' record
+// windows.
+
 // --------------------------------------------------------- demodulation --
 
 // One channel record per CTA: analytic signal by a length-ns transform pair
@@ -387,19 +390,19 @@ __global__ void __launch_bounds__(256) demod_kernel(const DemodJob *__restrict__
 }
 
 struct SmemHeader {
-    uint64_t full[kStages];   // producer -> consumers: the stage's copies have landed
-    uint64_t empty[kStages];  // consumers -> producer: every consumer warp is done with it
-    int2 wf[kStages][kMaxGroup];  // (window start, band flags) per staged channel
+    uint64_t full[kMaxStages];   // producer -> consumers: the stage's copies have landed
+    uint64_t empty[kMaxStages];  // consumers -> producer: every consumer warp is done with it
+    int2 wf[kMaxStages][kMaxGroup];  // (window start, band flags) per staged channel
     // per row band (consumer warp): the stage's channels that every pixel of the
     // band counts, then those that only some pixels count
-    uint8_t list[kStages][kWarps][kMaxGroup];
-    uint8_t nfull[kStages][kWarps], ntot[kStages][kWarps];
+    uint8_t list[kMaxStages][kWarps][kMaxGroup];
+    uint8_t nfull[kMaxStages][kWarps], ntot[kMaxStages][kWarps];
     // per stage that starts an angle: the tile's delay tables (integer part and
     // remainder of the column terms [32], then of the row terms [up to 64];
     // kappa z of the rows)
-    int tK[kStages][kTileCols + 64];
-    float tF[kStages][kTileCols + 64];
-    float tZ[kStages][64];
+    int tK[kMaxStages][kTileCols + 64];
+    float tF[kMaxStages][kTileCols + 64];
+    float tZ[kMaxStages][64];
     // multi-frame jobs: consumers -> storer (the tile's images are staged),
     // storer -> consumers (the staging area is free again)
     uint64_t epi_full, epi_empty;
@@ -829,6 +832,7 @@ __global__ void __launch_bounds__(beamform_threads<NF>(),
     // stage size; inside a stage the layout is the job's: int2 rows [G][32],
     // float dx^2 [G][32], windows [G][wmax].
     constexpr int EPI = epi_bytes(NF, ROWS);
+    constexpr int kStages = stages_for_rows(ROWS);
     constexpr int CFL = epi_col_floats(ROWS);
     auto stage_base = [&](int st) {
         return smem + kHeaderBytes + EPI + (size_t)st * stage_stride;
@@ -1846,7 +1850,7 @@ cudaError_t launch_bf_t(const BfJob *jobs, const int *prefix, int njobs, int til
         return e;
     // persistent grid: every CTA resident at once, each walking the tiles
     const int grid = std::max(1, std::min(tiles, std::max(occ, 1) * sms));
-    const int stride = (int)((smem - kHeaderBytes - epi_bytes(NF, ROWS)) / kStages);
+    const int stride = (int)((smem - kHeaderBytes - epi_bytes(NF, ROWS)) / stages_for_rows(ROWS));
     k<<<grid, threads, smem, st>>>(jobs, prefix, njobs, tiles, stride, err);
     return cudaGetLastError();
 }
@@ -1895,7 +1899,7 @@ cudaError_t launch_bf_p(const BfJob *jobs, const int *prefix, int njobs, int til
 size_t beamform_smem_bytes(int wmax, int group, int prec, int nf, int rows)
 {
     return (size_t)kHeaderBytes + (size_t)epi_bytes(nf, rows) +
-           (size_t)kStages * stage_bytes(group, wmax, pair_bytes(prec), nf);
+           (size_t)stages_for_rows(rows) * stage_bytes(group, wmax, pair_bytes(prec), nf);
 }
 
 // Image columns per envelope CTA for a power-of-two transform: two per
