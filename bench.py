@@ -70,8 +70,8 @@ def dist_info():
 # (profiles/beamform_kernel_cyst512_8frames.md: 8 frames per launch; the
 # traffic grows with the frames).  Valid only for the kernel source the
 # capture was taken on: any other source reports null.
-TRAFFIC_CAPTURE = {"sources_sha256": "125130ff0af8738700236621f624fd8c76aa0b64c7f02bf06b7bf8652ae77458",
-                   "frames": 8, "bytes": 4684288 + 0}
+TRAFFIC_CAPTURE = {"sources_sha256": "f32a54e843874d3d85f7daf40e8e8fc6e8c3d8505ed56b5d7c9150dfc627cb85",
+                   "frames": 8, "bytes": 4688640 + 0}
 
 
 def beamform_traffic(frames):
