@@ -99,6 +99,11 @@ enum {
     BF_ENOTFOUND = -6,   /* unknown ticket */
     BF_ENOSYS = -7       /* feature not available in this build */
 };
+/* Error-path testing: the environment variable BF_FAULT, a comma-separated
+ * list read on every use, injects failures on the host: alloc (device
+ * allocations fail with BF_ENOMEM), submit (admission refuses requests with
+ * BF_EAGAIN), copy (a request's RF copy fails with BF_ECUDA).  Unset in
+ * normal use.  bf_selftest_wait exercises the device-side bounded wait. */
 
 /* Paper: Sec. II-B (array, pixel grid and the time of flight of Eq. (1)).
  * Create a handle for one geometry and pixel grid.  fs_hz: sampling rate,
