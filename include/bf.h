@@ -211,7 +211,10 @@ BF_API int bf_submit_many(bf_handle *h, int32_t n, const int16_t *const *rf, int
  * every result into outs[k] (host or device, out_bytes each; outs or outs[k]
  * NULL discards) with one synchronisation at the end and releases every
  * ticket; returns the first failure of any ticket (all are released).  On
- * BF_PENDING / BF_ETIMEDOUT / BF_ENOTFOUND nothing is released. */
+ * BF_PENDING / BF_ETIMEDOUT / BF_ENOTFOUND nothing is released.  Device and
+ * page-locked host destinations (16-byte aligned) are written by a copy
+ * kernel, the latter through their device-mapped address: a host buffer
+ * registered read-only for the device must not be an output. */
 BF_API int bf_poll_many(bf_handle *h, int32_t n, const uint64_t *tickets, float *const *outs,
                         size_t out_bytes, int64_t timeout_us);
 
