@@ -67,9 +67,9 @@ def dist_info():
 
 
 # DRAM bytes (read + write) of one beamform_kernel launch from an ncu capture
-# (profiles/beamform_kernel_cyst512_8frames.md: 8 frames per launch; the
-# traffic grows with the frames).  Valid only for the kernel source the
-# capture was taken on: any other source reports null.
+# of the 512 x 512 workload at 8 frames per launch (the traffic grows with the
+# frames).  Valid only for the kernel source the capture was taken on: any
+# other source reports null.
 TRAFFIC_CAPTURE = {"sources_sha256": "f32a54e843874d3d85f7daf40e8e8fc6e8c3d8505ed56b5d7c9150dfc627cb85",
                    "frames": 8, "bytes": 4688640 + 0}
 

@@ -113,11 +113,15 @@ enum {
 BF_API int bf_create(const bf_geometry *geometry, const bf_grid *grid, double fs_hz,
                      double f0_hz, double c_mps, bf_handle **out);
 
-/* Free a handle and its device memory.  BF_EINVAL while tickets are pending. */
+/* Paper: no counterpart (resource lifetime of this implementation).
+ * Free a handle and its device memory.  BF_EINVAL while tickets are pending;
+ * the handle stays valid then. */
 BF_API int bf_destroy(bf_handle *h);
 
-/* Device stream for all of this handle's work (a cudaStream_t; NULL = the
- * library's own non-blocking stream). */
+/* Paper: no counterpart (stream ordering of this implementation).
+ * Device stream for all of this handle's work (a cudaStream_t; NULL = the
+ * library's own non-blocking stream).  The caller keeps ownership of the
+ * stream and must keep it alive while the handle uses it. */
 BF_API int bf_set_stream(bf_handle *h, void *cuda_stream);
 
 /* Paper: Sec. II-B-3 (the f-k migrations the paper evaluates next to the
@@ -147,7 +151,8 @@ BF_API int bf_fkmig(bf_handle *h, const int16_t *rf_dev, int32_t n_samples,
  * call (a prepared batch keeps the value it was created with). */
 BF_API int bf_set_pdas_order(bf_handle *h, double p);
 
-/* Bytes of one output for the given mode_and_flags: images * nx * nz * 4. */
+/* Paper: no counterpart (buffer sizing).
+ * Bytes of one output for the given mode_and_flags: images * nx * nz * 4. */
 BF_API size_t bf_output_bytes(const bf_handle *h, uint32_t mode_and_flags);
 
 /* Paper: Sec. II-B, Eq. (1) (delay, interpolation, apodization, sum), the
@@ -186,7 +191,10 @@ BF_API int bf_submit(bf_handle *h, const int16_t *rf, int32_t n_samples,
                      const double *angles_rad, int32_t n_angles, uint32_t mode_and_flags,
                      uint64_t *ticket_out);
 
-/* Wait up to timeout_us (0: do not wait; < 0: wait without limit) for a
+/* Paper: the image of one frame the front end streamed in (Sec. II-A) comes
+ * back beamformed as bf_beamform computes it (Sec. II-B, Eq. (1), Fig. 3);
+ * request tickets have no counterpart.
+ * Wait up to timeout_us (0: do not wait; < 0: wait without limit) for a
  * ticket.  BF_PENDING (timeout_us == 0) or BF_ETIMEDOUT (timeout passed) if
  * not ready, leaving the ticket valid; BF_OK after copying the result into
  * out (host or device, out_bytes >= bf_output_bytes; out == NULL discards
@@ -218,28 +226,33 @@ BF_API int bf_submit_many(bf_handle *h, int32_t n, const int16_t *const *rf, int
 BF_API int bf_poll_many(bf_handle *h, int32_t n, const uint64_t *tickets, float *const *outs,
                         size_t out_bytes, int64_t timeout_us);
 
-/* Serving-engine introspection: the batch a launched ticket rides in and how
+/* Paper: no counterpart (serving-engine introspection of this implementation).
+ * The batch a launched ticket rides in and how
  * many frames that batch holds (BF_PENDING while still queued). */
 BF_API int bf_ticket_batch(bf_handle *h, uint64_t ticket, int32_t *batch_id,
                            int32_t *batch_frames);
 
-/* Device time of a ticket's batch once it has finished: when the batch began
+/* Paper: no counterpart (latency measurement of the serving engine).
+ * Device time of a ticket's batch once it has finished: when the batch began
  * and ended executing, in ms since the engine started (BF_PENDING before). */
 BF_API int bf_ticket_times(bf_handle *h, uint64_t ticket, double *start_ms, double *end_ms);
 
-/* Hold (paused != 0) or resume the serving engine's launches on the current
+/* Paper: no counterpart (serving-engine control).
+ * Hold (paused != 0) or resume the serving engine's launches on the current
  * device.  Submissions are still admitted while paused; on resume everything
  * queued is launched as batches. */
 BF_API int bf_engine_pause(int32_t paused);
 
-/* Serving-engine knobs for the current device (values <= 0 keep the current
+/* Paper: no counterpart (serving-engine control).
+ * Serving-engine knobs for the current device (values <= 0 keep the current
  * setting): frames per launched batch (default 64), batches in flight
  * (default 3), device memory budget of admitted requests in bytes (default
  * half the device, or BF_MEM_BUDGET_MB from the environment). */
 BF_API int bf_engine_configure(int32_t max_batch, int32_t max_inflight,
                                uint64_t memory_budget_bytes);
 
-/* Wait for the handle's stream and report device-side failures of its
+/* Paper: no counterpart (error reporting of this implementation).
+ * Wait for the handle's stream and report device-side failures of its
  * bf_beamform work (BF_ETIMEDOUT when a bounded wait inside a kernel gave up). */
 BF_API int bf_sync(bf_handle *h);
 
@@ -263,14 +276,20 @@ typedef struct bf_frame {
  * are copied; the RF and output buffers must stay valid while the batch is
  * launched. */
 BF_API int bf_batch_create(const bf_frame *frames, int32_t n_frames, bf_batch **out);
-/* Launch a prepared batch on a stream (cudaStream_t; NULL = default stream). */
+/* Paper: as bf_batch_create.  Launch a prepared batch on a stream
+ * (cudaStream_t; NULL = default stream): replays its CUDA graph. */
 BF_API int bf_batch_launch(bf_batch *b, void *cuda_stream);
-/* Synchronise the stream and report device-side failures of the batch's launches. */
+/* Paper: no counterpart (error reporting).  Synchronise the stream and report
+ * device-side failures of the batch's launches. */
 BF_API int bf_batch_status(bf_batch *b, void *cuda_stream);
-/* Device time of the last completed replay, from events captured in the graph:
+/* Paper: no counterpart (per-stage timing; the paper times whole
+ * reconstructions, Sec. III-B).
+ * Device time of the last completed replay, from events captured in the graph:
  * ms3[0] ingest (+ resets), ms3[1] beamforming launches, ms3[2] envelope + log.
  * *kernel_launches (optional) receives the number of kernels one replay runs. */
 BF_API int bf_batch_timing(bf_batch *b, float *ms3, int32_t *kernel_launches);
+/* Paper: no counterpart.  Free a batch (its graph, tables and scratch); the
+ * caller's RF and output buffers are not touched. */
 BF_API int bf_batch_destroy(bf_batch *b);
 
 /* Paper: the F-number aperture and the record bound of Sec. II-B.
@@ -352,10 +371,13 @@ BF_API int bf_logdb_static(const float *y_dev, int32_t nx, int32_t nz, double z0
                            double f0_hz, double c_mps, int32_t bandpass, float *db_dev,
                            void *cuda_stream);
 
-/* Thread-local message of the last failure ("" if none). */
+/* Paper: no counterpart (error reporting of this implementation).
+ * Thread-local message of the last failure on the calling thread ("" if
+ * none).  The string belongs to the library and stays valid until the next
+ * failing call on the same thread. */
 BF_API const char *bf_last_error(void);
 
-/* Library version: major * 10000 + minor * 100 + patch. */
+/* Paper: no counterpart.  Library version: major * 10000 + minor * 100 + patch. */
 BF_API int bf_version(void);
 
 #ifdef __cplusplus

@@ -673,7 +673,10 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
                 ij.maxbits_more[q] = g.stage != BF_OUT_RF ? g.maxbits : nullptr;
             }
         }
-        ij.chunks = (ij.nf * ((ij.nsp + 7) / 8) + 255) / 256;
+        // threads per record row: one per 8 pairs and frame (per frame pair for
+        // FP32 multi-frame jobs)
+        const int units = (f.prec == kPrecF32 && ij.nf > 1) ? ij.nf / 2 : ij.nf;
+        ij.chunks = (units * ((ij.nsp + 7) / 8) + 255) / 256;
         ig[f.prec].push_back(ij);
     }
     for (auto &kv : ig) {

@@ -29,6 +29,7 @@
 #include <thread>
 
 #include "bf_engine.h"
+#include "bf_ptr.h"
 
 namespace bfi {
 
@@ -137,9 +138,12 @@ enum PtrKind { kPageable = 0, kPinned = 1, kDevice = 2 };
 // CTAs per frame of the batched copy kernels (records in, images out).
 constexpr int kCopyBlocksIn = 2, kCopyBlocksOut = 1;
 
-// dev (optional): an address of the memory a kernel may use (device memory
-// itself, or the device-mapped address of pinned host memory), else null.
-PtrKind pointer_kind(const void *p, void **dev = nullptr)
+// dev (optional): an address of the memory a copy kernel on `device` may use
+// (device memory of that device, or the device-mapped address of page-locked
+// host memory; for a buffer the kernel writes, only memory from
+// cudaHostAlloc, since registered memory may be read-only for the device),
+// else null, and the caller takes the cudaMemcpyAsync path.
+PtrKind pointer_kind(const void *p, int device, void **dev = nullptr, bool write = false)
 {
     if (dev)
         *dev = nullptr;
@@ -149,13 +153,26 @@ PtrKind pointer_kind(const void *p, void **dev = nullptr)
         return kPageable;
     }
     if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
-        if (dev && a.type == cudaMemoryTypeDevice)
-            *dev = const_cast<void *>(p);
+        if (dev)
+            *dev = kernel_address(a, p, device, device, write, false);
         return kDevice;
     }
     if (a.type == cudaMemoryTypeHost) {
-        if (dev)
-            *dev = a.devicePointer;
+        if (dev) {
+            int current = -1;
+            if (cudaGetDevice(&current) != cudaSuccess) {
+                cudaGetLastError();
+                current = -1;
+            }
+            bool host_alloc = false;
+            if (write) {
+                unsigned flags = 0;
+                host_alloc = cudaHostGetFlags(&flags, const_cast<void *>(p)) == cudaSuccess;
+                if (!host_alloc)
+                    cudaGetLastError();
+            }
+            *dev = kernel_address(a, p, device, current, write, host_alloc);
+        }
         return kPinned;
     }
     return kPageable;
@@ -480,7 +497,7 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
     // pageable host data through the slot's pinned staging.
     cudaError_t e;
     void *rf_dev = nullptr;
-    const PtrKind kind = pointer_kind(rf, &rf_dev);
+    const PtrKind kind = pointer_kind(rf, device_, &rf_dev);
     const bool inject = fault_injected("copy");
     if (defer && !inject && rf_dev && copy_segment_ok(rf_dev, s.rf.p, rf_bytes)) {
         // batched with the call's other frames: registered now, queued by flush()
@@ -720,7 +737,7 @@ int Engine::poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes, in
     if (!rc && out) {
         Slot &s = *req->slot;
         cudaError_t e;
-        if (pointer_kind(out) != kPageable) {
+        if (pointer_kind(out, device_) != kPageable) {
             e = cudaMemcpyAsync(out, s.out.p, req->out_bytes, cudaMemcpyDefault, d2h_);
             if (e == cudaSuccess)
                 e = cudaStreamSynchronize(d2h_);
@@ -840,7 +857,7 @@ int Engine::poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const
             Slot &s = *r.slot;
             cudaError_t e = cudaSuccess;
             void *out_dev = nullptr;
-            const PtrKind kind = pointer_kind(out, &out_dev);
+            const PtrKind kind = pointer_kind(out, device_, &out_dev, true);
             if (out_dev && copy_segment_ok(s.out.p, out_dev, r.out_bytes)) {
                 list.seg[list.n++] = CopySeg{s.out.p, out_dev, (unsigned long long)r.out_bytes};
                 listed.emplace_back(out, k);

@@ -153,10 +153,12 @@ __device__ __forceinline__ float pdas_root(float v, float inv_p, bool square)
 }
 
 // Receive path length beyond the depth term, in samples:
-//   sqrt(dx^2 + z^2) - z = dx^2 / (sqrt(dx^2 + z^2) + z).
-// The large, pixel-only part of the delay (transmit leg + depth) comes from
-// the host as an exact integer + remainder, so FP32 only has to carry this
-// small term; its relative error (a few ulp) stays far below a sample.
+//   q = sqrt(d2 + z^2) - z = d2 / (sqrt(d2 + z^2) + z),
+// d2 = (kappa (x_p - x_i))^2, z = kappa z_p.  The large, pixel-only part of
+// the delay (transmit leg + depth) comes from the host as an exact integer +
+// remainder, so FP32 only has to carry this small term, formed without
+// cancellation; its relative error (a few ulp) keeps the delay within ~1e-6
+// samples (float32 emulation: 1e-6 rms, 1e-5 max over |x_p - x_i| <= z_p / 3).
 // dx2 >= 1e-30 (host floor), so the square root never sees 0; dx2 + z^2 is
 // formed with one rounding.
 __device__ __forceinline__ float rx_excess(float dx2, float z)
@@ -284,10 +286,12 @@ __device__ __forceinline__ void row_pairs(const int16_t *__restrict__ u, int ns,
 }
 
 // Record rows to sample pairs.  A job's CTAs take its rows in order, `chunks`
-// CTAs per row; thread g of a row handles pairs 8 (g / nf) .. + 7 of frame
-// g % nf.  nf = 1 writes [row][nsp]; a multi-frame job (nf = 2, 4) writes its
-// frames interleaved, pair j of frame f at [row][j][f], so that the frame
-// lanes of a warp fill adjacent slots.
+// CTAs per row.  nf = 1 writes [row][nsp] (thread g: pairs 8 g .. 8 g + 7).
+// A multi-frame job (nf = 2, 4) writes its frames interleaved per pair index:
+// FP32 as frame pairs, pair j of frames 2q, 2q + 1 at [row][j][q] as
+// (mid_2q, mid_2q+1, diff_2q, diff_2q+1) (thread g: frame pair g % (nf / 2),
+// pairs 8 (g / (nf / 2)) .. + 7); FP16 / BF16 as one 4-byte pair per frame at
+// [row][j][f] (thread g: frame g % nf, pairs 8 (g / nf) .. + 7).
 template <int PREC>
 __global__ void __launch_bounds__(256) ingest_kernel(const IngestJob *__restrict__ jobs,
                                                      const int *__restrict__ blk_prefix, int njobs)
@@ -305,28 +309,40 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestJob *__restrict
     }
     const int nf = J.nf;  // 1, 2 or 4
     const int g = chunk * blockDim.x + threadIdx.x;
+    auto record = [&](int f) { return f == 0 ? J.rf : J.rf_more[f - 1]; };
+    auto vec_ok = [&](const int16_t *rf) {
+        return (J.ns & 7) == 0 && (reinterpret_cast<unsigned long long>(rf) & 15) == 0;
+    };
+    float2 fp[8];
+    unsigned hp[8];
+    if (PREC == kPrecF32 && nf > 1) {
+        const int npair = nf / 2;
+        const int q = g % npair, j0 = (g / npair) * 8;
+        if (j0 >= J.nsp)
+            return;
+        float2 fq[8];
+        const int16_t *ra = record(2 * q), *rb = record(2 * q + 1);
+        row_pairs<PREC>(ra + (size_t)row * J.ns, J.ns, j0, vec_ok(ra), fp, hp);
+        row_pairs<PREC>(rb + (size_t)row * J.ns, J.ns, j0, vec_ok(rb), fq, hp);
+        float4 *o = reinterpret_cast<float4 *>(J.pairs) + ((size_t)row * J.nsp + j0) * npair + q;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            o[(size_t)k * npair] = make_float4(fp[k].x, fq[k].x, fp[k].y, fq[k].y);
+        return;
+    }
     const int f = g & (nf - 1), j0 = (g / nf) * 8;
     if (j0 >= J.nsp)
         return;
-    const int16_t *__restrict__ rf = f == 0 ? J.rf : J.rf_more[f - 1];
+    const int16_t *__restrict__ rf = record(f);
     const int16_t *__restrict__ u = rf + (size_t)row * J.ns;
-    const bool vec = (J.ns & 7) == 0 && (reinterpret_cast<unsigned long long>(rf) & 15) == 0;
-    float2 fp[8];
-    unsigned hp[8];
-    row_pairs<PREC>(u, J.ns, j0, vec, fp, hp);
+    row_pairs<PREC>(u, J.ns, j0, vec_ok(rf), fp, hp);
     const size_t at = ((size_t)row * J.nsp + j0) * nf + f;  // slot of pair j0
     if (PREC == kPrecF32) {
         float2 *o = reinterpret_cast<float2 *>(J.pairs) + at;
-        if (nf == 1) {  // 16-byte stores of two pairs
 #pragma unroll
-            for (int q = 0; q < 8; q += 2)
-                reinterpret_cast<float4 *>(o)[q / 2] =
-                    make_float4(fp[q].x, fp[q].y, fp[q + 1].x, fp[q + 1].y);
-        } else {
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                o[(size_t)q * nf] = fp[q];
-        }
+        for (int k = 0; k < 8; k += 2)  // nf == 1: 16-byte stores of two pairs
+            reinterpret_cast<float4 *>(o)[k / 2] =
+                make_float4(fp[k].x, fp[k].y, fp[k + 1].x, fp[k + 1].y);
     } else {
         unsigned *o = reinterpret_cast<unsigned *>(J.pairs) + at;
         if (nf == 1) {
@@ -334,8 +350,8 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestJob *__restrict
             reinterpret_cast<uint4 *>(o)[1] = make_uint4(hp[4], hp[5], hp[6], hp[7]);
         } else {
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                o[(size_t)q * nf] = hp[q];
+            for (int k = 0; k < 8; ++k)
+                o[(size_t)k * nf] = hp[k];
         }
     }
 }
@@ -580,34 +596,48 @@ __device__ __forceinline__ f32x2_t mul2(f32x2_t a, f32x2_t b)
 
 // Rounded delays of rows j and j + 1 for one channel (d2 packed twice): the
 // rx_excess arithmetic of both rows in paired instructions, each half with
-// exactly the scalar version's operations and roundings.  m holds the delay
-// plus the rounding constant (integer in its low bits), al the offset in
-// [-1/2, 1/2].
-__device__ __forceinline__ void delay2(f32x2_t D2, float Za, float Zb, float fa, float fb,
-                                       float &ma, float &mb, float &ala, float &alb)
+// exactly the scalar version's operations and roundings, plus the pixels'
+// remainders.  m holds the delay plus the rounding constant (integer in its
+// low bits), al the offset in [-1/2, 1/2].
+__device__ __forceinline__ void delay2(f32x2_t D2, f32x2_t Zp, f32x2_t Fp, float &ma, float &mb,
+                                       float &ala, float &alb)
 {
-    const f32x2_t Zp = pk2(Za, Zb);
     const f32x2_t s = fma2(Zp, Zp, D2);
     float sa, sb;
     upk2(s, sa, sb);
     const f32x2_t r = mul2(s, pk2(rsqrt_approx(sa), rsqrt_approx(sb)));
     float da, db;
     upk2(add2(r, Zp), da, db);
-    const f32x2_t x = fma2(D2, pk2(rcp_approx(da), rcp_approx(db)), pk2(fa, fb));
+    const f32x2_t x = fma2(D2, pk2(rcp_approx(da), rcp_approx(db)), Fp);
     const f32x2_t MG = pk2(kRoundMagic, kRoundMagic);
     const f32x2_t m = add2(x, MG);
     upk2(m, ma, mb);
     upk2(sub2(x, sub2(m, MG)), ala, alb);
 }
 
+// Per-angle constants of a thread's rows, packed in row pairs for delay2: the
+// depth term z and the remainder f (minus 1/2).
+template <int ROWS>
+struct RowPack {
+    f32x2_t Z[ROWS / 2], F[ROWS / 2];
+    __device__ __forceinline__ void set(const float *z, const float *f)
+    {
+#pragma unroll
+        for (int j = 0; j < ROWS; j += 2) {
+            Z[j / 2] = pk2(z[j], z[j + 1]);
+            F[j / 2] = pk2(f[j], f[j + 1]);
+        }
+    }
+};
+
 // Accumulate one channel into the ROWS pixels of this thread.  CHECK: test
 // every pixel's row against the channel's counted rows (otherwise the whole
 // row band of the warp counts it).
 template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS, bool CHECK>
 __device__ __forceinline__ void accumulate(uint32_t win, int wmax, int w0, float d2, int2 vr,
-                                           int r_first, const float *Z, const float *fp,
-                                           const int *Kc, float *S1, float *T1, float *T2,
-                                           float *Su2, float *P1, float inv_p, bool square)
+                                           int r_first, const RowPack<ROWS> &P, const int *Kc,
+                                           float *S1, float *T1, float *T2, float *Su2, float *P1,
+                                           float inv_p, bool square)
 {
     constexpr int PB = PairIO<PREC>::kBytes;
     static_assert(ROWS % 2 == 0, "rows are processed in pairs");
@@ -616,7 +646,7 @@ __device__ __forceinline__ void accumulate(uint32_t win, int wmax, int w0, float
 #pragma unroll
     for (int j = 0; j < ROWS; j += 2) {
         float m[2], al[2];  // al in [-1/2, 1/2]
-        delay2(D2, Z[j], Z[j + 1], fp[j], fp[j + 1], m[0], m[1], al[0], al[1]);
+        delay2(D2, P.Z[j / 2], P.F[j / 2], m[0], m[1], al[0], al[1]);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int jj = j + h;
@@ -639,18 +669,23 @@ __device__ __forceinline__ void accumulate(uint32_t win, int wmax, int w0, float
     }
 }
 
-// The NF frames' staged pairs at one window index of a multi-frame job
-// (interleaved by frame, [pair][frame]): v[f] = the frame's sample at offset
-// al, read with 16-byte loads (two FP32 pairs, four FP16 / BF16 pairs each).
+// The NF frames' samples at one window index of a multi-frame job, as NF / 2
+// frame pairs (v[q] = frames 2q, 2q + 1).  FP32 records are staged as
+// (mid_2q, mid_2q+1, diff_2q, diff_2q+1) per window index and frame pair, so
+// one 16-byte load and one paired FMA interpolate two frames; FP16 / BF16
+// records keep one 4-byte pair per frame ([pair][frame]).
 template <int PREC, int NF>
-__device__ __forceinline__ void interp_frames(uint32_t a, float al, float *v)
+__device__ __forceinline__ void interp_frames(uint32_t a, float al, f32x2_t *v)
 {
     if constexpr (PREC == kPrecF32) {
+        const f32x2_t AL = pk2(al, al);
 #pragma unroll
-        for (int f = 0; f < NF; f += 2) {
-            const float4 q = lds_f32x4(a + (uint32_t)f * 8u);
-            v[f] = fmaf(al, q.y, q.x);
-            v[f + 1] = fmaf(al, q.w, q.z);
+        for (int q = 0; q < NF / 2; ++q) {
+            f32x2_t mid, diff;
+            asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];"
+                         : "=l"(mid), "=l"(diff)
+                         : "r"(a + (uint32_t)q * 16u));
+            v[q] = fma2(AL, diff, mid);
         }
     } else {
         unsigned w[NF];
@@ -662,6 +697,7 @@ __device__ __forceinline__ void interp_frames(uint32_t a, float al, float *v)
             asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(w[0]), "=r"(w[1]) : "r"(a));
         }
         const float t = al + 0.5f;
+        float x[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             float lo, hi;
@@ -673,19 +709,26 @@ __device__ __forceinline__ void interp_frames(uint32_t a, float al, float *v)
                 lo = __uint_as_float(w[f] << 16);
                 hi = __uint_as_float(w[f] & 0xffff0000u);
             }
-            v[f] = fmaf(t, hi - lo, lo);
+            x[f] = fmaf(t, hi - lo, lo);
         }
+#pragma unroll
+        for (int q = 0; q < NF / 2; ++q)
+            v[q] = pk2(x[2 * q], x[2 * q + 1]);
     }
 }
 
 // One channel into the ROWS pixels of this thread for NF frames of one plan:
 // the delay of each pixel is formed once and read from every frame's pairs
-// (interleaved by frame in the window).
+// (interleaved by frame in the window); the sums of two frames move in paired
+// FP32 instructions.  DMAS sums s = sign(v) sqrt|v| and s^2 (= |v| up to the
+// square root's rounding, so that the pairwise products the identity
+// ((sum s)^2 - sum s^2) / 2 stands for are those of the computed s).
 template <int PREC, bool DMAS, int ROWS, int NF, bool CHECK>
 __device__ __forceinline__ void accumulate_fn(uint32_t win, int wmax, int w0, float d2, int2 vr,
-                                              int r_first, const float *Z, const float *fp,
-                                              const int *Kc, float (&S1)[NF][ROWS],
-                                              float (&T1)[NF][ROWS], float (&T2)[NF][ROWS])
+                                              int r_first, const RowPack<ROWS> &P, const int *Kc,
+                                              f32x2_t (&S1)[NF / 2][ROWS],
+                                              f32x2_t (&T1)[NF / 2][ROWS],
+                                              f32x2_t (&T2)[NF / 2][ROWS])
 {
     constexpr int PB = PairIO<PREC>::kBytes;
     const unsigned span = (unsigned)(vr.y - vr.x);
@@ -693,22 +736,25 @@ __device__ __forceinline__ void accumulate_fn(uint32_t win, int wmax, int w0, fl
 #pragma unroll
     for (int j = 0; j < ROWS; j += 2) {
         float m[2], al[2];
-        delay2(D2, Z[j], Z[j + 1], fp[j], fp[j + 1], m[0], m[1], al[0], al[1]);
+        delay2(D2, P.Z[j / 2], P.F[j / 2], m[0], m[1], al[0], al[1]);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int jj = j + h;
             const unsigned idx =
                 min((unsigned)(__float_as_int(m[h]) + Kc[jj] - w0), (unsigned)(wmax - 1));
-            float v[NF];
+            f32x2_t v[NF / 2];
             interp_frames<PREC, NF>(win + idx * (NF * PB), al[h], v);
             if (!CHECK || (unsigned)(r_first + jj - vr.x) <= span) {
 #pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    S1[f][jj] += v[f];
+                for (int q = 0; q < NF / 2; ++q) {
+                    S1[q][jj] = add2(S1[q][jj], v[q]);
                     if (DMAS) {
-                        const float av = fabsf(v[f]);
-                        T1[f][jj] += copysignf(sqrt_approx(av), v[f]);
-                        T2[f][jj] += av;
+                        float a, b;
+                        upk2(v[q], a, b);
+                        const f32x2_t sr = pk2(copysignf(sqrt_approx(fabsf(a)), a),
+                                               copysignf(sqrt_approx(fabsf(b)), b));
+                        T1[q][jj] = add2(T1[q][jj], sr);
+                        T2[q][jj] = fma2(sr, sr, T2[q][jj]);
                     }
                 }
             }
@@ -717,22 +763,21 @@ __device__ __forceinline__ void accumulate_fn(uint32_t win, int wmax, int w0, fl
 }
 
 // Two channels that every pixel of the band counts, interleaved: twice the
-// independent dependency chains per thread (square roots, reciprocal, shared
-// load) for the scheduler to overlap.
+// independent dependency chains per thread (square roots, shared loads) for
+// the scheduler to overlap.
 template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS>
 __device__ __forceinline__ void accumulate2(uint32_t win0, int w00, float d20, uint32_t win1,
-                                            int w01, float d21, int wmax, const float *Z,
-                                            const float *fp, const int *Kc, float *S1, float *T1,
-                                            float *T2, float *Su2, float *P1, float inv_p,
-                                            bool square)
+                                            int w01, float d21, int wmax, const RowPack<ROWS> &P,
+                                            const int *Kc, float *S1, float *T1, float *T2,
+                                            float *Su2, float *P1, float inv_p, bool square)
 {
     constexpr int PB = PairIO<PREC>::kBytes;
     const f32x2_t D20 = pk2(d20, d20), D21 = pk2(d21, d21);
 #pragma unroll
     for (int j = 0; j < ROWS; j += 2) {
         float m0[2], al0[2], m1[2], al1[2];
-        delay2(D20, Z[j], Z[j + 1], fp[j], fp[j + 1], m0[0], m0[1], al0[0], al0[1]);
-        delay2(D21, Z[j], Z[j + 1], fp[j], fp[j + 1], m1[0], m1[1], al1[0], al1[1]);
+        delay2(D20, P.Z[j / 2], P.F[j / 2], m0[0], m0[1], al0[0], al0[1]);
+        delay2(D21, P.Z[j / 2], P.F[j / 2], m1[0], m1[1], al1[0], al1[1]);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int jj = j + h;
@@ -765,16 +810,16 @@ __device__ __forceinline__ void accumulate2(uint32_t win0, int w00, float d20, u
 // s / sqrt|s| = sqrt|s| exp(j arg s) per angle.
 template <bool BB, int ROWS, bool CHECK>
 __device__ __forceinline__ void accumulate_iq(uint32_t win, int wmax, int w0, float d2, int2 vr,
-                                              int r_first, const float *Z, const float *fp,
-                                              const int *Kc, float c1, float c2, float *Yr,
-                                              float *Yi, float *Tr, float *Ti)
+                                              int r_first, const RowPack<ROWS> &P, const int *Kc,
+                                              float c1, float c2, float *Yr, float *Yi, float *Tr,
+                                              float *Ti)
 {
     const unsigned span = (unsigned)(vr.y - vr.x);
     const f32x2_t D2 = pk2(d2, d2);
 #pragma unroll
     for (int j = 0; j < ROWS; j += 2) {
         float mm[2], aa[2];
-        delay2(D2, Z[j], Z[j + 1], fp[j], fp[j + 1], mm[0], mm[1], aa[0], aa[1]);
+        delay2(D2, P.Z[j / 2], P.F[j / 2], mm[0], mm[1], aa[0], aa[1]);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int jj = j + h;
@@ -1059,18 +1104,23 @@ __global__ void __launch_bounds__(beamform_threads<NF>(),
         const int r_first = tz * TR + warp * ROWS;
 
         int Kc[ROWS];
-        float Z[ROWS], fp[ROWS];
+        RowPack<ROWS> P;
         float S1[ROWS], T1[ROWS], T2[ROWS], Yd[ROWS], Su2[ROWS], P1[ROWS], Yp[ROWS];
-        float FS1[NF][ROWS], FT1[NF][ROWS], FT2[NF][ROWS], FYd[NF][ROWS];  // NF > 1: per frame
+        // NF > 1: per frame pair (frames 2q, 2q + 1 in the two halves)
+        constexpr int NP = NF > 1 ? NF / 2 : 1;
+        f32x2_t FS1p[NP][ROWS], FT1[NP][ROWS], FT2[NP][ROWS], FYdp[NP][ROWS];
+        const f32x2_t zero2 = pk2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < ROWS; ++j) {
             S1[j] = T1[j] = T2[j] = Yd[j] = Su2[j] = P1[j] = Yp[j] = 0.f;
 #pragma unroll
-            for (int f = 0; f < NF; ++f)
-                FS1[f][j] = FT1[f][j] = FT2[f][j] = FYd[f][j] = 0.f;
+            for (int q = 0; q < NP; ++q)
+                FS1p[q][j] = FT1[q][j] = FT2[q][j] = FYdp[q][j] = zero2;
             Kc[j] = 0;
-            fp[j] = Z[j] = 0.f;
         }
+#pragma unroll
+        for (int j = 0; j < ROWS / 2; ++j)
+            P.Z[j] = P.F[j] = zero2;
         const float pdas_p = J->pdas_p, inv_p = J->pdas_inv_p;
         const bool square = pdas_p == 2.0f;  // uniform over the job
         // IQ: S1 / Y1i the IQ-DAS sum, T1 / Ti the per-angle BB-DMAS sum, Yd / Y2i BB-DMAS
@@ -1100,6 +1150,7 @@ __global__ void __launch_bounds__(beamform_threads<NF>(),
             if (g == 0) {  // this angle's delay tables, staged by the producer
                 const int ck = sh.tK[st][lane];
                 const float cf = sh.tF[st][lane];
+                float Z[ROWS], fp[ROWS];
 #pragma unroll
                 for (int j = 0; j < ROWS; ++j) {
                     const int rr = warp * ROWS + j;
@@ -1108,9 +1159,10 @@ __global__ void __launch_bounds__(beamform_threads<NF>(),
                     Z[j] = sh.tZ[st][rr];
                     T1[j] = T2[j] = P1[j] = Ti[j] = 0.f;
 #pragma unroll
-                    for (int f = 0; f < NF; ++f)
-                        FT1[f][j] = FT2[f][j] = 0.f;
+                    for (int q = 0; q < NP; ++q)
+                        FT1[q][j] = FT2[q][j] = zero2;
                 }
+                P.set(Z, fp);
             }
             const uint32_t base = smem_u32(stage_base(st));
             const uint32_t vrb = base + (uint32_t)lane * 8;                          // int2 [G][32]
@@ -1129,14 +1181,14 @@ __global__ void __launch_bounds__(beamform_threads<NF>(),
                 for (; k < nf; ++k) {
                     const int c = L[k];
                     accumulate_iq<DMAS, ROWS, false>(win_of(c), wmax, w0_of(c), d2_of(c),
-                                                     make_int2(0, 0), r_first, Z, fp, Kc, c1, c2,
+                                                     make_int2(0, 0), r_first, P, Kc, c1, c2,
                                                      S1, Y1i, T1, Ti);
                 }
 #pragma unroll 1
                 for (; k < nt; ++k) {
                     const int c = L[k];
                     accumulate_iq<DMAS, ROWS, true>(win_of(c), wmax, w0_of(c), d2_of(c), vr_of(c),
-                                                    r_first, Z, fp, Kc, c1, c2, S1, Y1i, T1, Ti);
+                                                    r_first, P, Kc, c1, c2, S1, Y1i, T1, Ti);
                 }
             } else if constexpr (NF > 1) {
                 // every channel once, each delay serving every frame
@@ -1145,13 +1197,13 @@ __global__ void __launch_bounds__(beamform_threads<NF>(),
                     const int c = L[k];
                     accumulate_fn<PREC, DMAS, ROWS, NF, false>(win_of(c), wmax, w0_of(c),
                                                                d2_of(c), make_int2(0, 0), r_first,
-                                                               Z, fp, Kc, FS1, FT1, FT2);
+                                                               P, Kc, FS1p, FT1, FT2);
                 }
 #pragma unroll 1
                 for (; k < nt; ++k) {
                     const int c = L[k];
                     accumulate_fn<PREC, DMAS, ROWS, NF, true>(win_of(c), wmax, w0_of(c), d2_of(c),
-                                                              vr_of(c), r_first, Z, fp, Kc, FS1,
+                                                              vr_of(c), r_first, P, Kc, FS1p,
                                                               FT1, FT2);
                 }
             } else {
@@ -1163,23 +1215,23 @@ __global__ void __launch_bounds__(beamform_threads<NF>(),
                     const int c0 = L[k], c1 = L[k + 1];
                     accumulate2<PREC, DMAS, CF, PDAS, ROWS>(win_of(c0), w0_of(c0), d2_of(c0),
                                                             win_of(c1), w0_of(c1), d2_of(c1), wmax,
-                                                            Z, fp, Kc, S1, T1, T2, Su2, P1, inv_p,
+                                                            P, Kc, S1, T1, T2, Su2, P1, inv_p,
                                                             square);
                 }
                 if (k < nf) {
                     const int c = L[k++];
                     accumulate<PREC, DMAS, CF, PDAS, ROWS, false>(win_of(c), wmax, w0_of(c),
                                                                   d2_of(c), make_int2(0, 0),
-                                                                  r_first, Z, fp, Kc, S1, T1, T2,
+                                                                  r_first, P, Kc, S1, T1, T2,
                                                                   Su2, P1, inv_p, square);
                 }
 #pragma unroll 1
                 for (; k < nt; ++k) {
                     const int c = L[k];
                     accumulate<PREC, DMAS, CF, PDAS, ROWS, true>(win_of(c), wmax, w0_of(c),
-                                                                 d2_of(c), vr_of(c), r_first, Z,
-                                                                 fp, Kc, S1, T1, T2, Su2, P1,
-                                                                 inv_p, square);
+                                                                 d2_of(c), vr_of(c), r_first, P,
+                                                                 Kc, S1, T1, T2, Su2, P1, inv_p,
+                                                                 square);
                 }
             }
             __syncwarp();
@@ -1190,8 +1242,9 @@ __global__ void __launch_bounds__(beamform_threads<NF>(),
                 for (int j = 0; j < ROWS; ++j) {
                     Yd[j] = fmaf(0.5f * T1[j], T1[j], fmaf(-0.5f, T2[j], Yd[j]));
 #pragma unroll
-                    for (int f = 0; f < NF; ++f)
-                        FYd[f][j] = fmaf(0.5f * FT1[f][j], FT1[f][j], fmaf(-0.5f, FT2[f][j], FYd[f][j]));
+                    for (int q = 0; q < NP; ++q)
+                        FYdp[q][j] = fma2(mul2(pk2(0.5f, 0.5f), FT1[q][j]), FT1[q][j],
+                                          fma2(pk2(-0.5f, -0.5f), FT2[q][j], FYdp[q][j]));
                 }
             }
             if (DMAS && IQ && g == ngroups - 1) {  // Eq. (4): ((1/M) sum s^)^2 per angle
@@ -1254,6 +1307,15 @@ __global__ void __launch_bounds__(beamform_threads<NF>(),
         const size_t plane = (size_t)nx * nz;
         float *__restrict__ y = J->y;
         if constexpr (NF > 1) {  // every frame of the job (DAS / DMAS only)
+            // frame f's sums: the low (even f) or high (odd f) half of its pair
+            float FS1[NF][ROWS], FYd[NF][ROWS];
+#pragma unroll
+            for (int q = 0; q < NP; ++q)
+#pragma unroll
+                for (int j = 0; j < ROWS; ++j) {
+                    upk2(FS1p[q][j], FS1[2 * q][j], FS1[2 * q + 1][j]);
+                    upk2(FYdp[q][j], FYd[2 * q][j], FYd[2 * q + 1][j]);
+                }
             if (staged_job(J)) {
                 // the tile's images into the staging area (plane p = frame, then
                 // combiner; column = lane), then the storer warp writes them out
