@@ -206,7 +206,8 @@ BF_API int bf_poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes,
 /* Paper: as bf_submit.  n frames of one geometry, sample count, angle set and
  * flags in one call: rf[k] (host or device) is frame k, tickets_out[k] its
  * ticket.  Every source has been copied when the call returns (one wait for
- * all the copies instead of one per frame).  The engine forms no batch from
+ * all the copies instead of one per frame; device and page-locked sources
+ * move by DMA on several streams).  The engine forms no batch from
  * pending work while the call admits its frames (unless a full batch is
  * pending), so the call's frames ride together.  *n_submitted (optional)
  * receives how many frames got tickets: on BF_EAGAIN the rest can be
@@ -215,14 +216,33 @@ BF_API int bf_submit_many(bf_handle *h, int32_t n, const int16_t *const *rf, int
                           const double *angles_rad, int32_t n_angles, uint32_t mode_and_flags,
                           uint64_t *tickets_out, int32_t *n_submitted);
 
+/* Paper: as bf_submit; the front end's frames stream in while earlier images
+ * leave (Sec. II-A).  bf_submit_many with a destination per frame: outs[k]
+ * (host or device, out_bytes >= bf_output_bytes each) receives frame k's
+ * result as soon as its batch finishes, copied by the batch itself, so that
+ * the transfer of one batch's images overlaps the next batch's kernels
+ * without the caller waiting in between.  Device destinations and host
+ * memory from cudaHostAlloc / cudaMallocHost are written directly; other host
+ * memory through the engine's page-locked staging, copied on by the poll.
+ * Each destination must stay valid and untouched until its ticket is polled:
+ * bf_poll / bf_poll_many then only wait (their out / outs arguments are
+ * ignored for these tickets) and release.  Errors as bf_submit_many, plus
+ * BF_EINVAL for a null or too small destination. */
+BF_API int bf_submit_many_into(bf_handle *h, int32_t n, const int16_t *const *rf,
+                               int32_t n_samples, const double *angles_rad, int32_t n_angles,
+                               uint32_t mode_and_flags, float *const *outs, size_t out_bytes,
+                               uint64_t *tickets_out, int32_t *n_submitted);
+
 /* Paper: as bf_poll.  Waits up to timeout_us for all n tickets, then copies
  * every result into outs[k] (host or device, out_bytes each; outs or outs[k]
  * NULL discards) with one synchronisation at the end and releases every
  * ticket; returns the first failure of any ticket (all are released).  On
- * BF_PENDING / BF_ETIMEDOUT / BF_ENOTFOUND nothing is released.  Device and
- * page-locked host destinations (16-byte aligned) are written by a copy
- * kernel, the latter through their device-mapped address: a host buffer
- * registered read-only for the device must not be an output. */
+ * BF_PENDING / BF_ETIMEDOUT / BF_ENOTFOUND nothing is released.  Device
+ * destinations and host destinations from cudaHostAlloc / cudaMallocHost are
+ * written by one DMA copy each, spread over several streams so that the copy
+ * engines run beside the next batch's kernels; other host memory (pageable,
+ * or registered with cudaHostRegister) goes through the engine's page-locked
+ * staging buffer. */
 BF_API int bf_poll_many(bf_handle *h, int32_t n, const uint64_t *tickets, float *const *outs,
                         size_t out_bytes, int64_t timeout_us);
 

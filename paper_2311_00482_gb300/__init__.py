@@ -33,7 +33,7 @@ _NAMES = {-1: "BF_EINVAL", -2: "BF_EAGAIN", -3: "BF_ENOMEM", -4: "BF_ECUDA", -5:
 EXPORTED = ("bf_create", "bf_destroy", "bf_set_stream", "bf_set_pdas_order", "bf_output_bytes",
             "bf_beamform",
             "bf_beamform_plain", "bf_fkmig",
-            "bf_submit", "bf_poll", "bf_submit_many", "bf_poll_many", "bf_ticket_batch", "bf_ticket_times", "bf_engine_pause",
+            "bf_submit", "bf_poll", "bf_submit_many", "bf_submit_many_into", "bf_poll_many", "bf_ticket_batch", "bf_ticket_times", "bf_engine_pause",
             "bf_engine_configure", "bf_sync",
             "bf_batch_create", "bf_batch_launch", "bf_batch_status", "bf_batch_timing",
             "bf_batch_destroy",
@@ -95,6 +95,9 @@ def load(path: str | None = None):
         "bf_poll": ([vp, u64, vp, ctypes.c_size_t, i64], ctypes.c_int),
         "bf_submit_many": ([vp, i32, ctypes.POINTER(vp), i32, dp, i32, u32, ctypes.POINTER(u64),
                             ctypes.POINTER(i32)], ctypes.c_int),
+        "bf_submit_many_into": ([vp, i32, ctypes.POINTER(vp), i32, dp, i32, u32, ctypes.POINTER(vp),
+                                 ctypes.c_size_t, ctypes.POINTER(u64), ctypes.POINTER(i32)],
+                                ctypes.c_int),
         "bf_poll_many": ([vp, i32, ctypes.POINTER(u64), ctypes.POINTER(vp), ctypes.c_size_t, i64],
                          ctypes.c_int),
         "bf_ticket_batch": ([vp, u64, ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
@@ -300,6 +303,29 @@ def bf_submit_many(h, rfs, n_samples, angles_rad, flags):
     done = ctypes.c_int32()
     rc = load().bf_submit_many(h, n, ptrs, int(n_samples), ap, len(a), int(flags), t,
                                ctypes.byref(done))
+    if rc != BF_OK:
+        err = BFError(rc, bf_last_error())
+        err.submitted = [t[k] for k in range(done.value)]
+        raise err
+    return [t[k] for k in range(n)]
+
+
+def bf_submit_many_into(h, rfs, n_samples, angles_rad, flags, outs):
+    """bf_submit_many with a destination per frame (see include/bf.h): each result
+    lands in outs[k] when its batch finishes; poll the tickets (without outs) to
+    wait for them and release them."""
+    a, ap = _angles(angles_rad)
+    n = len(rfs)
+    if len(outs) != n:
+        raise ValueError("one destination per frame")
+    ptrs = (ctypes.c_void_p * n)(*[_ptr(r) for r in rfs])
+    optr = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
+    nbytes = min((o.nbytes if isinstance(o, np.ndarray) else o.numel() * o.element_size())
+                 for o in outs) if n else 0
+    t = (ctypes.c_uint64 * n)()
+    done = ctypes.c_int32()
+    rc = load().bf_submit_many_into(h, n, ptrs, int(n_samples), ap, len(a), int(flags), optr,
+                                    nbytes, t, ctypes.byref(done))
     if rc != BF_OK:
         err = BFError(rc, bf_last_error())
         err.submitted = [t[k] for k in range(done.value)]

@@ -133,49 +133,26 @@ private:
     std::deque<Job *> q_;
 };
 
-enum PtrKind { kPageable = 0, kPinned = 1, kDevice = 2 };
+// Streams of the batched transfers (bf_submit_many, bf_poll_many): copies
+// spread over them run on several copy engines at once.
+constexpr int kXferStreams = 4;
 
-// CTAs per frame of the batched copy kernels (records in, images out).
-constexpr int kCopyBlocksIn = 2, kCopyBlocksOut = 1;
-
-// dev (optional): an address of the memory a copy kernel on `device` may use
-// (device memory of that device, or the device-mapped address of page-locked
-// host memory; for a buffer the kernel writes, only memory from
-// cudaHostAlloc, since registered memory may be read-only for the device),
-// else null, and the caller takes the cudaMemcpyAsync path.
-PtrKind pointer_kind(const void *p, int device, void **dev = nullptr, bool write = false)
+// How a caller's buffer moves (see copy_route); write: the copy writes it.
+CopyRoute route_of(const void *p, bool write)
 {
-    if (dev)
-        *dev = nullptr;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return kPageable;
+        return CopyRoute::kStaged;
     }
-    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
-        if (dev)
-            *dev = kernel_address(a, p, device, device, write, false);
-        return kDevice;
+    bool host_alloc = false;
+    if (a.type == cudaMemoryTypeHost && write) {
+        unsigned flags = 0;
+        host_alloc = cudaHostGetFlags(&flags, const_cast<void *>(p)) == cudaSuccess;
+        if (!host_alloc)
+            cudaGetLastError();
     }
-    if (a.type == cudaMemoryTypeHost) {
-        if (dev) {
-            int current = -1;
-            if (cudaGetDevice(&current) != cudaSuccess) {
-                cudaGetLastError();
-                current = -1;
-            }
-            bool host_alloc = false;
-            if (write) {
-                unsigned flags = 0;
-                host_alloc = cudaHostGetFlags(&flags, const_cast<void *>(p)) == cudaSuccess;
-                if (!host_alloc)
-                    cudaGetLastError();
-            }
-            *dev = kernel_address(a, p, device, current, write, host_alloc);
-        }
-        return kPinned;
-    }
-    return kPageable;
+    return copy_route(a.type, host_alloc, write);
 }
 
 // Page-locked host buffer that grows on demand (contents not kept).
@@ -290,6 +267,11 @@ struct Request {
     std::unique_ptr<Slot> slot;
     FramePrep fp;
     size_t out_bytes = 0;
+    // destination given at submission (bf_submit_many_into): the batch itself
+    // copies the result there (or, for a staged route, into the slot's pinned
+    // staging, which the poll copies on); null otherwise
+    float *dest = nullptr;
+    bool dest_staged = false;
     std::shared_ptr<Batch> batch;
     int state = 0;  // 0 queued, 1 launched, 2 failed to launch
     int rc = BF_OK;
@@ -307,6 +289,10 @@ public:
             cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
         cudaStreamCreateWithFlags(&copy_, cudaStreamNonBlocking);
         cudaStreamCreateWithFlags(&d2h_, cudaStreamNonBlocking);
+        for (int i = 0; i < kXferStreams; ++i) {
+            cudaStreamCreateWithFlags(&xin_[i], cudaStreamNonBlocking);
+            cudaStreamCreateWithFlags(&xout_[i], cudaStreamNonBlocking);
+        }
         size_t fr = 0, tot = 0;
         cudaMemGetInfo(&fr, &tot);
         budget_ = tot / 2;
@@ -318,17 +304,19 @@ public:
         worker_.detach();  // lives for the process
     }
 
-    // A request whose RF copy bf_submit_many batches into one kernel.
+    // A request whose RF copy bf_submit_many issues with the call's others.
     struct Deferred {
         std::shared_ptr<Request> req;
-        CopySeg seg;
+        const void *src;
+        size_t bytes;
     };
     // defer (bf_submit_many): a device or pinned source is not copied here; the
-    // request gets its ticket but is queued by flush() once the batched copy is
+    // request gets its ticket but is queued by flush() once its copy is
     // enqueued.  Other sources are copied (and queued) at once.
+    // dest (optional): where the batch delivers the result (see Request::dest).
     int submit(bf_handle *h, const int16_t *rf, int ns, const double *angles, int na,
                uint32_t flags, uint64_t *ticket, bool wait_copy = true,
-               std::vector<Deferred> *defer = nullptr);
+               std::vector<Deferred> *defer = nullptr, float *dest = nullptr);
     int flush(std::vector<Deferred> &defer);
     int poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes, int64_t timeout_us);
     int poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const *outs, size_t out_bytes,
@@ -338,6 +326,8 @@ public:
     {
         cudaSetDevice(device_);
         cudaError_t e = cudaStreamSynchronize(copy_);
+        for (int i = 0; i < kXferStreams && e == cudaSuccess; ++i)
+            e = cudaStreamSynchronize(xin_[i]);
         return e == cudaSuccess ? BF_OK : cuda_fail(e, "copying the requests' RF");
     }
     int batch_of(bf_handle *h, uint64_t ticket, int *id, int *frames);
@@ -394,6 +384,7 @@ private:
     int next_batch_ = 0;
     cudaStream_t streams_[kStreams]{};
     cudaStream_t copy_ = nullptr, d2h_ = nullptr;
+    cudaStream_t xin_[kXferStreams] = {}, xout_[kXferStreams] = {};
     std::thread worker_;
     ResPool res_pool_;
 };
@@ -411,7 +402,8 @@ std::unique_ptr<Slot> Engine::take_slot()
 }
 
 int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles, int na,
-                   uint32_t flags, uint64_t *ticket, bool wait_copy, std::vector<Deferred> *defer)
+                   uint32_t flags, uint64_t *ticket, bool wait_copy, std::vector<Deferred> *defer,
+                   float *dest)
 {
     int rc = check_frame_args(h, ns, angles, na, flags);
     if (rc)
@@ -423,6 +415,8 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
     auto req = std::make_shared<Request>();
     req->h = h;
     req->out_bytes = out_bytes;
+    req->dest = dest;
+    req->dest_staged = dest && route_of(dest, true) != CopyRoute::kDirect;
     {
         std::lock_guard<std::mutex> lk(mu_);
         if (live_ >= max_live_)
@@ -477,6 +471,8 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
     rc = s.rf.ensure(rf_bytes);
     if (!rc)
         rc = s.out.ensure(out_bytes);
+    if (!rc && req->dest_staged && !s.pin_out.ensure(out_bytes))
+        rc = fail(BF_ENOMEM, "page-locked staging of %zu bytes", out_bytes);
     if (!rc && !s.h2d && cudaEventCreateWithFlags(&s.h2d, cudaEventDisableTiming) != cudaSuccess)
         rc = fail(BF_ECUDA, "cudaEventCreate");
     if (!rc)
@@ -496,11 +492,10 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
     // caller's buffer (waited for: the caller may reuse it on return),
     // pageable host data through the slot's pinned staging.
     cudaError_t e;
-    void *rf_dev = nullptr;
-    const PtrKind kind = pointer_kind(rf, device_, &rf_dev);
+    const CopyRoute route = route_of(rf, false);
     const bool inject = fault_injected("copy");
-    if (defer && !inject && rf_dev && copy_segment_ok(rf_dev, s.rf.p, rf_bytes)) {
-        // batched with the call's other frames: registered now, queued by flush()
+    if (defer && !inject && route == CopyRoute::kDirect) {
+        // copied with the call's other frames: registered now, queued by flush()
         {
             std::lock_guard<std::mutex> lk(mu_);
             const size_t grow = need > before ? need - before : 0;
@@ -513,13 +508,13 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
             std::lock_guard<std::mutex> lk(h->mu);
             h->tickets[req->ticket] = req;
         }
-        defer->push_back(Deferred{req, CopySeg{rf_dev, s.rf.p, (unsigned long long)rf_bytes}});
+        defer->push_back(Deferred{req, rf, rf_bytes});
         *ticket = req->ticket;
         return BF_OK;
     }
     if (inject) {
         e = cudaErrorUnknown;  // stands for a failed copy; no CUDA call is made
-    } else if (kind != kPageable) {
+    } else if (route == CopyRoute::kDirect) {
         e = cudaMemcpyAsync(s.rf.p, rf, rf_bytes, cudaMemcpyDefault, copy_);
     } else if (!s.pin_in.ensure(rf_bytes)) {
         e = cudaErrorMemoryAllocation;
@@ -529,7 +524,7 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
     }
     if (e == cudaSuccess)
         e = cudaEventRecord(s.h2d, copy_);
-    if (e == cudaSuccess && kind != kPageable && wait_copy)
+    if (e == cudaSuccess && route == CopyRoute::kDirect && wait_copy)
         e = cudaEventSynchronize(s.h2d);
     {
         std::lock_guard<std::mutex> lk(mu_);
@@ -561,20 +556,19 @@ int Engine::flush(std::vector<Deferred> &defer)
         return BF_OK;
     cudaSetDevice(device_);
     cudaError_t e = cudaSuccess;
-    for (size_t i = 0; i < defer.size() && e == cudaSuccess; i += kMaxCopySegs) {
-        CopyList l{};
-        l.n = (int)std::min<size_t>(kMaxCopySegs, defer.size() - i);
-        for (int k = 0; k < l.n; ++k)
-            l.seg[k] = defer[i + k].seg;
-        e = launch_copy_segments(l, kCopyBlocksIn, copy_);
-    }
-    for (auto &d : defer)  // each slot's copy is done when the batched copies are
+    // one DMA per frame, spread over the transfer streams; each slot's copy
+    // event follows its own copy
+    for (size_t i = 0; i < defer.size() && e == cudaSuccess; ++i) {
+        Deferred &d = defer[i];
+        cudaStream_t st = xin_[i % kXferStreams];
+        e = cudaMemcpyAsync(d.req->slot->rf.p, d.src, d.bytes, cudaMemcpyDefault, st);
         if (e == cudaSuccess)
-            e = cudaEventRecord(d.req->slot->h2d, copy_);
+            e = cudaEventRecord(d.req->slot->h2d, st);
+    }
     std::string msg;
     int rc = BF_OK;
     if (e != cudaSuccess) {
-        rc = cuda_fail(e, "batched RF copy");
+        rc = cuda_fail(e, "RF copy");
         msg = bf_last_error();
     }
     {
@@ -624,6 +618,16 @@ void Engine::launch(std::vector<std::shared_ptr<Request>> &reqs)
         cudaEventRecord(R.start, st);
     if (!rc)
         rc = enqueue(frames, hl, R.dl, st);
+    // results with a destination leave with the batch (a copy engine moves them
+    // while the next batch's kernels run)
+    for (size_t i = 0; i < reqs.size() && !rc; ++i) {
+        Request &q = *reqs[i];
+        if (!q.dest)
+            continue;
+        void *to = q.dest_staged ? q.slot->pin_out.p : (void *)q.dest;
+        if (cudaMemcpyAsync(to, q.slot->out.p, q.out_bytes, cudaMemcpyDefault, st) != cudaSuccess)
+            rc = fail(BF_ECUDA, "cudaMemcpyAsync (result to its destination)");
+    }
     // the status word travels back with the batch: polls read it without a sync
     if (!rc && cudaMemcpyAsync(R.err_host, R.dl.err.p, sizeof(int), cudaMemcpyDeviceToHost, st) !=
                    cudaSuccess)
@@ -734,10 +738,13 @@ int Engine::poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes, in
         else if (v)
             rc = fail(BF_ECUDA, "device-side check failed (status 0x%x)", v);
     }
-    if (!rc && out) {
+    if (!rc && req->dest) {  // delivered by the batch (staged: from pinned staging)
+        if (req->dest_staged)
+            CopyPool::get().copy(req->dest, req->slot->pin_out.p, req->out_bytes);
+    } else if (!rc && out) {
         Slot &s = *req->slot;
         cudaError_t e;
-        if (pointer_kind(out, device_) != kPageable) {
+        if (route_of(out, true) == CopyRoute::kDirect) {
             e = cudaMemcpyAsync(out, s.out.p, req->out_bytes, cudaMemcpyDefault, d2h_);
             if (e == cudaSuccess)
                 e = cudaStreamSynchronize(d2h_);
@@ -779,7 +786,7 @@ int Engine::poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const
             if (it == h->tickets.end())
                 return fail(BF_ENOTFOUND, "unknown ticket %llu", (unsigned long long)tickets[k]);
             reqs[k] = it->second;
-            if (outs && outs[k] && out_bytes < reqs[k]->out_bytes)
+            if (!reqs[k]->dest && outs && outs[k] && out_bytes < reqs[k]->out_bytes)
                 return fail(BF_EINVAL, "output buffer too small (%zu < %zu bytes)", out_bytes,
                             reqs[k]->out_bytes);
         }
@@ -820,24 +827,11 @@ int Engine::poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const
     cudaSetDevice(device_);
     int rc = BF_OK;
     std::vector<int> staged;
-    // device and pinned destinations: the images leave in batched copy kernels
-    // (falling back to one copy per image if a launch fails)
-    CopyList list{};
-    std::vector<std::pair<float *, int>> listed;  // (destination, request) of list's segments
-    auto launch_list = [&]() -> cudaError_t {
-        cudaError_t le = launch_copy_segments(list, kCopyBlocksOut, d2h_);
-        if (le != cudaSuccess) {
-            cudaGetLastError();
-            le = cudaSuccess;
-            for (auto &dk : listed)
-                if (le == cudaSuccess)
-                    le = cudaMemcpyAsync(dk.first, reqs[dk.second]->slot->out.p,
-                                         reqs[dk.second]->out_bytes, cudaMemcpyDefault, d2h_);
-        }
-        list.n = 0;
-        listed.clear();
-        return le;
-    };
+    // device and pinned destinations: one DMA per image, spread over the
+    // transfer streams (copy engines run beside the next batch's kernels);
+    // the rest through the slots' pinned staging
+    int direct = 0;
+    std::vector<int> staged_dest;  // results the batch left in pinned staging
     for (int k = 0; k < n; ++k) {
         Request &r = *reqs[k];
         int rk = r.rc ? fail(r.rc, "%s", r.err.c_str()) : BF_OK;
@@ -852,19 +846,15 @@ int Engine::poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const
                 rk = fail(v & kErrTimeout ? BF_ETIMEDOUT : BF_ECUDA,
                           "device-side failure in a batch (status 0x%x)", v);
         }
-        float *out = outs ? outs[k] : nullptr;
+        float *out = r.dest ? nullptr : (outs ? outs[k] : nullptr);
+        if (!rk && r.dest && r.dest_staged)  // delivered by the batch into pinned staging
+            staged_dest.push_back(k);
         if (!rk && out) {
             Slot &s = *r.slot;
             cudaError_t e = cudaSuccess;
-            void *out_dev = nullptr;
-            const PtrKind kind = pointer_kind(out, device_, &out_dev, true);
-            if (out_dev && copy_segment_ok(s.out.p, out_dev, r.out_bytes)) {
-                list.seg[list.n++] = CopySeg{s.out.p, out_dev, (unsigned long long)r.out_bytes};
-                listed.emplace_back(out, k);
-                if (list.n == kMaxCopySegs)
-                    e = launch_list();
-            } else if (kind != kPageable) {
-                e = cudaMemcpyAsync(out, s.out.p, r.out_bytes, cudaMemcpyDefault, d2h_);
+            if (route_of(out, true) == CopyRoute::kDirect) {
+                e = cudaMemcpyAsync(out, s.out.p, r.out_bytes, cudaMemcpyDefault,
+                                    xout_[direct++ % kXferStreams]);
             } else if (!s.pin_out.ensure(r.out_bytes)) {
                 e = cudaErrorMemoryAllocation;
             } else {
@@ -877,15 +867,17 @@ int Engine::poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const
         if (rk && !rc)
             rc = rk;
     }
-    cudaError_t e = list.n ? launch_list() : cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(d2h_);
+    for (int i = 0; i < kXferStreams && e == cudaSuccess; ++i)
+        e = cudaStreamSynchronize(xout_[i]);
     if (e != cudaSuccess && !rc)
         rc = cuda_fail(e, "copying the results");
-    e = cudaStreamSynchronize(d2h_);
-    if (e != cudaSuccess && !rc)
-        rc = cuda_fail(e, "copying the results");
-    if (e == cudaSuccess)
+    if (e == cudaSuccess) {
         for (int k : staged)
             CopyPool::get().copy(outs[k], reqs[k]->slot->pin_out.p, reqs[k]->out_bytes);
+        for (int k : staged_dest)
+            CopyPool::get().copy(reqs[k]->dest, reqs[k]->slot->pin_out.p, reqs[k]->out_bytes);
+    }
     {
         std::lock_guard<std::mutex> lk(h->mu);
         for (int k = 0; k < n; ++k)
@@ -990,14 +982,24 @@ BF_API int bf_poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes, 
     return engine_for(h->device)->poll(h, ticket, out, out_bytes, timeout_us);
 }
 
-BF_API int bf_submit_many(bf_handle *h, int32_t n, const int16_t *const *rf, int32_t n_samples,
-                          const double *angles_rad, int32_t n_angles, uint32_t flags,
-                          uint64_t *tickets_out, int32_t *n_submitted)
+static int submit_many(bf_handle *h, int32_t n, const int16_t *const *rf, int32_t n_samples,
+                       const double *angles_rad, int32_t n_angles, uint32_t flags,
+                       float *const *outs, size_t out_bytes, uint64_t *tickets_out,
+                       int32_t *n_submitted)
 {
     if (!h || !rf || !tickets_out || n < 0)
         return fail(BF_EINVAL, "null argument");
     if (n_submitted)
         *n_submitted = 0;
+    if (outs) {
+        const size_t need = frame_out_bytes(h, flags);
+        for (int k = 0; k < n; ++k) {
+            if (!outs[k])
+                return fail(BF_EINVAL, "null destination %d", k);
+            if (out_bytes < need)
+                return fail(BF_EINVAL, "destination too small (%zu < %zu bytes)", out_bytes, need);
+        }
+    }
     cudaSetDevice(h->device);
     Engine *eng = engine_for(h->device);
     struct Hold {  // the call's frames form their batches together
@@ -1008,14 +1010,14 @@ BF_API int bf_submit_many(bf_handle *h, int32_t n, const int16_t *const *rf, int
     int rc = BF_OK, k = 0;
     {
         Hold hold(eng);  // released once every frame is admitted (copies may still run)
-        std::vector<Engine::Deferred> defer;  // device and pinned sources: one batched copy
+        std::vector<Engine::Deferred> defer;  // device and pinned sources: DMA per frame
         for (; k < n; ++k) {
             if (!rf[k]) {
                 rc = fail(BF_EINVAL, "null record pointer %d", k);
                 break;
             }
             rc = eng->submit(h, rf[k], n_samples, angles_rad, n_angles, flags, tickets_out + k,
-                             false, &defer);
+                             false, &defer, outs ? outs[k] : nullptr);
             if (rc)
                 break;
         }
@@ -1027,6 +1029,25 @@ BF_API int bf_submit_many(bf_handle *h, int32_t n, const int16_t *const *rf, int
         *n_submitted = k;
     const int rw = eng->wait_copies();  // every submitted source copied before returning
     return rc ? rc : rw;
+}
+
+BF_API int bf_submit_many(bf_handle *h, int32_t n, const int16_t *const *rf, int32_t n_samples,
+                          const double *angles_rad, int32_t n_angles, uint32_t mode_and_flags,
+                          uint64_t *tickets_out, int32_t *n_submitted)
+{
+    return submit_many(h, n, rf, n_samples, angles_rad, n_angles, mode_and_flags, nullptr, 0,
+                       tickets_out, n_submitted);
+}
+
+BF_API int bf_submit_many_into(bf_handle *h, int32_t n, const int16_t *const *rf,
+                               int32_t n_samples, const double *angles_rad, int32_t n_angles,
+                               uint32_t mode_and_flags, float *const *outs, size_t out_bytes,
+                               uint64_t *tickets_out, int32_t *n_submitted)
+{
+    if (!outs)
+        return fail(BF_EINVAL, "null destinations");
+    return submit_many(h, n, rf, n_samples, angles_rad, n_angles, mode_and_flags, outs, out_bytes,
+                       tickets_out, n_submitted);
 }
 
 BF_API int bf_poll_many(bf_handle *h, int32_t n, const uint64_t *tickets, float *const *outs,

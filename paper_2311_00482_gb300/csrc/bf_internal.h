@@ -182,24 +182,6 @@ struct LogJob {
 cudaError_t kernel_setup(const void *k, size_t smem, int threads, bool max_carveout, int *sms,
                          int *occ);
 
-// Batched copies (bf_copy.cu): up to kMaxCopySegs segments per launch, each
-// with device-usable addresses (device memory, or the device-mapped address of
-// pinned host memory), 16-byte aligned, a multiple of 16 bytes long.
-struct CopySeg {
-    const void *src;
-    void *dst;
-    unsigned long long bytes;
-};
-constexpr int kMaxCopySegs = 64;
-struct CopyList {  // passed by value as a kernel parameter (1.5 KB)
-    CopySeg seg[kMaxCopySegs];
-    int n;
-};
-bool copy_segment_ok(const void *src, const void *dst, size_t bytes);
-// blocks_per_seg CTAs of 256 threads per segment: few, so that copies running
-// beside a batch's kernels take few SMs (the host link, not the SMs, bounds them)
-cudaError_t launch_copy_segments(const CopyList &list, int blocks_per_seg, cudaStream_t stream);
-
 // Kernel launchers (bf_kernels.cu).  All enqueue on `stream` and return the
 // launch status.  `variant` holds the BF_DMAS / BF_CF bits the launch computes
 // (all its jobs must share them, the precision and the rows per thread);

@@ -1,37 +1,33 @@
-// Which address a copy kernel of the serving engine may use for a buffer the
-// caller passed (RF records in, images out), decided from what
-// cudaPointerGetAttributes reported.  Header-only and free of CUDA calls, so
-// that the decision can be checked on a machine without a GPU.
+// How the serving engine moves a caller's buffer (RF records in, images out),
+// decided from what cudaPointerGetAttributes and cudaHostGetFlags reported.
+// Header-only and free of CUDA calls, so that the decision can be checked on a
+// machine without a GPU.
 #pragma once
 
 #include <cuda_runtime.h>
 
 namespace bfi {
 
-// a: the buffer's attributes; p: the caller's pointer; device: the engine's
-// device (where the copy kernel runs); current: the device that was current
-// when `a` was taken (a.devicePointer is valid there only); write: the kernel
-// would write the buffer; host_alloc: a page-locked host buffer came from
+// Direct: one cudaMemcpyAsync between the buffer and the engine's slot (a copy
+// engine moves it, beside whatever kernels run).  Staged: through the slot's
+// page-locked staging buffer and a host memcpy.
+enum class CopyRoute { kDirect, kStaged };
+
+// type: the buffer's memory type; host_alloc: page-locked host memory from
 // cudaHostAlloc / cudaMallocHost (cudaHostGetFlags succeeded), as opposed to
-// memory registered with cudaHostRegister, which may be read-only for the
-// device.  Returns the address to use, or null when the buffer must take the
-// cudaMemcpyAsync path instead:
-//   device memory of another device (no peer access is set up);
-//   page-locked host memory without a mapping on the engine's device;
-//   registered host memory the kernel would write.
-inline void *kernel_address(const cudaPointerAttributes &a, const void *p, int device, int current,
-                            bool write, bool host_alloc)
+// memory registered with cudaHostRegister, which may be registered read-only
+// for the device; write: the copy writes the buffer.
+//   device memory (of any device: cudaMemcpyDefault copies across devices)
+//   and page-locked host memory are read directly;
+//   they are written directly too, except registered host memory;
+//   pageable (unregistered) and managed memory go through the staging buffer.
+inline CopyRoute copy_route(cudaMemoryType type, bool host_alloc, bool write)
 {
-    if (a.type == cudaMemoryTypeDevice)
-        return a.device == device ? const_cast<void *>(p) : nullptr;
-    if (a.type == cudaMemoryTypeHost) {
-        if (current != device || a.devicePointer == nullptr)
-            return nullptr;
-        if (write && !host_alloc)
-            return nullptr;
-        return a.devicePointer;
-    }
-    return nullptr;  // managed or unregistered memory
+    if (type == cudaMemoryTypeDevice)
+        return CopyRoute::kDirect;
+    if (type == cudaMemoryTypeHost)
+        return (!write || host_alloc) ? CopyRoute::kDirect : CopyRoute::kStaged;
+    return CopyRoute::kStaged;
 }
 
 }  // namespace bfi

@@ -494,3 +494,46 @@ def test_two_row_tiles_leave_other_combiners_on_the_default(torch, monkeypatch):
         assert_close(got[1], ref["cf"], bf.BF_PREC_FP32, "cf")
     finally:
         bf.bf_destroy(h)
+
+
+def test_submit_many_into_delivers_to_every_destination_kind(torch):
+    """Results delivered by the batches themselves to destinations given at
+    submission: pinned, pageable and device buffers; every one equals the
+    frame beamformed alone, and polling (without outputs) releases the tickets."""
+    acq = synth.SPECKLE_POINTS_128.with_(nx=48, nz=80)
+    flags = bf.BF_DAS | bf.BF_DMAS | bf.BF_OUT_LOGDB
+    rfs = [synth.speckle_points_frame(acq, seed=synth.BASE_SEED + 360 + k)[0] for k in range(6)]
+    h = make_handle(acq)
+    try:
+        solo = [run_gpu(torch, acq, rf, flags, h=h) for rf in rfs]
+        srcs = [torch.from_numpy(rfs[0]).pin_memory(), rfs[1], torch.from_numpy(rfs[2]).cuda(),
+                torch.from_numpy(rfs[3]).pin_memory(), rfs[4], torch.from_numpy(rfs[5]).cuda()]
+        outs = [torch.full((2, acq.nx, acq.nz), float("nan")).pin_memory(),
+                np.full((2, acq.nx, acq.nz), np.nan, np.float32),
+                torch.full((2, acq.nx, acq.nz), float("nan"), device="cuda"),
+                torch.full((2, acq.nx, acq.nz), float("nan"), device="cuda"),
+                torch.full((2, acq.nx, acq.nz), float("nan")).pin_memory(),
+                np.full((2, acq.nx, acq.nz), np.nan, np.float32)]
+        for _ in range(2):  # the second round reuses the released slots
+            tickets = bf.bf_submit_many_into(h, srcs, acq.n_samples, acq.angles_rad, flags, outs)
+            assert bf.bf_poll_many(h, tickets, None, timeout_us=30_000_000) == bf.BF_OK
+            for o, ref in zip(outs, solo):
+                got = o if isinstance(o, np.ndarray) else o.cpu().numpy()
+                np.testing.assert_allclose(got, ref, atol=2e-3)
+            with pytest.raises(bf.BFError):  # released
+                bf.bf_poll(h, tickets[0], None, timeout_us=0)
+            for o in outs:
+                o.fill_(float("nan")) if not isinstance(o, np.ndarray) else o.fill(np.nan)
+        # single polls release such tickets too
+        tickets = bf.bf_submit_many_into(h, srcs[:2], acq.n_samples, acq.angles_rad, flags, outs[:2])
+        for t in tickets:
+            assert bf.bf_poll(h, t, None, timeout_us=30_000_000) == bf.BF_OK
+        for o, ref in zip(outs[:2], solo[:2]):
+            got = o if isinstance(o, np.ndarray) else o.cpu().numpy()
+            np.testing.assert_allclose(got, ref, atol=2e-3)
+        small = [torch.zeros(4)]
+        with pytest.raises(bf.BFError) as ei:
+            bf.bf_submit_many_into(h, srcs[:1], acq.n_samples, acq.angles_rad, flags, small)
+        assert ei.value.code == bf.BF_EINVAL
+    finally:
+        bf.bf_destroy(h)
