@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libbf.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["bf_kernels.cu", "bf_static.cu"]
+CU_SOURCES = ["bf_kernels.cu", "bf_envelope.cu", "bf_static.cu"]
 CPP_SOURCES = ["bf_api.cpp", "bf_engine.cpp", "bf_tables.cpp"]
 
 

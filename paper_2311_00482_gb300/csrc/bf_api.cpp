@@ -743,10 +743,16 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
                       ((uintptr_t)e.env & 15) == 0)
                          ? 1
                          : 0;
-            hl.env_prefix.push_back(cols);
-            cols += (h->g.nx + e.cols_per_block - 1) / e.cols_per_block;
-            hl.env.push_back(e);
-            hl.env_smem = std::max(hl.env_smem, envelope_smem_bytes(e.fft_m, e.bluestein));
+            if (envelope_warp_ok(e.nz, e.fft_m, e.bluestein)) {
+                hl.envw_prefix.push_back(hl.envw_pairs);
+                hl.envw_pairs += (h->g.nx + 1) / 2;
+                hl.envw.push_back(e);
+            } else {
+                hl.env_prefix.push_back(cols);
+                cols += (h->g.nx + e.cols_per_block - 1) / e.cols_per_block;
+                hl.env.push_back(e);
+                hl.env_smem = std::max(hl.env_smem, envelope_smem_bytes(e.fft_m, e.bluestein));
+            }
             if (f.stage == BF_OUT_LOGDB) {
                 LogJob l{};
                 l.env = e.env;
@@ -785,6 +791,8 @@ int DeviceLaunch::upload(const HostLaunch &hl, cudaStream_t st, bool async)
     if (!rc) rc = put(ingest_prefix, hl.ingest_prefix.data(), hl.ingest_prefix.size() * sizeof(int));
     if (!rc) rc = put(env, hl.env.data(), hl.env.size() * sizeof(EnvJob));
     if (!rc) rc = put(env_prefix, hl.env_prefix.data(), hl.env_prefix.size() * sizeof(int));
+    if (!rc) rc = put(envw, hl.envw.data(), hl.envw.size() * sizeof(EnvJob));
+    if (!rc) rc = put(envw_prefix, hl.envw_prefix.data(), hl.envw_prefix.size() * sizeof(int));
     if (!rc) rc = put(log, hl.log.data(), hl.log.size() * sizeof(LogJob));
     if (!rc) rc = put(blk_prefix, hl.blk_prefix.data(), hl.blk_prefix.size() * sizeof(int));
     if (!rc) rc = put(demod, hl.demod.data(), hl.demod.size() * sizeof(DemodJob));
@@ -871,6 +879,12 @@ int enqueue(const std::vector<FramePrep> &frames, const HostLaunch &hl, DeviceLa
     if (!hl.env.empty()) {
         e = launch_envelope((const EnvJob *)dl.env.p, (const int *)dl.env_prefix.p, (int)hl.env.size(),
                             hl.env_blocks, hl.env_smem, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "envelope launch");
+    }
+    if (!hl.envw.empty()) {
+        e = launch_envelope_warp((const EnvJob *)dl.envw.p, (const int *)dl.envw_prefix.p,
+                                 (int)hl.envw.size(), hl.envw_pairs, st);
         if (e != cudaSuccess)
             return cuda_fail(e, "envelope launch");
     }
@@ -1287,6 +1301,13 @@ BF_API int bf_beamform_plain(bf_handle *h, const int16_t *rf_dev, int32_t n_samp
         if (e != cudaSuccess)
             rc = cuda_fail(e, "envelope launch");
     }
+    if (!rc && !hl.envw.empty()) {
+        e = launch_envelope_warp((const EnvJob *)h->launch.envw.p,
+                                 (const int *)h->launch.envw_prefix.p, (int)hl.envw.size(),
+                                 hl.envw_pairs, h->stream);
+        if (e != cudaSuccess)
+            rc = cuda_fail(e, "envelope launch");
+    }
     if (!rc && !hl.log.empty()) {
         e = launch_log((const LogJob *)h->launch.log.p, (const int *)h->launch.blk_prefix.p,
                        (int)hl.log.size(), hl.log_blocks, 70.0f, h->stream);
@@ -1526,7 +1547,8 @@ BF_API int bf_batch_create(const bf_frame *frames, int32_t n, bf_batch **out)
         if (e == cudaSuccess)
             e = cudaEventCreate(&m);
     b->launches = (int)b->hl.igroups.size() + (b->hl.demod.empty() ? 0 : 1) +
-                  (int)b->hl.groups.size() + (b->hl.env.empty() ? 0 : 1) + (b->hl.log.empty() ? 0 : 1);
+                  (int)b->hl.groups.size() + (b->hl.env.empty() ? 0 : 1) + (b->hl.envw.empty() ? 0 : 1) +
+                  (b->hl.log.empty() ? 0 : 1);
     if (e == cudaSuccess)
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {

@@ -145,6 +145,10 @@ struct HostLaunch {
     std::vector<int> env_prefix;
     int env_blocks = 0;
     size_t env_smem = 0;
+    // 512-row images: the warp-per-column-pair envelope kernel (column pairs)
+    std::vector<EnvJob> envw;
+    std::vector<int> envw_prefix;
+    int envw_pairs = 0;
     std::vector<LogJob> log;
     std::vector<int> blk_prefix;
     int log_blocks = 0;
@@ -155,6 +159,7 @@ struct HostLaunch {
 
 struct DeviceLaunch {
     DevMem jobs, tile_prefix, ingest, ingest_prefix, env, env_prefix, log, blk_prefix, err;
+    DevMem envw, envw_prefix;
     DevMem demod, demod_prefix;
     int upload(const HostLaunch &hl, cudaStream_t st, bool async);
 };

@@ -205,6 +205,12 @@ cudaError_t launch_envelope(const EnvJob *jobs_dev, const int *blk_prefix_dev, i
                             int total_blocks, size_t smem_bytes, cudaStream_t stream);
 cudaError_t launch_log(const LogJob *jobs_dev, const int *blk_prefix_dev, int njobs,
                        int total_blocks, float dynamic_range_db, cudaStream_t stream);
+// Envelope of 512-row images by the warp-per-column-pair kernel (bf_envelope.cu):
+// the jobs it takes (power-of-two depth of 512, no Bluestein), and its launch
+// over total_pairs column pairs (pair_prefix_dev: each job's first pair).
+bool envelope_warp_ok(int nz, int fft_m, int bluestein);
+cudaError_t launch_envelope_warp(const EnvJob *jobs_dev, const int *pair_prefix_dev, int njobs,
+                                 int total_pairs, cudaStream_t stream);
 // One frame through the plain baseline kernel (FP32, global loads, one thread
 // per pixel); job.y receives the beamformed modes.
 cudaError_t launch_plain(const BfJob &job, const int16_t *rf, const int2 *valid, const float *dx2,
