@@ -164,14 +164,22 @@ void angle_tables(const GeomHost &g, const GeometryHost &geo, int ns,
             out.valid[o + 1] = hi;
         }
     });
-    // Window of sample pairs one tile needs per channel: the delay grows by at
-    // most 2 kappa dz per row and (1 + |sin|) kappa dx per column.
+    // Window of sample pairs one tile needs per channel, over the pixels that
+    // count it: the delay grows by at most (1 + cos) kappa dz <= 2 kappa dz per
+    // row and by at most (|sin| + 1 / sqrt(1 + 4 F^2)) kappa dx per column (the
+    // transmit leg's slope, plus the receive leg's slope |x_p - x_i| /
+    // sqrt((x_p - x_i)^2 + z_p^2) inside the aperture |x_p - x_i| <= z_p / (2 F)).
+    // Two counted pixels of a tile are joined by a row-then-column or
+    // column-then-row path inside the aperture (the aperture widens with
+    // depth), so the spread adds up along it.  The planner checks every window
+    // against wmax (an error, never a silent clamp).
     const int align = 16 / pair_bytes(prec);
     const double dz = g.nz > 1 ? (g.z1 - g.z0) / (double)(g.nz - 1) : 0.0;
     const double dx = g.nx > 1 ? (g.x1 - g.x0) / (double)(g.nx - 1) : 0.0;
     const int rows = std::min(tile_rows(rows_per_thread), g.nz) - 1;
     const int cols = std::min(kTileCols, g.nx) - 1;
-    double spread = 2.0 * kappa * dz * rows + (1.0 + smax) * kappa * dx * cols;
+    const double rx_slope = 1.0 / std::sqrt(1.0 + 4.0 * g.fnum * g.fnum);
+    double spread = 2.0 * kappa * dz * rows + (smax + rx_slope) * kappa * dx * cols;
     int span = (int)std::ceil(spread) + 1 + 4 + align;
     // Box widths are whole multiples of 128 bytes, so every shared-memory
     // destination of a tensor copy (channel stride wmax, box offsets) stays
