@@ -278,6 +278,63 @@ def fk_migrate(rf, pitch, angles_rad, fs, c):
     return np.abs(img[:ns, :ne]).T.copy()
 
 
+def fk_stolt(rf, pitch, angles_rad, fs, c):
+    """Stolt's f-k migration for plane waves (Sec. II-B-3): the exploding
+    reflector model fitted to the plane-wave two-way time, migrated with Stolt's
+    mapping and mapped back onto the native grid [N][Ns] (column i at element
+    i, row m at depth m dz, dz = c / (2 fs)); |image|, compounded over angles.
+
+    The fit (the reading this library takes; the paper cites the method): after
+    the transmit's lateral delay x_i sin(theta) / c is removed, a scatterer at
+    (x0, z0) draws c t(u) = z0 (1 + cos) - u sin + sqrt(u^2 + z0^2), u = x - x0.
+    An exploding reflector at (x0', z0') seen with velocity v draws
+    v t = sqrt((x - x0')^2 + z0'^2).  Matching the two in value, slope and
+    curvature at u = 0 gives
+        v = c / beta, beta = sqrt(1 + cos - sin^2 / 2),
+        z0' = beta z0, x0' = x0 + z0 sin.
+    Stolt's mapping for that model takes the output wavenumbers (Kx, Kz') to
+    the temporal frequency w = v sqrt(Kx^2 + Kz'^2); the image is then mapped
+    back by the shear and scale (x, z) -> (x + z sin, beta z), which in the
+    spectrum reads Kz' = (Kz - Kx sin) / beta.  In bins (X, Q as in
+    fk_migrate): Q' = (Q - X sin) / beta, the temporal bin
+        pos = (2 / beta) sqrt(X^2 + Q'^2),
+    kept where Q' > 0 and 0 <= pos < nt / 2, interpolated linearly as in
+    fk_migrate and weighted by (1/2) dpos/dQ = Q' / (beta^2 sqrt(X^2 + Q'^2)).
+    """
+    rf = np.asarray(rf, dtype=np.float64)
+    na, ne, ns = rf.shape
+    nt, nk = fk_sizes(ne, ns)
+    dz = c / (2.0 * fs)
+    x = (np.arange(ne) - 0.5 * (ne - 1)) * pitch
+    b = np.arange(nt // 2 + 1, dtype=np.float64)
+    ms = np.where(np.arange(nk) < nk // 2, np.arange(nk), np.arange(nk) - nk).astype(np.float64)
+    X = ms * (nt * dz / (nk * pitch))                         # [nk]
+    Q = np.arange(1, nt // 2 + 1, dtype=np.float64)           # [nt/2]
+    XX, QQ = np.meshgrid(X, Q)                                # [q][m]
+    spec = np.zeros((nt, nk), dtype=np.complex128)            # [Kz bin][Kx bin]
+    cols = np.broadcast_to(np.arange(nk)[None, :], XX.shape)
+    for a in range(na):
+        st, ct = np.sin(angles_rad[a]), np.cos(angles_rad[a])
+        D = np.fft.rfft(rf[a], n=nt, axis=1)                  # [N][nt/2+1]
+        D = D * np.exp(1j * np.pi * b[None, :] * x[:, None] * st / (nt * dz))
+        D = np.fft.fft(D, n=nk, axis=0)                       # [nk][nt/2+1]
+        bet = np.sqrt(1.0 + ct - 0.5 * st * st)
+        Qp = (QQ - st * XX) / bet
+        rad = np.sqrt(XX * XX + Qp * Qp)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            pos = (2.0 / bet) * rad
+            w = Qp / (bet * bet * rad)
+        ok = (Qp > 0) & (pos >= 0) & (pos < nt // 2)
+        pos = np.where(ok, pos, 0.0)
+        i0 = np.floor(pos).astype(np.int64)
+        al = pos - i0
+        i1 = np.minimum(i0 + 1, nt // 2)
+        val = (1 - al) * D[cols, i0] + al * D[cols, i1]
+        spec[1:nt // 2 + 1] += np.where(ok, val * w, 0.0)
+    img = np.fft.ifft2(spec)                                  # [z][x]
+    return np.abs(img[:ns, :ne]).T.copy()
+
+
 def delayed_samples(rf, x_elem, angles_rad, grid, ix, iz, fs, c, f_number):
     """Per (angle, channel) interpolated samples of one pixel and their flags."""
     rf = np.ascontiguousarray(rf, dtype=np.int16)
