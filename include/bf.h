@@ -87,6 +87,8 @@ enum { BF_OUT_RF = 0, BF_OUT_ENV = 1 << 8, BF_OUT_LOGDB = 2 << 8, BF_OUT_MASK = 
  * Their outputs are magnitude images: BF_OUT_RF and BF_OUT_ENV both return
  * them, BF_OUT_LOGDB their -70 dB log compression. */
 enum { BF_IQDAS = 1 << 12, BF_BBDMAS = 1 << 13, BF_IQ_MASK = 3 << 12 };
+/* bf_fkmig only: Stolt's mapping instead of the exact plane-wave one (bit 16). */
+enum { BF_FK_STOLT = 1 << 16 };
 
 enum {
     BF_OK = 0,
@@ -124,21 +126,32 @@ BF_API int bf_destroy(bf_handle *h);
  * stream and must keep it alive while the handle uses it. */
 BF_API int bf_set_stream(bf_handle *h, void *cuda_stream);
 
-/* Paper: Sec. II-B-3 (the f-k migrations the paper evaluates next to the
- * beamformers).  Plane-wave f-k migration of one device-resident frame: per
- * angle the records' spectrum along time (zero-padded to nt, the power of two
- * >= 2 n_samples), the transmit's lateral delay x_i sin(theta) / c removed,
- * the spectrum along the elements (zero-padded to nk >= 2 n_elements), then
- * every output wavenumber (Kx, Kz > 0) takes the temporal frequency
- * f = c k / (2 pi), k = (Kx^2 + Kz^2) / (2 (Kx sin + Kz cos)) (the exact
- * mapping of the delay model above), interpolated linearly and weighted by
- * dk/dKz where the receive wave propagates; the angles' spectra are summed and
- * transformed back.  Output on the native grid, not the handle's pixel grid:
- * out_dev float [n_elements][n_samples], column i at element i, row m at depth
- * m c / (2 fs), holding |image| (flags BF_OUT_RF or BF_OUT_ENV) or its -70 dB
- * log compression (BF_OUT_LOGDB); no other flag bits.  Needs equally spaced
- * elements (2 to 2048), 2 <= n_samples <= 4096; BF_EINVAL otherwise.  Enqueued
- * on the handle's stream; uses scratch owned by the handle. */
+/* Paper: Sec. II-B-3 (Lu's and Stolt's f-k migrations, which the paper
+ * evaluates next to the beamformers).  Plane-wave f-k migration of one
+ * device-resident frame: per angle the records' spectrum along time
+ * (zero-padded to nt, the power of two >= 2 n_samples), the transmit's lateral
+ * delay x_i sin(theta) / c removed, the spectrum along the elements
+ * (zero-padded to nk >= 2 n_elements), then every output wavenumber
+ * (Kx, Kz > 0) takes the spectrum at a temporal frequency, interpolated
+ * linearly and weighted by the mapping's Jacobian; the angles' spectra are
+ * summed and transformed back.  The mapping:
+ *   default: the exact one of the delay model above, f = c k / (2 pi),
+ *     k = (Kx^2 + Kz^2) / (2 (Kx sin + Kz cos)), where the receive wave
+ *     propagates;
+ *   BF_FK_STOLT: Stolt's, for the exploding reflector fitted to the
+ *     plane-wave two-way time at the scatterer's lateral position (velocity
+ *     c / b, b = sqrt(1 + cos - sin^2 / 2)): f = c sqrt(Kx^2 + Kz'^2) / (2 pi b),
+ *     Kz' = (Kz - Kx sin) / b, the shear and scale that map the exploding
+ *     reflector's image back onto the native grid, where Kz' > 0.
+ * The mapping is tabulated on the host in double precision (kept while the
+ * sample count, angles and mapping stay the same); the device only gathers.
+ * Output on the native grid, not the handle's pixel grid: out_dev float
+ * [n_elements][n_samples], column i at element i, row m at depth m c / (2 fs),
+ * holding |image| (flags BF_OUT_RF or BF_OUT_ENV) or its -70 dB log
+ * compression (BF_OUT_LOGDB); no flag bits besides these and BF_FK_STOLT.
+ * Needs equally spaced elements (2 to 2048), 2 <= n_samples <= 4096; BF_EINVAL
+ * otherwise.  Enqueued on the handle's stream; uses scratch owned by the
+ * handle. */
 BF_API int bf_fkmig(bf_handle *h, const int16_t *rf_dev, int32_t n_samples,
                     const double *angles_rad, int32_t n_angles, uint32_t mode_and_flags,
                     float *out_dev);

@@ -1138,8 +1138,9 @@ BF_API int bf_fkmig(bf_handle *h, const int16_t *rf_dev, int32_t n_samples,
         return fail(BF_EINVAL, "null handle");
     if (!rf_dev || !out_dev || !angles_rad)
         return fail(BF_EINVAL, "null argument");
-    if (flags & ~(uint32_t)BF_OUT_MASK)
-        return fail(BF_EINVAL, "bf_fkmig takes only an output stage in its flags");
+    if (flags & ~((uint32_t)BF_OUT_MASK | (uint32_t)BF_FK_STOLT))
+        return fail(BF_EINVAL, "bf_fkmig takes only an output stage and BF_FK_STOLT in its flags");
+    const bool stolt = (flags & BF_FK_STOLT) != 0;
     const int stage = flags & BF_OUT_MASK;
     if (stage != BF_OUT_RF && stage != BF_OUT_ENV && stage != BF_OUT_LOGDB)
         return fail(BF_EINVAL, "unknown output stage bits");
@@ -1180,6 +1181,13 @@ BF_API int bf_fkmig(bf_handle *h, const int16_t *rf_dev, int32_t n_samples,
             beta[(size_t)a * ne + i] = (float)(kPi * x * sc[2 * a] / ((double)nt * dz));
         }
     }
+    // The mapping tables (geometry only): rebuilt when the sample count, the
+    // angles or the mapping change.
+    const int half = nt / 2;
+    const size_t npts = (size_t)half * nk;
+    std::vector<double> key{(double)n_samples, stolt ? 1.0 : 0.0};
+    key.insert(key.end(), angles_rad, angles_rad + n_angles);
+    const bool rebuild = key != h->fk_key;
     std::shared_ptr<EnvTablesDev> tt, tk;
     int rc = env_tables(nt, tt);
     if (!rc)
@@ -1195,16 +1203,28 @@ BF_API int bf_fkmig(bf_handle *h, const int16_t *rf_dev, int32_t n_samples,
         rc = h->fk_max.ensure(sizeof(unsigned));
     if (!rc)
         rc = h->fk_beta.ensure(beta.size() * sizeof(float));
-    if (!rc)
-        rc = h->fk_sc.ensure(sc.size() * sizeof(double));
+    if (!rc && rebuild)
+        rc = h->fk_i0.ensure((size_t)n_angles * npts * sizeof(int));
+    if (!rc && rebuild)
+        rc = h->fk_aw.ensure((size_t)n_angles * npts * sizeof(float2));
     if (rc)
         return rc;
+    if (rebuild) {
+        std::vector<int> i0;
+        std::vector<float> aw;
+        fk_mapping_tables(ne, nt, nk, pitch, dz, sc, stolt, i0, aw);
+        cudaError_t ce = cudaMemcpy(h->fk_i0.p, i0.data(), i0.size() * sizeof(int),
+                                    cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy(h->fk_aw.p, aw.data(), aw.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess)
+            return cuda_fail(ce, "bf_fkmig mapping tables");
+        h->fk_key = key;
+    }
     h->call.clear();  // the device tables above may have moved
     cudaStream_t st = h->stream;
     cudaError_t e = cudaMemcpyAsync(h->fk_beta.p, beta.data(), beta.size() * sizeof(float),
                                     cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->fk_sc.p, sc.data(), sc.size() * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && stage == BF_OUT_LOGDB)
         e = cudaMemsetAsync(h->fk_max.p, 0, sizeof(unsigned), st);
     if (e != cudaSuccess)
@@ -1216,10 +1236,10 @@ BF_API int bf_fkmig(bf_handle *h, const int16_t *rf_dev, int32_t n_samples,
     J.img = stage == BF_OUT_LOGDB ? (float *)h->fk_img.p : out_dev;
     J.maxbits = stage == BF_OUT_LOGDB ? (unsigned *)h->fk_max.p : nullptr;
     J.beta = (const float *)h->fk_beta.p;
-    J.sc = (const double *)h->fk_sc.p;
+    J.map_i0 = (const int *)h->fk_i0.p;
+    J.map_aw = (const float2 *)h->fk_aw.p;
     J.tw_t = (const float2 *)tt->tw.p;
     J.tw_k = (const float2 *)tk->tw.p;
-    J.r = (double)nt * dz / ((double)nk * pitch);
     J.na = n_angles;
     J.ne = ne;
     J.ns = n_samples;

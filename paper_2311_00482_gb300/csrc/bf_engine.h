@@ -210,7 +210,9 @@ struct bf_handle {
     bfi::FrameScratch scratch;     // bf_beamform
     bfi::DeviceLaunch launch;      // bf_beamform
     bfi::CallCache call;           // bf_beamform's last call
-    bfi::DevMem fk_D, fk_spec, fk_img, fk_beta, fk_sc, fk_max, fk_log, fk_logp;  // bf_fkmig scratch
+    bfi::DevMem fk_D, fk_spec, fk_img, fk_beta, fk_max, fk_log, fk_logp;  // bf_fkmig scratch
+    bfi::DevMem fk_i0, fk_aw;     // bf_fkmig mapping tables, for fk_key
+    std::vector<double> fk_key;   // (n_samples, Stolt?, angles...) of the tables
     bool err_cleared = false;
     std::map<uint64_t, std::shared_ptr<bfi::Request>> tickets;
 };

@@ -140,10 +140,14 @@ struct FkJob {
     float *img;           // [ne][ns] magnitude image
     unsigned *maxbits;    // image maximum (float bits) for the log stage, or null
     const float *beta;    // [na][ne] pi x_i sin(theta_a) / (nt dz): lateral phase per time bin
-    const double *sc;     // [na][2] sin, cos of the angles
+    // the mapping, decided on the host in double precision: per (angle, Kz bin
+    // q = 1 .. nt/2, Kx bin) the temporal bin i0 below the mapped position (-1:
+    // the point takes nothing from this angle) and (interpolation weight of
+    // bin i0 + 1, spectral weight)
+    const int *map_i0;    // [na][nt/2][nk]
+    const float2 *map_aw; // [na][nt/2][nk]
     const float2 *tw_t;   // [nt] exp(-2 pi i k / nt)
     const float2 *tw_k;   // [nk] exp(-2 pi i k / nk)
-    double r;             // nt dz / (nk pitch): lateral bin in units of temporal bins
     int na, ne, ns, nt, lgt, nk, lgk;
 };
 

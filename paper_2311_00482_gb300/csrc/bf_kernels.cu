@@ -1778,41 +1778,30 @@ __global__ void __launch_bounds__(256) fk_rows_kernel(float2 *data, int rows, in
         data[(size_t)r0 * n + t] = S[t];
 }
 
-// Migrated spectrum at (q = 1 .. nt/2, m): every angle's temporal bin
-// pos = (X^2 + Q^2) / (X sin + Q cos) of lateral bin m, interpolated and
-// weighted by dk/dKz, summed.  The mapping's decisions and the bin position
-// are formed in double precision without fused multiply-adds.
+// Migrated spectrum at (q = 1 .. nt/2, m): every angle's spectrum of lateral
+// bin m, interpolated between temporal bins i0 and i0 + 1 and weighted, summed.
+// The mapping (exact plane-wave or Stolt's) is tabulated on the host in double
+// precision: this kernel only gathers and sums in FP32.
 __global__ void __launch_bounds__(256) fk_map_kernel(const FkJob J)
 {
     const int nk = J.nk, half = J.nt / 2;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)half * nk)
         return;
-    const int q = (int)(idx / nk) + 1, m = (int)(idx - (long long)(q - 1) * nk);
-    const double X = __dmul_rn((double)(m < nk / 2 ? m : m - nk), J.r);
-    const double Q = (double)q;
-    const double num = __dadd_rn(__dmul_rn(X, X), __dmul_rn(Q, Q));
+    const int m = (int)(idx % nk);
     const int nf = half + 1;
     float2 acc = make_float2(0.f, 0.f);
     for (int a = 0; a < J.na; ++a) {
-        const double st = __ldg(J.sc + 2 * a), ct = __ldg(J.sc + 2 * a + 1);
-        const double den = __dadd_rn(__dmul_rn(X, st), __dmul_rn(Q, ct));
-        if (!(den > 0.0))
+        const size_t t = (size_t)a * half * nk + (size_t)idx;
+        const int i0 = __ldg(J.map_i0 + t);
+        if (i0 < 0)
             continue;
-        const double pos = __ddiv_rn(num, den);
-        if (!(fabs(__dsub_rn(__dmul_rn(2.0, X), __dmul_rn(pos, st))) <= pos) || !(pos >= 0.0) ||
-            !(pos < (double)half))
-            continue;
-        const double w = __ddiv_rn(__dsub_rn(__dmul_rn(Q, den), __dmul_rn(__dmul_rn(0.5, num), ct)),
-                                   __dmul_rn(den, den));
-        const double fl = floor(pos);
-        const int i0 = (int)fl, i1 = min(i0 + 1, half);
-        const float al = (float)(pos - fl);
+        const float2 aw = __ldg(J.map_aw + t);  // (alpha, weight)
+        const int i1 = min(i0 + 1, half);
         const float2 *D = J.D + (size_t)a * nf * nk + m;
         const float2 v0 = D[(size_t)i0 * nk], v1 = D[(size_t)i1 * nk];
-        const float wf = (float)w;
-        acc.x = fmaf(wf, fmaf(al, v1.x - v0.x, v0.x), acc.x);
-        acc.y = fmaf(wf, fmaf(al, v1.y - v0.y, v0.y), acc.y);
+        acc.x = fmaf(aw.y, fmaf(aw.x, v1.x - v0.x, v0.x), acc.x);
+        acc.y = fmaf(aw.y, fmaf(aw.x, v1.y - v0.y, v0.y), acc.y);
     }
     J.spec[idx] = acc;
 }

@@ -219,6 +219,55 @@ void bandpass_bins(int nz, double z0, double z1, double c, double f0, int &lo, i
     }
 }
 
+void fk_mapping_tables(int ne, int nt, int nk, double pitch, double dz,
+                       const std::vector<double> &sc, bool stolt, std::vector<int> &i0,
+                       std::vector<float> &aw)
+{
+    (void)ne;
+    const int na = (int)sc.size() / 2, half = nt / 2;
+    const size_t npts = (size_t)half * nk;
+    i0.assign((size_t)na * npts, -1);
+    aw.assign((size_t)na * npts * 2, 0.0f);
+    // lateral bin m in units of temporal bins: X = m_s (nt dz / (nk pitch))
+    const double r = (double)nt * dz / ((double)nk * pitch);
+    for (int a = 0; a < na; ++a) {
+        const double st = sc[2 * a], ct = sc[2 * a + 1];
+        const double bet = std::sqrt(1.0 + ct - 0.5 * st * st);  // Stolt: depth scale
+        parallel_for(half, [&](int qi) {
+            const double Q = (double)(qi + 1);
+            for (int m = 0; m < nk; ++m) {
+                const double X = (double)(m < nk / 2 ? m : m - nk) * r;
+                double pos, w;
+                bool ok;
+                if (!stolt) {
+                    // exact plane-wave mapping k = (Kx^2 + Kz^2) / (2 (Kx sin + Kz cos))
+                    const double den = X * st + Q * ct;
+                    const double num = X * X + Q * Q;
+                    pos = num / den;
+                    w = (Q * den - 0.5 * num * ct) / (den * den);
+                    ok = den > 0.0 && std::fabs(2.0 * X - pos * st) <= pos && pos >= 0.0 &&
+                         pos < (double)half;
+                } else {
+                    // Stolt's mapping of the exploding reflector at velocity c / bet,
+                    // sheared and scaled back onto the native grid
+                    const double Qp = (Q - st * X) / bet;
+                    const double rad = std::sqrt(X * X + Qp * Qp);
+                    pos = (2.0 / bet) * rad;
+                    w = Qp / (bet * bet * rad);
+                    ok = Qp > 0.0 && pos >= 0.0 && pos < (double)half;
+                }
+                if (!ok)
+                    continue;
+                const double fl = std::floor(pos);
+                const size_t t = (size_t)a * npts + (size_t)qi * nk + m;
+                i0[t] = (int)fl;
+                aw[2 * t] = (float)(pos - fl);
+                aw[2 * t + 1] = (float)w;
+            }
+        });
+    }
+}
+
 static void fft_inplace(std::vector<std::complex<double>> &a)
 {
     const size_t n = a.size();

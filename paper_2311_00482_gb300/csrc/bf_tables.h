@@ -48,6 +48,15 @@ void angle_tables(const GeomHost &g, const GeometryHost &geo, int ns,
                   const std::vector<double> &angles, int prec, int rows, int stage_bytes,
                   PlanHost &out);
 void bandpass_bins(int nz, double z0, double z1, double c, double f0, int &lo, int &hi);
+// Plane-wave f-k mapping of every (angle, Kz bin q = 1 .. nt/2, Kx bin m):
+// i0 [na][nt/2][nk] the temporal bin below the mapped position (-1: nothing
+// taken), aw [na][nt/2][nk][2] its interpolation weight toward i0 + 1 and the
+// spectral weight.  sc: sin, cos of each angle.  stolt: Stolt's mapping of the
+// exploding-reflector fit instead of the exact plane-wave mapping.  Double
+// precision, evaluated in the order the definitions are written.
+void fk_mapping_tables(int ne, int nt, int nk, double pitch, double dz,
+                       const std::vector<double> &sc, bool stolt, std::vector<int> &i0,
+                       std::vector<float> &aw);
 void envelope_tables(int nz, EnvHost &out);
 
 }  // namespace bfi
