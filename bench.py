@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--prec", default="fp32", choices=["fp32", "fp16", "bf16"])
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-serving", action="store_true", help="skip the short serving-latency leg")
     p.add_argument("--workload", default="cyst512",
                    choices=["cyst512", "batch256", "serving", "precision", "sweep", "iq", "fk"],
                    help="cyst512: the headline line; the others print informational lines")
@@ -403,6 +404,10 @@ def run_ours(args):
         "gpu_launches": launches * args.steps,
         "clocks": clocks,
     }
+    if rank == 0 and not args.no_serving:
+        # serving latency beside throughput: a short Poisson-served leg (not part
+        # of the timed steps above)
+        line["serving_latency_ms"] = serving_latency(torch, bf)
     if rank == 0 and ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = time_oracle(acq, rfs, args.cpu_seconds)
     batch.close()
@@ -672,79 +677,88 @@ def run_sweep(args):
                       "rows": rows}), flush=True)
 
 
-def run_serving(args):
+SERVING_WORKLOAD = ("serving: Poisson arrivals, square grids 128..1024 px, 1..7 plane waves, DAS or "
+                    "DMAS, 64 ch x 2048 samples, pinned host RF in, pinned host dB image out; "
+                    "engine = continuous batching with FP16 storage, plain = FIFO of one-frame "
+                    "FP32 launches")
+
+
+class ServingTrace:
     """Poisson arrivals of mixed requests, pinned host RF in and host dB images
     out: the continuous-batching engine (FP16 storage) against a FIFO in front
     of the plain FP32 one-frame-per-launch kernel, on the same trace."""
-    import queue
-    import threading
 
-    torch, bf = _setup_gpu()
-    sys.setswitchinterval(1e-5)  # the submitting thread spins; let the completion thread in
-    rng = np.random.default_rng(synth.BASE_SEED + 4)
-    base = synth.cyst_wires_frame(synth.CYST_WIRES_512)[0][0]
-    rf_host = torch.from_numpy(np.ascontiguousarray(np.broadcast_to(base, (7,) + base.shape)))
-    rf_host = rf_host.pin_memory()
-    handles = {}
+    def __init__(self, torch, bf, n_requests, seed=synth.BASE_SEED + 4):
+        self.torch, self.bf, self.N = torch, bf, n_requests
+        self.rng = np.random.default_rng(seed)
+        base = synth.cyst_wires_frame(synth.CYST_WIRES_512)[0][0]
+        self.rf_host = torch.from_numpy(
+            np.ascontiguousarray(np.broadcast_to(base, (7,) + base.shape))).pin_memory()
+        self.handles = {}
+        self.trace = []
+        for _ in range(n_requests):
+            n = 64 * int(self.rng.integers(2, 17))  # 128 .. 1024 pixels per side
+            na = int(self.rng.integers(1, 8))
+            mode = bf.BF_DAS if self.rng.random() < 0.5 else bf.BF_DMAS
+            self.trace.append((n, na, mode, np.deg2rad(synth.angles_linspace(na))))
+        self.outs = {n: torch.empty((1, n, n), dtype=torch.float32).pin_memory()
+                     for n, *_ in self.trace}
+        self.stream = torch.cuda.Stream()
+        self.rf_dev = torch.empty_like(self.rf_host, device="cuda")
+        self.out_dev = torch.empty((1024 * 1024,), dtype=torch.float32, device="cuda")
+        for h in set(self.handle(n) for n, *_ in self.trace):
+            bf.bf_set_stream(h, self.stream)
+        # untimed pass: every table, slot and scratch buffer exists before the clock starts
+        seen = set()
+        for k in range(self.N):
+            if self.trace[k][:3] not in seen:
+                seen.add(self.trace[k][:3])
+                self.plain_run(k)
+        for k0 in range(0, self.N, 128):  # in chunks: admission caps the requests in flight
+            ks = range(k0, min(self.N, k0 + 128))
+            tickets = [self.engine_submit(k) for k in ks]
+            for k, t in zip(ks, tickets):
+                self.engine_wait(k, t)
 
-    def handle(n):
-        if n not in handles:
-            handles[n] = _handle(bf, synth.CYST_WIRES_512.with_(nx=n, nz=n))
-        return handles[n]
+    def handle(self, n):
+        if n not in self.handles:
+            self.handles[n] = _handle(self.bf, synth.CYST_WIRES_512.with_(nx=n, nz=n))
+        return self.handles[n]
 
-    N = args.requests
-    trace = []
-    for _ in range(N):
-        n = 64 * int(rng.integers(2, 17))  # 128 .. 1024 pixels per side
-        na = int(rng.integers(1, 8))
-        mode = bf.BF_DAS if rng.random() < 0.5 else bf.BF_DMAS
-        trace.append((n, na, mode, np.deg2rad(synth.angles_linspace(na))))
-    outs = {n: torch.empty((1, n, n), dtype=torch.float32).pin_memory() for n, *_ in trace}
-    stream = torch.cuda.Stream()
-    rf_dev = torch.empty_like(rf_host, device="cuda")
-    out_dev = torch.empty((1024 * 1024,), dtype=torch.float32, device="cuda")
-
-    def engine_submit(k):
-        n, na, mode, ang = trace[k]
+    def engine_submit(self, k):
+        bf = self.bf
+        n, na, mode, ang = self.trace[k]
         while True:
             try:
-                return bf.bf_submit(handle(n), rf_host[:na], 2048, ang,
+                return bf.bf_submit(self.handle(n), self.rf_host[:na], 2048, ang,
                                     mode | bf.BF_PREC_FP16 | bf.BF_OUT_LOGDB)
             except bf.BFError as e:
                 if e.code != bf.BF_EAGAIN:
                     raise
 
-    def engine_wait(k, ticket):
-        n = trace[k][0]
-        bf.bf_poll(handle(n), ticket, outs[n], timeout_us=60_000_000)
+    def engine_wait(self, k, ticket):
+        n = self.trace[k][0]
+        self.bf.bf_poll(self.handle(n), ticket, self.outs[n], timeout_us=60_000_000)
 
-    def plain_run(k):
-        n, na, mode, ang = trace[k]
-        h = handle(n)
+    def plain_run(self, k):
+        torch, bf = self.torch, self.bf
+        n, na, mode, ang = self.trace[k]
+        h = self.handle(n)
         nb = na * 64 * 2048
-        with torch.cuda.stream(stream):
-            rf_dev.view(-1)[:nb].copy_(rf_host.view(-1)[:nb], non_blocking=True)
-            bf.bf_beamform_plain(h, rf_dev.view(-1)[:nb], 2048, ang, mode | bf.BF_OUT_LOGDB,
-                                 out_dev[:n * n])
-            outs[n].view(-1).copy_(out_dev[:n * n], non_blocking=True)
-        stream.synchronize()
+        with torch.cuda.stream(self.stream):
+            self.rf_dev.view(-1)[:nb].copy_(self.rf_host.view(-1)[:nb], non_blocking=True)
+            bf.bf_beamform_plain(h, self.rf_dev.view(-1)[:nb], 2048, ang, mode | bf.BF_OUT_LOGDB,
+                                 self.out_dev[:n * n])
+            self.outs[n].view(-1).copy_(self.out_dev[:n * n], non_blocking=True)
+        self.stream.synchronize()
 
-    for h in set(handle(n) for n, *_ in trace):
-        bf.bf_set_stream(h, stream)
-    # untimed pass: every table, slot and scratch buffer exists before the clock starts
-    seen = set()
-    for k in range(N):
-        if (trace[k][0], trace[k][1], trace[k][2]) not in seen:
-            seen.add((trace[k][0], trace[k][1], trace[k][2]))
-            plain_run(k)
-    for k0 in range(0, N, 128):  # in chunks: admission caps the requests in flight
-        ks = range(k0, min(N, k0 + 128))
-        tickets = [engine_submit(k) for k in ks]
-        for k, t in zip(ks, tickets):
-            engine_wait(k, t)
+    def drive(self, rate, kind):
+        """One pass of the trace at `rate` Hz; kind "batched_fp16" or "plain_fp32"."""
+        import queue
+        import threading
 
-    def drive(rate, kind):
-        gaps = rng.exponential(1.0 / rate, N)
+        N = self.N
+        gaps = self.rng.exponential(1.0 / rate, N)
         lat, t_sub = [0.0] * N, [0.0] * N
         handoff = queue.Queue()
 
@@ -752,9 +766,9 @@ def run_serving(args):
             for k in range(N):
                 item = handoff.get()
                 if kind == "batched_fp16":
-                    engine_wait(k, item)
+                    self.engine_wait(k, item)
                 else:
-                    plain_run(k)
+                    self.plain_run(k)
                 lat[k] = time.perf_counter() - t_sub[k]
 
         th = threading.Thread(target=completer)
@@ -766,26 +780,52 @@ def run_serving(args):
             while time.perf_counter() < t_next:
                 pass
             t_sub[k] = time.perf_counter()
-            handoff.put(engine_submit(k) if kind == "batched_fp16" else k)
+            handoff.put(self.engine_submit(k) if kind == "batched_fp16" else k)
         th.join()
         t_all = time.perf_counter() - t0
-        units = sum(n * n * 64 * na for n, na, _, _ in trace)
+        units = sum(n * n * 64 * na for n, na, _, _ in self.trace)
         return {"rate_hz": rate, "engine": kind, "frames_per_s": N / t_all,
                 "gpixel_ch_per_s": units / t_all / 1e9,
                 "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                 "p99_ms": 1e3 * float(np.percentile(lat, 99))}
 
+    def close(self):
+        for h in self.handles.values():
+            self.bf.bf_destroy(h)
+        self.handles = {}
+
+
+def serving_latency(torch, bf, n_requests=300, rates=(2000, 10000)):
+    """The short serving leg of the default line: per rate the engine's and the
+    plain kernel's frame latency (submission to the dB image on the host)."""
+    sys.setswitchinterval(1e-5)  # the submitting thread spins; let the completion thread in
+    st = ServingTrace(torch, bf, n_requests)
+    try:
+        rows = []
+        for rate in rates:
+            e = st.drive(rate, "batched_fp16")
+            p = st.drive(rate, "plain_fp32")
+            rows.append({"rate_hz": rate, "p50": e["p50_ms"], "p99": e["p99_ms"],
+                         "frames_per_s": e["frames_per_s"], "plain_p50": p["p50_ms"],
+                         "plain_p99": p["p99_ms"], "plain_frames_per_s": p["frames_per_s"]})
+        return {"workload": SERVING_WORKLOAD, "requests_per_rate": n_requests, "rates": rows}
+    finally:
+        st.close()
+
+
+def run_serving(args):
+    """Poisson arrivals at 1, 2, 5, 10 and 20 kHz (see ServingTrace)."""
+    torch, bf = _setup_gpu()
+    sys.setswitchinterval(1e-5)  # the submitting thread spins; let the completion thread in
+    st = ServingTrace(torch, bf, args.requests)
     results = []
     for rate in (1000, 2000, 5000, 10000, 20000):
         for kind in ("batched_fp16", "plain_fp32"):
-            results.append(drive(rate, kind))
+            results.append(st.drive(rate, kind))
             print(json.dumps(results[-1]), flush=True)
-    print(json.dumps({"workload": "serving: Poisson arrivals, square grids 128..1024 px, 1..7 plane waves, "
-                                  "DAS or DMAS, 64 ch x 2048 samples, pinned host RF in, pinned host "
-                                  "dB image out; plain_fp32 = FIFO of one-frame launches",
-                      "requests_per_rate": N, "results": results}), flush=True)
-    for h in handles.values():
-        bf.bf_destroy(h)
+    print(json.dumps({"workload": SERVING_WORKLOAD, "requests_per_rate": args.requests,
+                      "results": results}), flush=True)
+    st.close()
 
 
 def main():
