@@ -158,13 +158,14 @@ static int encode_pairs_map(CUtensorMap *map, void *base, int rows, int nsp, int
 
 // Pairs per frame of one tensor copy of an nf-frame job's interleaved window
 // ([pair][frame], wmax pairs): the largest divisor of wmax whose copy spans at
-// most kMaxBox elements and a multiple of 16 bytes (0: none).
+// most kMaxBox tensor elements (IQ pairs: two each) and a multiple of 16 bytes
+// (0: none).
 static int interleaved_box(int wmax, int nf, int prec)
 {
     const int pb = pair_bytes(prec);
     if ((wmax * nf * pb) % 16 != 0)
         return 0;
-    for (int d = std::min(wmax, kMaxBox / nf); d >= 1; --d)
+    for (int d = std::min(wmax, kMaxBox / (nf * pair_elems(prec))); d >= 1; --d)
         if (wmax % d == 0 && (d * nf * pb) % 16 == 0)
             return d;
     return 0;
@@ -208,7 +209,8 @@ static int env_tables(int nz, std::shared_ptr<EnvTablesDev> &out)
 // Tile configuration of a workload: what bf_autotune measured fastest for it,
 // else entry 0 (4 rows per thread, 32-row tiles, three CTAs per SM, measured
 // faster than 8 rows on every grid tried); BF_TILE_ROWS=8 forces entry 3,
-// BF_TILE_ROWS=2 entry 4 (DAS / DMAS of RF records; others keep entry 0).
+// BF_TILE_ROWS=2 entry 4 (DAS / DMAS of RF records, IQ-DAS / BB-DMAS; others
+// keep entry 0).
 static int choose_cfg(const bf_handle *h, const PlanKey &key)
 {
     if (const char *e = std::getenv("BF_TILE_ROWS")) {
@@ -227,13 +229,13 @@ int handle_plan(bf_handle *h, int ns, const double *angles, int na, uint32_t fla
                 int cfg)
 {
     const int prec = frame_prec(flags);
-    const bool narrow_ok = prec != kPrecIQ && (flags & BF_MODE_MASK & ~(BF_DAS | BF_DMAS)) == 0;
+    const bool narrow_ok = (flags & BF_MODE_MASK & ~(BF_DAS | BF_DMAS)) == 0;
     PlanKey key{ns, prec, std::vector<double>(angles, angles + na), 0};
     std::lock_guard<std::mutex> lk(h->mu);
     key.cfg = (cfg >= 0 && cfg < kNumTileConfigs) ? cfg : choose_cfg(h, key);
     if (kTileConfigs[key.cfg].rows == 2 && !narrow_ok) {
         if (cfg >= 0)
-            return fail(BF_EINVAL, "two-row tiles serve DAS / DMAS of RF records only");
+            return fail(BF_EINVAL, "two-row tiles serve DAS / DMAS and IQ-DAS / BB-DMAS only");
         key.cfg = 0;
     }
     auto it = h->plans.find(key);
@@ -474,13 +476,16 @@ int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *ang
 
 // Host-side launch description of a set of frames (job arrays + prefixes).
 // Frames can share one beamforming job (and every delay) when they use the
-// same plan with the same combiners: DAS and / or DMAS of RF records, up to
-// two frames on 32-row tiles and four on 16-row tiles.
+// same plan with the same combiners: DAS and / or DMAS of RF records, or
+// IQ-DAS and / or BB-DMAS (which share the carrier phase as well), up to two
+// frames on 32-row tiles and four on 16-row tiles.
 static int plan_frames_per_job(const Plan *p, int modes, int prec, int cap)
 {
     const int m = modes & (BF_MODE_MASK | BF_IQ_MASK);
-    if (prec == kPrecIQ || (m & ~(BF_DAS | BF_DMAS)) != 0)
+    if ((m & ~(BF_DAS | BF_DMAS | BF_IQ_MASK)) != 0)
         return 1;
+    if (prec == kPrecIQ && demod_smem_bytes(p->ns, true) > (size_t)kMaxSmemPerCta)
+        return 1;  // a frame pair's demodulation does not fit one CTA
     for (int nf = p->rows == 2 ? 4 : p->rows == 4 ? 2 : 1; nf > 1; nf /= 2)
         if (nf <= cap &&
             beamform_smem_bytes(p->wmax, p->group, prec, nf, p->rows) <= (size_t)kMaxSmemPerCta &&
@@ -510,7 +515,9 @@ static int lead_map(const FramePrep &f, int nf, int box)
     if (S.mapnf_base == f.pairs && S.mapnf_rows == rows && S.mapnf_nsp == nsp &&
         S.mapnf_box == box && S.mapnf_prec == f.prec && S.mapnf_nf == nf)
         return BF_OK;
-    int rc = encode_map(&S.map_nf_host, f.pairs, rows, nsp * nf, pair_bytes(f.prec), box * nf, 1);
+    const int k = pair_elems(f.prec);  // IQ pairs: two 8-byte elements each
+    int rc = encode_map(&S.map_nf_host, f.pairs, rows, nsp * nf * k, pair_bytes(f.prec) / k,
+                        box * nf * k, 1);
     if (rc)
         return rc;
     S.mapnf_base = f.pairs;
@@ -599,8 +606,12 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
         j.iq_c1 = (float)(2.0 * kPi * r);
         j.iq_c2 = (float)(kPi * r);
         j.maxbits = (f.prec == kPrecIQ && f.stage == BF_OUT_LOGDB) ? f.maxbits : nullptr;
-        for (int q = 0; q < kMaxFramesPerJob - 1; ++q)
+        for (int q = 0; q < kMaxFramesPerJob - 1; ++q) {
             j.y_more[q] = more[q] ? more[q]->y : nullptr;
+            j.maxbits_more[q] = (more[q] && f.prec == kPrecIQ && more[q]->stage == BF_OUT_LOGDB)
+                                    ? more[q]->maxbits
+                                    : nullptr;
+        }
         if (nf > 1) {  // the frames' pairs interleaved in the lead's scratch
             j.rf_map = (const CUtensorMap *)f.scratch->map_nf.p;
             j.box = box_nf;
@@ -632,12 +643,23 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
         hl.groups.push_back(g);
     }
     std::map<int, std::vector<IngestJob>> ig;
-    for (const FramePrep &f : frames) {
-        if (f.prec == kPrecIQ) {
-            const double r = f.h->g.f0 / f.h->g.fs;
+    // IQ frames: one demodulation job per frame, or per frame pair of a
+    // multi-frame job (into the lead's interleaved array)
+    for (size_t fi = 0; fi < frames.size(); ++fi) {
+        const FramePrep &f = frames[fi];
+        if (f.prec != kPrecIQ || member[fi])
+            continue;
+        std::vector<size_t> job{fi};
+        job.insert(job.end(), partners[fi].begin(), partners[fi].end());
+        const int nf = (int)job.size();
+        const double r = f.h->g.f0 / f.h->g.fs;
+        for (int q = 0; q < (nf == 1 ? 1 : nf / 2); ++q) {
+            const FramePrep &a = frames[job[nf == 1 ? 0 : 2 * q]];
             DemodJob d{};
-            d.rf = f.rf;
+            d.rf = a.rf;
             d.pairs = (float4 *)f.pairs;
+            d.nf = nf;
+            d.fi = nf == 1 ? 0 : 2 * q;
             d.rows = f.na * f.h->g.ne;
             d.ns = f.ns;
             d.nsp = f.plan->nsp;
@@ -646,12 +668,17 @@ void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl)
                 ++d.lgn;
             d.rot = make_float2((float)std::cos(2.0 * kPi * r), (float)-std::sin(2.0 * kPi * r));
             d.tw = (const float2 *)f.dt->tw.p;
-            d.maxbits = f.stage != BF_OUT_RF ? f.maxbits : nullptr;
+            d.maxbits = a.stage != BF_OUT_RF ? a.maxbits : nullptr;
+            if (nf > 1) {
+                const FramePrep &b = frames[job[2 * q + 1]];
+                d.rf2 = b.rf;
+                d.maxbits2 = b.stage != BF_OUT_RF ? b.maxbits : nullptr;
+                hl.demod_pairs = true;
+            }
             hl.demod_prefix.push_back(hl.demod_rows);
             hl.demod_rows += d.rows;
             hl.demod_max_ns = std::max(hl.demod_max_ns, f.ns);
             hl.demod.push_back(d);
-            continue;
         }
     }
     for (size_t fi = 0; fi < frames.size(); ++fi) {
@@ -860,7 +887,7 @@ int enqueue(const std::vector<FramePrep> &frames, const HostLaunch &hl, DeviceLa
     }
     if (!hl.demod.empty()) {
         e = launch_demod((const DemodJob *)dl.demod.p, (const int *)dl.demod_prefix.p,
-                         (int)hl.demod.size(), hl.demod_rows, hl.demod_max_ns, st);
+                         (int)hl.demod.size(), hl.demod_rows, hl.demod_max_ns, hl.demod_pairs, st);
         if (e != cudaSuccess)
             return cuda_fail(e, "demodulation launch");
     }

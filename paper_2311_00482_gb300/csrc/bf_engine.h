@@ -155,6 +155,7 @@ struct HostLaunch {
     std::vector<DemodJob> demod;   // IQ frames: records to analytic-signal pairs
     std::vector<int> demod_prefix;
     int demod_rows = 0, demod_max_ns = 0;
+    bool demod_pairs = false;  // some demodulation job covers a frame pair
 };
 
 struct DeviceLaunch {

@@ -72,6 +72,9 @@ struct BfJob {
     // frames, interleaved by frame ([row][pair][frame]), and box counts pairs
     // per frame of one copy.
     float *y_more[kMaxFramesPerJob - 1];
+    // IQ jobs: the further frames' image maxima (as maxbits below; null where
+    // that frame's images do not feed the log stage)
+    unsigned *maxbits_more[kMaxFramesPerJob - 1];
     int nx, nz, na, ne;
     int wmax;             // window length (pairs) staged per channel and tile
     int box;              // TMA box width (pairs); wmax is a multiple of it
@@ -123,10 +126,19 @@ struct IngestJob {
 // power-of-two-length FFT), then pair j (samples k = j - kPadL and k + 1)
 // holds mid = (A + B) / 2 and diff = B - A with A = a[k],
 // B = a[k + 1] exp(-j 2 pi f0 / fs) (zero outside the record).
+//
+// Frames of a multi-frame IQ job (nf = 2 or 4) are demodulated in frame pairs
+// (frames fi and fi + 1 of the job, one job entry per pair) into the lead
+// frame's array, interleaved for the beamformer's paired arithmetic: per pair
+// index j a block of 4 nf floats, and in it per frame pair q = fi / 2 eight
+// floats (mid.re, mid.im, diff.re, diff.im, each for frames 2q and 2q + 1).
 struct DemodJob {
-    const int16_t *rf;    // [rows][ns]
-    float4 *pairs;        // [rows][nsp] (mid.re, mid.im, diff.re, diff.im)
+    const int16_t *rf;    // [rows][ns] (the pair's first frame)
+    const int16_t *rf2;   // nf > 1: the pair's second frame
+    float4 *pairs;        // nf == 1: [rows][nsp] (mid.re, mid.im, diff.re, diff.im)
     int rows, ns, nsp, lgn;
+    int nf, fi;           // frames of the beamforming job, the (first) frame's index in it
+    unsigned *maxbits2;   // nf > 1: the second frame's image maxima (or null)
     float2 rot;           // exp(-j 2 pi f0 / fs)
     const float2 *tw;     // [ns] exp(-2 pi i k / ns)
     unsigned *maxbits;    // the frame's image maxima, zeroed by the job's first CTA (or null)
@@ -194,9 +206,10 @@ cudaError_t launch_plan(const PlanJob &job, int *err_dev, cudaStream_t stream);
 // total_blocks: the jobs' rows x chunks (blk_prefix_dev: each job's first CTA).
 cudaError_t launch_ingest(const IngestJob *jobs_dev, const int *blk_prefix_dev, int njobs,
                           int total_blocks, int prec, cudaStream_t stream);
+// pairs: some job demodulates a frame pair (four transform buffers per CTA)
 cudaError_t launch_demod(const DemodJob *jobs_dev, const int *row_prefix_dev, int njobs,
-                         int total_rows, int max_ns, cudaStream_t stream);
-size_t demod_smem_bytes(int ns);
+                         int total_rows, int max_ns, bool pairs, cudaStream_t stream);
+size_t demod_smem_bytes(int ns, bool pairs);
 // f-k migration launches (bf_kernels.cu), in order on `stream`.
 cudaError_t launch_fkmig(const FkJob &job, cudaStream_t stream);
 // nf: frames per job (1, 2 or 4, with 4 on two-row tiles only; the frames of

@@ -366,25 +366,15 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestJob *__restrict
 
 // --------------------------------------------------------- demodulation --
 
-// One channel record per CTA: analytic signal by a length-ns transform pair
-// (one-sided spectrum: H = 1 at 0 and ns/2, 2 between, 0 above), then the
-// complex interpolation pairs of the IQ beamformer.
-__global__ void __launch_bounds__(256) demod_kernel(const DemodJob *__restrict__ jobs,
-                                                    const int *__restrict__ row_prefix, int njobs)
+// Analytic signal of one int16 record u of length m = 2^lgm, scaled by m:
+// length-m transform of u in X (Y the work buffer), one-sided spectrum
+// (H = 1 at 0 and m/2, 2 between, 0 above), inverse transform.  Returns the
+// buffer (X or Y) holding it.
+__device__ float2 *analytic_scaled(const int16_t *__restrict__ u, int m, int lgm, float2 *X,
+                                   float2 *Y, const float2 *tw)
 {
-    extern __shared__ __align__(16) float2 dbuf[];
-    const int jb = find_job(row_prefix, njobs, blockIdx.x);
-    const DemodJob J = jobs[jb];
-    const int row = blockIdx.x - __ldg(row_prefix + jb);
-    if (row == 0 && J.maxbits && threadIdx.x < 4)  // before any later kernel takes a maximum
-        J.maxbits[threadIdx.x] = 0u;
-    const int m = J.ns, lgm = J.lgn;
-    float2 *X = dbuf, *Y = dbuf + m, *tw = dbuf + 2 * (size_t)m;
-    const int16_t *__restrict__ u = J.rf + (size_t)row * m;
-    for (int k = threadIdx.x; k < m; k += blockDim.x) {
-        tw[k] = __ldg(J.tw + k);
+    for (int k = threadIdx.x; k < m; k += blockDim.x)
         X[k] = make_float2((float)__ldg(u + k), 0.f);
-    }
     __syncthreads();
     float2 *S = fft_r8(X, Y, m, lgm, 1, tw, false);
     for (int k = threadIdx.x; k < m; k += blockDim.x) {
@@ -392,16 +382,59 @@ __global__ void __launch_bounds__(256) demod_kernel(const DemodJob *__restrict__
         S[k] = make_float2(S[k].x * h, S[k].y * h);
     }
     __syncthreads();
-    float2 *A = fft_r8(S, S == X ? Y : X, m, lgm, 1, tw, true);  // m * analytic signal
+    return fft_r8(S, S == X ? Y : X, m, lgm, 1, tw, true);
+}
+
+// Interpolation pair j of an analytic signal A (scaled by m): mid = (a + b) / 2,
+// diff = b - a with a = A[k], b = A[k + 1] exp(-j 2 pi f0 / fs), k = j - kPadL
+// (zero outside the record).
+__device__ __forceinline__ float4 demod_pair(const float2 *A, int j, int m, float2 rot, float inv)
+{
+    const int k = j - kPadL;
+    const float2 a0 = (k >= 0 && k < m) ? A[k] : make_float2(0.f, 0.f);
+    const float2 a1 = (k + 1 >= 0 && k + 1 < m) ? A[k + 1] : make_float2(0.f, 0.f);
+    const float2 b = cmul(a1, rot);
+    return make_float4(0.5f * (a0.x + b.x) * inv, 0.5f * (a0.y + b.y) * inv, (b.x - a0.x) * inv,
+                       (b.y - a0.y) * inv);
+}
+
+// One channel record per CTA (of one frame, or of the two frames of a frame
+// pair of a multi-frame job): analytic signal, then the complex interpolation
+// pairs of the IQ beamformer.
+__global__ void __launch_bounds__(256) demod_kernel(const DemodJob *__restrict__ jobs,
+                                                    const int *__restrict__ row_prefix, int njobs)
+{
+    extern __shared__ __align__(16) float2 dbuf[];
+    const int jb = find_job(row_prefix, njobs, blockIdx.x);
+    const DemodJob J = jobs[jb];
+    const int row = blockIdx.x - __ldg(row_prefix + jb);
+    if (row == 0 && threadIdx.x < 4) {  // before any later kernel takes a maximum
+        if (J.maxbits)
+            J.maxbits[threadIdx.x] = 0u;
+        if (J.maxbits2)
+            J.maxbits2[threadIdx.x] = 0u;
+    }
+    const int m = J.ns, lgm = J.lgn;
+    float2 *X = dbuf, *Y = dbuf + m, *tw = dbuf + 2 * (size_t)m, *Z = dbuf + 3 * (size_t)m;
+    for (int k = threadIdx.x; k < m; k += blockDim.x)
+        tw[k] = __ldg(J.tw + k);
     const float inv = 1.f / (float)m;
-    float4 *__restrict__ out = J.pairs + (size_t)row * J.nsp;
+    const float2 *A = analytic_scaled(J.rf + (size_t)row * m, m, lgm, X, Y, tw);
+    if (J.nf == 1) {
+        float4 *__restrict__ out = J.pairs + (size_t)row * J.nsp;
+        for (int j = threadIdx.x; j < J.nsp; j += blockDim.x)
+            out[j] = demod_pair(A, j, m, J.rot, inv);
+        return;
+    }
+    // frame pair: the second frame's analytic signal in the two free buffers,
+    // then per pair index the pair's eight floats in two 16-byte stores
+    const float2 *B = analytic_scaled(J.rf2 + (size_t)row * m, m, lgm, A == X ? Y : X, Z, tw);
+    float4 *__restrict__ out = J.pairs + (size_t)row * J.nsp * J.nf + J.fi / 2 * 2;
     for (int j = threadIdx.x; j < J.nsp; j += blockDim.x) {
-        const int k = j - kPadL;
-        const float2 a0 = (k >= 0 && k < m) ? A[k] : make_float2(0.f, 0.f);
-        const float2 a1 = (k + 1 >= 0 && k + 1 < m) ? A[k + 1] : make_float2(0.f, 0.f);
-        const float2 b = cmul(a1, J.rot);
-        out[j] = make_float4(0.5f * (a0.x + b.x) * inv, 0.5f * (a0.y + b.y) * inv, (b.x - a0.x) * inv,
-                             (b.y - a0.y) * inv);
+        const float4 a = demod_pair(A, j, m, J.rot, inv), b = demod_pair(B, j, m, J.rot, inv);
+        float4 *o = out + (size_t)j * J.nf;
+        o[0] = make_float4(a.x, b.x, a.y, b.y);
+        o[1] = make_float4(a.z, b.z, a.w, b.w);
     }
 }
 
@@ -845,15 +878,78 @@ __device__ __forceinline__ void accumulate_iq(uint32_t win, int wmax, int w0, fl
     }
 }
 
+// One channel of IQ beamforming into the ROWS pixels of this thread for NF
+// frames of one plan: the delay and the carrier phase of each pixel are formed
+// once and serve every frame.  The frames' pairs are staged by frame pair
+// (mid.re, mid.im, diff.re, diff.im of frames 2q and 2q + 1, eight floats),
+// so two frames move through each paired FP32 instruction; per frame the
+// operations and roundings are those of accumulate_iq.
+template <bool BB, int ROWS, int NF, bool CHECK>
+__device__ __forceinline__ void accumulate_iq_fn(uint32_t win, int wmax, int w0, float d2, int2 vr,
+                                                 int r_first, const RowPack<ROWS> &P,
+                                                 const int *Kc, float c1, float c2,
+                                                 f32x2_t (&Yr)[NF / 2][ROWS],
+                                                 f32x2_t (&Yi)[NF / 2][ROWS],
+                                                 f32x2_t (&Tr)[NF / 2][ROWS],
+                                                 f32x2_t (&Ti)[NF / 2][ROWS])
+{
+    const unsigned span = (unsigned)(vr.y - vr.x);
+    const f32x2_t D2 = pk2(d2, d2);
+#pragma unroll
+    for (int j = 0; j < ROWS; j += 2) {
+        float mm[2], aa[2];
+        delay2(D2, P.Z[j / 2], P.F[j / 2], mm[0], mm[1], aa[0], aa[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int jj = j + h;
+            const float al = aa[h];  // alpha - 1/2
+            const unsigned idx =
+                min((unsigned)(__float_as_int(mm[h]) + Kc[jj] - w0), (unsigned)(wmax - 1));
+            float sn, cs;
+            __sincosf(fmaf(al, c1, c2), &sn, &cs);
+            const f32x2_t AL = pk2(al, al), CS = pk2(cs, cs), SN = pk2(sn, sn),
+                          NSN = pk2(-sn, -sn);
+            const uint32_t a = win + idx * (uint32_t)(NF * 16);
+#pragma unroll
+            for (int q = 0; q < NF / 2; ++q) {
+                f32x2_t mre, mim, dre, dim;
+                asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];"
+                             : "=l"(mre), "=l"(mim)
+                             : "r"(a + (uint32_t)q * 32u));
+                asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];"
+                             : "=l"(dre), "=l"(dim)
+                             : "r"(a + (uint32_t)q * 32u + 16u));
+                const f32x2_t br = fma2(AL, dre, mre), bi = fma2(AL, dim, mim);
+                const f32x2_t sr = fma2(br, CS, mul2(bi, NSN)), si = fma2(br, SN, mul2(bi, CS));
+                if (!CHECK || (unsigned)(r_first + jj - vr.x) <= span) {
+                    Yr[q][jj] = add2(Yr[q][jj], sr);
+                    Yi[q][jj] = add2(Yi[q][jj], si);
+                    if (BB) {
+                        float qa, qb;
+                        upk2(fma2(sr, sr, fma2(si, si, pk2(1e-30f, 1e-30f))), qa, qb);
+                        const f32x2_t w = pk2(rsqrt_approx(sqrt_approx(qa)),
+                                              rsqrt_approx(sqrt_approx(qb)));
+                        Tr[q][jj] = fma2(sr, w, Tr[q][jj]);
+                        Ti[q][jj] = fma2(si, w, Ti[q][jj]);
+                    }
+                }
+            }
+        }
+    }
+}
+
 // Resident CTAs per SM the register budget is sized for: three 16- or 32-row
 // tiles, one 64-row tile (measured: capping 64-row tiles at two CTAs per SM
 // costs more in spills and lost overlap than the extra warps win).
 // Multi-frame jobs hold NF times the accumulators and NF windows per channel
 // and stage: two CTAs per SM when NF * ROWS = 8 (two frames of 4 rows, four
-// frames of 2 rows).
+// frames of 2 rows), and for every multi-frame IQ job (six complex or paired
+// sums per pixel and frame).
 template <int PREC, bool DMAS, bool CF, bool PDAS, int ROWS, int NF>
 constexpr int beamform_min_blocks()
 {
+    if (PREC == kPrecIQ && NF > 1)  // complex sums: two CTAs per SM for every multi-frame job
+        return 2;
     return ROWS == 8 ? 1 : (NF * ROWS >= 8 ? 2 : 3);
 }
 
@@ -1109,6 +1205,10 @@ __global__ void __launch_bounds__(beamform_threads<NF>(),
         // NF > 1: per frame pair (frames 2q, 2q + 1 in the two halves)
         constexpr int NP = NF > 1 ? NF / 2 : 1;
         f32x2_t FS1p[NP][ROWS], FT1[NP][ROWS], FT2[NP][ROWS], FYdp[NP][ROWS];
+        // IQ, NF > 1: FS1p / FYi the IQ-DAS sums, FT1 / FTi the per-angle BB-DMAS
+        // sums, FYdp / FY2i BB-DMAS
+        constexpr int NQ = IQ && NF > 1 ? NP : 1;
+        f32x2_t FYi[NQ][ROWS], FTi[NQ][ROWS], FY2i[NQ][ROWS];
         const f32x2_t zero2 = pk2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < ROWS; ++j) {
@@ -1116,6 +1216,9 @@ __global__ void __launch_bounds__(beamform_threads<NF>(),
 #pragma unroll
             for (int q = 0; q < NP; ++q)
                 FS1p[q][j] = FT1[q][j] = FT2[q][j] = FYdp[q][j] = zero2;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                FYi[q][j] = FTi[q][j] = FY2i[q][j] = zero2;
             Kc[j] = 0;
         }
 #pragma unroll
@@ -1161,6 +1264,9 @@ __global__ void __launch_bounds__(beamform_threads<NF>(),
 #pragma unroll
                     for (int q = 0; q < NP; ++q)
                         FT1[q][j] = FT2[q][j] = zero2;
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q)
+                        FTi[q][j] = zero2;
                 }
                 P.set(Z, fp);
             }
@@ -1176,7 +1282,23 @@ __global__ void __launch_bounds__(beamform_threads<NF>(),
             auto d2_of = [&](int c) { return lds_f32(d2b + (uint32_t)c * (kTileCols * 4)); };
             auto vr_of = [&](int c) { return lds_int2(vrb + (uint32_t)c * (kTileCols * 8)); };
             int k = 0;
-            if constexpr (IQ) {
+            if constexpr (IQ && NF > 1) {
+                // every channel once, its delay and carrier phase serving every frame
+#pragma unroll 1
+                for (; k < nf; ++k) {
+                    const int c = L[k];
+                    accumulate_iq_fn<DMAS, ROWS, NF, false>(win_of(c), wmax, w0_of(c), d2_of(c),
+                                                            make_int2(0, 0), r_first, P, Kc, c1,
+                                                            c2, FS1p, FYi, FT1, FTi);
+                }
+#pragma unroll 1
+                for (; k < nt; ++k) {
+                    const int c = L[k];
+                    accumulate_iq_fn<DMAS, ROWS, NF, true>(win_of(c), wmax, w0_of(c), d2_of(c),
+                                                           vr_of(c), r_first, P, Kc, c1, c2, FS1p,
+                                                           FYi, FT1, FTi);
+                }
+            } else if constexpr (IQ) {
 #pragma unroll 1
                 for (; k < nf; ++k) {
                     const int c = L[k];
@@ -1247,13 +1369,33 @@ __global__ void __launch_bounds__(beamform_threads<NF>(),
                                           fma2(pk2(-0.5f, -0.5f), FT2[q][j], FYdp[q][j]));
                 }
             }
-            if (DMAS && IQ && g == ngroups - 1) {  // Eq. (4): ((1/M) sum s^)^2 per angle
+            if (DMAS && IQ && NF == 1 && g == ngroups - 1) {  // Eq. (4): ((1/M) sum s^)^2 per angle
 #pragma unroll
                 for (int j = 0; j < ROWS; ++j) {
                     const float ur = T1[j] * invM[j], ui = Ti[j] * invM[j];
                     Yd[j] += fmaf(ur, ur, -ui * ui);
                     Y2i[j] = fmaf(2.f * ur, ui, Y2i[j]);
                 }
+            }
+            if (DMAS && IQ && NF > 1 && g == ngroups - 1) {  // the same per frame
+#pragma unroll
+                for (int q = 0; q < NQ; ++q)
+#pragma unroll
+                    for (int j = 0; j < ROWS; ++j) {
+                        float tr[2], ti[2], yd[2], y2[2];
+                        upk2(FT1[q][j], tr[0], tr[1]);
+                        upk2(FTi[q][j], ti[0], ti[1]);
+                        upk2(FYdp[q][j], yd[0], yd[1]);
+                        upk2(FY2i[q][j], y2[0], y2[1]);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const float ur = tr[h] * invM[j], ui = ti[h] * invM[j];
+                            yd[h] += fmaf(ur, ur, -ui * ui);
+                            y2[h] = fmaf(2.f * ur, ui, y2[h]);
+                        }
+                        FYdp[q][j] = pk2(yd[0], yd[1]);
+                        FY2i[q][j] = pk2(y2[0], y2[1]);
+                    }
             }
             if (PDAS && g == ngroups - 1) {  // Eq. (3) per angle, then the coherent sum
 #pragma unroll
@@ -1264,7 +1406,7 @@ __global__ void __launch_bounds__(beamform_threads<NF>(),
         if (!ok)
             return;  // warp-uniform: a bounded wait ran out (error bit set)
 
-        if constexpr (IQ) {  // magnitude images (and their maxima for the log stage)
+        if constexpr (IQ && NF == 1) {  // magnitude images (and their maxima for the log stage)
             const size_t plane = (size_t)nx * nz;
             float *__restrict__ y = J->y;
             const int modes = J->modes;
@@ -1316,6 +1458,42 @@ __global__ void __launch_bounds__(beamform_threads<NF>(),
                     upk2(FS1p[q][j], FS1[2 * q][j], FS1[2 * q + 1][j]);
                     upk2(FYdp[q][j], FYd[2 * q][j], FYd[2 * q + 1][j]);
                 }
+            if constexpr (IQ) {
+                // magnitude images, and each frame's maxima for the log stage
+                float FYi_[NF][ROWS], FY2i_[NF][ROWS];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q)
+#pragma unroll
+                    for (int j = 0; j < ROWS; ++j) {
+                        upk2(FYi[q][j], FYi_[2 * q][j], FYi_[2 * q + 1][j]);
+                        upk2(FY2i[q][j], FY2i_[2 * q][j], FY2i_[2 * q + 1][j]);
+                    }
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    float m0 = 0.f, m1 = 0.f;
+#pragma unroll
+                    for (int j = 0; j < ROWS; ++j) {
+                        FS1[f][j] = sqrtf(fmaf(FS1[f][j], FS1[f][j], FYi_[f][j] * FYi_[f][j]));
+                        FYd[f][j] = sqrtf(fmaf(FYd[f][j], FYd[f][j], FY2i_[f][j] * FY2i_[f][j]));
+                        if (col_ok && r_first + j < nz) {
+                            m0 = fmaxf(m0, FS1[f][j]);
+                            m1 = fmaxf(m1, FYd[f][j]);
+                        }
+                    }
+                    unsigned *mb = f == 0 ? J->maxbits : J->maxbits_more[f - 1];
+                    if (mb) {  // uniform per job; every lane of the warp is here
+                        const unsigned r0 = __reduce_max_sync(0xffffffffu, __float_as_uint(m0));
+                        const unsigned r1 = __reduce_max_sync(0xffffffffu, __float_as_uint(m1));
+                        if (lane == 0) {
+                            int slot = 0;
+                            if (modes & BF_DAS)
+                                atomicMax(mb + slot++, r0);
+                            if (modes & BF_DMAS)
+                                atomicMax(mb + slot, r1);
+                        }
+                    }
+                }
+            }
             if (staged_job(J)) {
                 // the tile's images into the staging area (plane p = frame, then
                 // combiner; column = lane), then the storer warp writes them out
@@ -1934,6 +2112,15 @@ cudaError_t launch_bf_frames(const BfJob *j, const int *pf, int njobs, int tiles
                 : launch_bf_t<kPrecBF16, false, false, false, ROWS, NF>(j, pf, njobs, tiles, smem, err, st);
 }
 
+// IQ-DAS (always) and BB-DMAS (in the DMAS slot) jobs of NF frames each.
+template <int ROWS, int NF>
+cudaError_t launch_bf_iq(const BfJob *j, const int *pf, int njobs, int tiles, size_t smem, int dmas,
+                         int *err, cudaStream_t st)
+{
+    return dmas ? launch_bf_t<kPrecIQ, true, false, false, ROWS, NF>(j, pf, njobs, tiles, smem, err, st)
+                : launch_bf_t<kPrecIQ, false, false, false, ROWS, NF>(j, pf, njobs, tiles, smem, err, st);
+}
+
 template <int PREC>
 cudaError_t launch_bf_p(const BfJob *jobs, const int *prefix, int njobs, int tiles, size_t smem,
                         int dmas, int cf, int pdas, int rows, int *err, cudaStream_t st)
@@ -1989,14 +2176,14 @@ cudaError_t launch_ingest(const IngestJob *jobs_dev, const int *blk_prefix_dev, 
     return cudaGetLastError();
 }
 
-size_t demod_smem_bytes(int ns) { return (size_t)3 * ns * sizeof(float2); }
+size_t demod_smem_bytes(int ns, bool pairs) { return (size_t)(pairs ? 4 : 3) * ns * sizeof(float2); }
 
 cudaError_t launch_demod(const DemodJob *jobs_dev, const int *row_prefix_dev, int njobs,
-                         int total_rows, int max_ns, cudaStream_t stream)
+                         int total_rows, int max_ns, bool pairs, cudaStream_t stream)
 {
     if (njobs <= 0 || total_rows <= 0)
         return cudaSuccess;
-    const size_t smem = demod_smem_bytes(max_ns);
+    const size_t smem = demod_smem_bytes(max_ns, pairs);
     int sms = 0;
     cudaError_t e = kernel_setup((const void *)demod_kernel, smem, 256, false, &sms, nullptr);
     if (e != cudaSuccess)
@@ -2014,11 +2201,23 @@ cudaError_t launch_beamform(const BfJob *jobs_dev, const int *tile_prefix_dev, i
     const int dmas = (variant & BF_DMAS) ? 1 : 0, cf = (variant & BF_CF) ? 1 : 0;
     const int pdas = (variant & BF_PDAS) ? 1 : 0;
     if (nf > 1 || rows == 2) {
-        // frames sharing the delays, and every two-row tile: DAS / DMAS of RF records
-        if (cf || pdas || prec == kPrecIQ)
+        // frames sharing the delays, and every two-row tile: DAS / DMAS of RF
+        // records, IQ-DAS / BB-DMAS of analytic signals
+        if (cf || pdas)
             return cudaErrorInvalidValue;
         const BfJob *j = jobs_dev;
         const int *pf = tile_prefix_dev;
+        if (prec == kPrecIQ) {
+            if (rows == 4 && nf == 2)
+                return launch_bf_iq<4, 2>(j, pf, njobs, total_tiles, smem_bytes, dmas, err_dev, stream);
+            if (rows == 2 && nf == 4)
+                return launch_bf_iq<2, 4>(j, pf, njobs, total_tiles, smem_bytes, dmas, err_dev, stream);
+            if (rows == 2 && nf == 2)
+                return launch_bf_iq<2, 2>(j, pf, njobs, total_tiles, smem_bytes, dmas, err_dev, stream);
+            if (rows == 2 && nf == 1)
+                return launch_bf_iq<2, 1>(j, pf, njobs, total_tiles, smem_bytes, dmas, err_dev, stream);
+            return cudaErrorInvalidValue;
+        }
         if (rows == 4 && nf == 2)
             return launch_bf_frames<4, 2>(j, pf, njobs, total_tiles, smem_bytes, prec, dmas, err_dev, stream);
         if (rows == 2 && nf == 4)

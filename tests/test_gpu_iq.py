@@ -119,3 +119,124 @@ def test_iq_argument_checks(torch):
             bf.bf_beamform_plain(h, rf, 1024, [0.0], bf.BF_IQDAS, out)
     finally:
         bf.bf_destroy(h)
+
+
+def assert_db_close(got, mag, what):
+    """dB image against the oracle's magnitude image `mag`: per pixel within the
+    first-order change of 20 log10(mag / max) under a magnitude error
+    E = 2e-6 of the peak, 8.686 E / max(mag, 10^(-70/20) peak) + 8.686 E / peak
+    (0.055 dB at the -70 dB floor)."""
+    peak = float(mag.max())
+    e = 2e-6 * peak
+    tol = 8.686 * e / np.maximum(mag, 10 ** (-70 / 20) * peak) + 8.686 * e / peak
+    err = np.abs(got - oracle.log_compress(mag))
+    assert np.all(err <= tol), "%s: %d pixels off, worst %.3f dB" % (what, int((err > tol).sum()),
+                                                                     float(err.max()))
+
+
+def scaled_frames(acq, n, seed0):
+    """n distinct records, frame k at (k + 2) / (n + 1) of its synthesized amplitude,
+    so that the frames' image maxima (and dB images) differ."""
+    out = []
+    for k in range(n):
+        rf = synth.speckle_points_frame(acq, seed=seed0 + k)[0].astype(np.float64)
+        out.append(np.round(rf * (k + 2) / (n + 1)).astype(np.int16))
+    return out
+
+
+# (tile rows, frames, depth): seven frames on 16-row tiles make one four-frame
+# job, one two-frame job and one frame alone; five on 32-row tiles two
+# two-frame jobs and one alone.  Depth 92 with aligned images takes the
+# bulk-copy epilogue, 90 the row-pair stores, 91 the per-pixel stores.
+@pytest.mark.parametrize("rows,n,nz", [("2", 7, 92), ("2", 7, 90), ("2", 7, 91), ("4", 5, 92)])
+def test_iq_frames_share_delay_and_carrier_phase(torch, monkeypatch, rows, n, nz):
+    """Multi-frame IQ jobs (Sec. II-B-1, Eq. (4)): every frame's IQ-DAS and
+    BB-DMAS images match the oracle, equal the frame's single-frame result on
+    the same tiles bit for bit (each frame's arithmetic is the single-frame
+    kernel's), and the log stage normalises each frame by its own maximum."""
+    monkeypatch.setenv("BF_TILE_ROWS", rows)
+    acq = synth.SPECKLE_POINTS_128.with_(nx=70, nz=nz, angles_deg=(-4.0, 4.0))
+    rfs = scaled_frames(acq, n, synth.BASE_SEED + 900)
+    flags = bf.BF_IQDAS | bf.BF_BBDMAS
+    h = make_handle(acq)
+    try:
+        assert bf.bf_plan_info(h, acq.n_samples, acq.angles_rad, flags)["rows"] == int(rows)
+        rf_d = [torch.from_numpy(r).cuda() for r in rfs]
+        for stage in (bf.BF_OUT_RF, bf.BF_OUT_LOGDB):
+            outs = [torch.full((2, acq.nx, acq.nz), float("nan"), device="cuda") for _ in rfs]
+            batch = bf.Batch([(h, rf_d[k], acq.n_samples, acq.angles_rad, flags | stage, outs[k])
+                              for k in range(n)])
+            try:
+                batch.launch()
+                batch.status()
+                got = [o.cpu().numpy().astype(np.float64) for o in outs]
+            finally:
+                batch.close()
+            for k in range(n):
+                ref = iq_ref(acq, rfs[k])
+                single = run_gpu(torch, acq, rfs[k], flags | stage, h=h)
+                np.testing.assert_array_equal(got[k], single, "frame %d stage %d" % (k, stage))
+                for m, name in enumerate(("iqdas", "bbdmas")):
+                    if stage == bf.BF_OUT_RF:
+                        assert_close(got[k][m], ref[name], bf.BF_PREC_FP32, "%s %d" % (name, k))
+                    else:
+                        assert_db_close(got[k][m], ref[name], "%s dB %d" % (name, k))
+    finally:
+        bf.bf_destroy(h)
+
+
+@pytest.mark.parametrize("flags", [bf.BF_IQDAS, bf.BF_BBDMAS])
+def test_iq_multi_frame_single_combiner(torch, monkeypatch, flags):
+    """Four-frame jobs with one IQ combiner: every frame against the oracle."""
+    monkeypatch.setenv("BF_TILE_ROWS", "2")
+    acq = synth.SPECKLE_POINTS_128.with_(nx=40, nz=64, angles_deg=(3.0,))
+    rfs = scaled_frames(acq, 4, synth.BASE_SEED + 920)
+    name = "iqdas" if flags == bf.BF_IQDAS else "bbdmas"
+    h = make_handle(acq)
+    try:
+        rf_d = [torch.from_numpy(r).cuda() for r in rfs]
+        outs = [torch.full((1, acq.nx, acq.nz), float("nan"), device="cuda") for _ in rfs]
+        batch = bf.Batch([(h, rf_d[k], acq.n_samples, acq.angles_rad, flags, outs[k])
+                          for k in range(4)])
+        try:
+            batch.launch()
+            batch.status()
+        finally:
+            batch.close()
+        for k in range(4):
+            assert_close(outs[k].cpu().numpy()[0].astype(np.float64), iq_ref(acq, rfs[k])[name],
+                         bf.BF_PREC_FP32, "%s %d" % (name, k))
+    finally:
+        bf.bf_destroy(h)
+
+
+def test_iq_job_with_mixed_output_stages(torch, monkeypatch):
+    """Frames of one plan asking for different outputs share a job: the
+    log-compressed frames get their own maxima, the magnitude frames none."""
+    monkeypatch.setenv("BF_TILE_ROWS", "2")
+    acq = synth.SPECKLE_POINTS_128.with_(nx=48, nz=80, angles_deg=(0.0,))
+    rfs = scaled_frames(acq, 4, synth.BASE_SEED + 940)
+    base = bf.BF_IQDAS | bf.BF_BBDMAS
+    stages = [bf.BF_OUT_LOGDB, bf.BF_OUT_RF, bf.BF_OUT_LOGDB, bf.BF_OUT_ENV]
+    h = make_handle(acq)
+    try:
+        rf_d = [torch.from_numpy(r).cuda() for r in rfs]
+        outs = [torch.full((2, acq.nx, acq.nz), float("nan"), device="cuda") for _ in rfs]
+        batch = bf.Batch([(h, rf_d[k], acq.n_samples, acq.angles_rad, base | stages[k], outs[k])
+                          for k in range(4)])
+        try:
+            batch.launch()
+            batch.status()
+        finally:
+            batch.close()
+        for k in range(4):
+            got = outs[k].cpu().numpy().astype(np.float64)
+            np.testing.assert_array_equal(got, run_gpu(torch, acq, rfs[k], base | stages[k], h=h))
+            ref = iq_ref(acq, rfs[k])
+            for m, name in enumerate(("iqdas", "bbdmas")):
+                if stages[k] == bf.BF_OUT_LOGDB:
+                    assert_db_close(got[m], ref[name], "%s dB %d" % (name, k))
+                else:
+                    assert_close(got[m], ref[name], bf.BF_PREC_FP32, "%s %d" % (name, k))
+    finally:
+        bf.bf_destroy(h)
