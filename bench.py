@@ -56,6 +56,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-serving", action="store_true", help="skip the short serving-latency leg")
+    p.add_argument("--no-tune", action="store_true",
+                   help="skip the autotuner: the library's default tiles, or BF_TILE_ROWS (profiling)")
+    p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling)")
     p.add_argument("--workload", default="cyst512",
                    choices=["cyst512", "batch256", "serving", "precision", "sweep", "iq", "fk"],
                    help="cyst512: the headline line; the others print informational lines")
@@ -71,11 +74,11 @@ def dist_info():
 
 
 # DRAM bytes (read + write) of one beamform_kernel launch from an ncu capture
-# of the 512 x 512 workload at 8 frames per launch (the traffic grows with the
-# frames).  Valid only for the kernel source the capture was taken on: any
-# other source reports null.
-TRAFFIC_CAPTURE = {"sources_sha256": "f32a54e843874d3d85f7daf40e8e8fc6e8c3d8505ed56b5d7c9150dfc627cb85",
-                   "frames": 8, "bytes": 4688640 + 0}
+# of the 512 x 512 workload at the benchmark's own 64 frames per launch
+# (other frame counts are scaled by the frames).  Valid only for the kernel
+# source the capture was taken on: any other source reports null.
+TRAFFIC_CAPTURE = {"sources_sha256": "07585f2fc6d4843550826e76a27c2c9ce49fc5f80016fd8958bec39cbd465eff",
+                   "frames": 64, "bytes": 32043264 + 80064768}
 
 
 def beamform_traffic(frames):
@@ -265,7 +268,11 @@ def run_ours(args):
     active = int(np.clip(valid[..., 1] - valid[..., 0] + 1, 0, None).sum())
     nm = 2
     # tile configuration from the library's autotuner (setup, not timed)
-    tune = bf.bf_autotune(h, acq.n_samples, acq.angles_rad, flags, frames=min(B, 16))
+    if args.no_tune:
+        tune = {"rows": bf.bf_plan_info(h, acq.n_samples, acq.angles_rad, flags)["rows"],
+                "stage_bytes": None, "candidates_us": None}
+    else:
+        tune = bf.bf_autotune(h, acq.n_samples, acq.angles_rad, flags, frames=min(B, 16))
     rf_dev = [torch.from_numpy(rfs[k % len(rfs)]).to(dev) for k in range(B)]
     out_dev = [torch.empty((nm, acq.nx, acq.nz), dtype=torch.float32, device=dev) for _ in range(B)]
     batch = bf.Batch([(h, rf_dev[k], acq.n_samples, acq.angles_rad, flags, out_dev[k])
@@ -340,13 +347,15 @@ def run_ours(args):
                 if record:
                     lat.extend([time.perf_counter() - t_sub0] * B)
 
-    e2e_run(max(2, args.warmup), False)
-    barrier()
-    t0 = time.perf_counter()
-    e2e_run(e2e_steps, True)
-    t_e2e = time.perf_counter() - t0
+    if not args.no_e2e:
+        e2e_run(max(2, args.warmup), False)
+        barrier()
+        t0 = time.perf_counter()
+        e2e_run(e2e_steps, True)
+        t_e2e = time.perf_counter() - t0
     clocks = sampler.stop()
-    t_e2e = max_over_ranks(t_e2e, dev)
+    if not args.no_e2e:
+        t_e2e = max_over_ranks(t_e2e, dev)
 
     # ---- results (rank 0)
     units_step = B * nominal_units(acq)
@@ -376,11 +385,12 @@ def run_ours(args):
         "dtype": {"fp32": "f32", "fp16": "f16-storage/f32", "bf16": "bf16-storage/f32"}[args.prec],
         "data": "synthetic",
         "frames_per_s": ws * B * args.steps / t_dev,
-        "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
-                       "p99": 1e3 * float(np.percentile(lat, 99)),
-                       "source": "e2e leg: a step's %d frames submitted together (%d steps in flight), "
-                                 "latency from submission to every result of the step on the "
-                                 "host" % (B, E2E_DEPTH)},
+        "latency_ms": None if args.no_e2e else {
+            "p50": 1e3 * float(np.percentile(lat, 50)),
+            "p99": 1e3 * float(np.percentile(lat, 99)),
+            "source": "e2e leg: a step's %d frames submitted together (%d steps in flight), "
+                      "latency from submission to every result of the step on the host"
+                      % (B, E2E_DEPTH)},
         "config": {"workload": WORKLOAD, "frames_per_step": B, "global_batch": B * ws,
                    "parallelism": "replicas (frames sharded, no collective)",
                    "l2": "flushed before every timed step (256 MiB write)",
@@ -396,11 +406,12 @@ def run_ours(args):
                                    "triple + 1 receive-distance root per (pixel, channel, angle) "
                                    "shared by the step's %d frames)" % (sm_count, sm_max, B),
                      "traffic": beamform_traffic(B),
-                     "traffic_unit": "DRAM bytes per launch (ncu capture scaled by frames)"},
-        "e2e": {"value": job_value(ws, units_step, e2e_steps, t_e2e), "unit": UNIT,
-                "h2d_bytes_per_step": B * rfs[0].nbytes,
-                "d2h_bytes_per_step": B * nm * acq.nx * acq.nz * 4,
-                "frames_per_s": ws * B * e2e_steps / t_e2e},
+                     "traffic_unit": "DRAM bytes per launch (ncu capture at 64 frames per launch)"},
+        "e2e": None if args.no_e2e else {
+            "value": job_value(ws, units_step, e2e_steps, t_e2e), "unit": UNIT,
+            "h2d_bytes_per_step": B * rfs[0].nbytes,
+            "d2h_bytes_per_step": B * nm * acq.nx * acq.nz * 4,
+            "frames_per_s": ws * B * e2e_steps / t_e2e},
         "gpu_launches": launches * args.steps,
         "clocks": clocks,
     }
