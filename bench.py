@@ -556,41 +556,45 @@ def run_iq(args):
 
 def run_fk(args):
     """Plane-wave f-k migration of the 64-channel, 2048-sample cyst record (one
-    and three angles): time per frame on the device and rel-L2 against the oracle."""
+    and three angles; the exact plane-wave mapping and Stolt's): time per frame
+    on the device and rel-L2 against the oracle."""
     import oracle
 
     torch, bf = _setup_gpu()
     rows = []
     for angles in ((0.0,), (-7.0, 0.0, 7.0)):
-        acq = synth.CYST_WIRES_512.with_(angles_deg=angles)
-        rf, _ = synth.cyst_wires_frame(acq)
-        h = _handle(bf, acq)
-        stream = torch.cuda.Stream()
-        bf.bf_set_stream(h, stream)
-        rf_d = torch.from_numpy(rf).cuda()
-        out = torch.empty((acq.n_elements, acq.n_samples), dtype=torch.float32, device="cuda")
-        for _ in range(5):
-            bf.bf_fkmig(h, rf_d, acq.n_samples, acq.angles_rad, bf.BF_OUT_LOGDB, out)
-        torch.cuda.synchronize()
-        ts = []
-        for _ in range(50):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            bf.bf_fkmig(h, rf_d, acq.n_samples, acq.angles_rad, bf.BF_OUT_LOGDB, out)
-            b.record(stream)
+        for mapping, flag, ref_fn in (("exact", 0, oracle.fk_migrate),
+                                      ("stolt", bf.BF_FK_STOLT, oracle.fk_stolt)):
+            acq = synth.CYST_WIRES_512.with_(angles_deg=angles)
+            rf, _ = synth.cyst_wires_frame(acq)
+            h = _handle(bf, acq)
+            stream = torch.cuda.Stream()
+            bf.bf_set_stream(h, stream)
+            rf_d = torch.from_numpy(rf).cuda()
+            out = torch.empty((acq.n_elements, acq.n_samples), dtype=torch.float32, device="cuda")
+            for _ in range(5):
+                bf.bf_fkmig(h, rf_d, acq.n_samples, acq.angles_rad, bf.BF_OUT_LOGDB | flag, out)
             torch.cuda.synchronize()
-            ts.append(a.elapsed_time(b))
-        bf.bf_fkmig(h, rf_d, acq.n_samples, acq.angles_rad, bf.BF_OUT_RF, out)
-        torch.cuda.synchronize()
-        ref = oracle.fk_migrate(rf, acq.pitch_m, acq.angles_rad, acq.fs_hz, acq.c_mps)
-        got = out.cpu().numpy().astype(np.float64)
-        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-        t0 = time.perf_counter()
-        oracle.fk_migrate(rf, acq.pitch_m, acq.angles_rad, acq.fs_hz, acq.c_mps)
-        cpu_ms = 1e3 * (time.perf_counter() - t0)
-        rows.append({"angles": len(angles), "gpu_ms": statistics.median(ts), "frames_per_s":
-                     1e3 / statistics.median(ts), "oracle_ms_numpy": cpu_ms, "rel_l2": err})
-        bf.bf_destroy(h)
+            ts = []
+            for _ in range(50):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                bf.bf_fkmig(h, rf_d, acq.n_samples, acq.angles_rad, bf.BF_OUT_LOGDB | flag, out)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            bf.bf_fkmig(h, rf_d, acq.n_samples, acq.angles_rad, bf.BF_OUT_RF | flag, out)
+            torch.cuda.synchronize()
+            ref = ref_fn(rf, acq.pitch_m, acq.angles_rad, acq.fs_hz, acq.c_mps)
+            got = out.cpu().numpy().astype(np.float64)
+            err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+            t0 = time.perf_counter()
+            ref_fn(rf, acq.pitch_m, acq.angles_rad, acq.fs_hz, acq.c_mps)
+            cpu_ms = 1e3 * (time.perf_counter() - t0)
+            rows.append({"mapping": mapping, "angles": len(angles), "gpu_ms": statistics.median(ts),
+                         "frames_per_s": 1e3 / statistics.median(ts), "oracle_ms_numpy": cpu_ms,
+                         "rel_l2": err})
+            bf.bf_destroy(h)
     print(json.dumps({"workload": "plane-wave f-k migration, 64 ch x 2048 samples (cyst + wires), "
                                   "native grid 64 x 2048, -70 dB log, one frame per call",
                       "rows": rows}), flush=True)
