@@ -46,8 +46,42 @@ __device__ __constant__ float2 kW32[16] = {
     {-7.071067812e-01f, 7.071067812e-01f}, {-8.314696123e-01f, 5.555702330e-01f},
     {-9.238795325e-01f, 3.826834324e-01f}, {-9.807852804e-01f, 1.950903220e-01f}};
 
-__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex add / subtract as one paired FP32 instruction (Blackwell f32x2):
+// the real and imaginary parts of a float2 sit in a register pair.
+__device__ __forceinline__ float2 c_add(float2 a, float2 b)
+{
+    unsigned long long ra, rb, rc;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(rc) : "l"(ra), "l"(rb));
+    float2 c;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(c.x), "=f"(c.y) : "l"(rc));
+    return c;
+}
+
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b)
+{
+    unsigned long long ra, rb, rc;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rc) : "l"(ra), "l"(rb));
+    float2 c;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(c.x), "=f"(c.y) : "l"(rc));
+    return c;
+}
+
+// s * a + b with s a scalar (both halves), as one paired FMA.
+__device__ __forceinline__ float2 c_sfma(float s, float2 a, float2 b)
+{
+    unsigned long long rs, ra, rb, rc;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(rs) : "f"(s));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rc) : "l"(rs), "l"(ra), "l"(rb));
+    float2 c;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(c.x), "=f"(c.y) : "l"(rc));
+    return c;
+}
 
 // b * W_32^e (INV: conjugate), W_32 = exp(-2 pi i / 32), 0 <= e < 32; e is a
 // compile-time constant wherever this is used (quarter turns are swaps).
@@ -72,11 +106,16 @@ template <bool INV>
 __device__ __forceinline__ void dft4(float2 &a, float2 &b, float2 &c, float2 &d)
 {
     const float2 t0 = c_add(a, c), t1 = c_sub(a, c), t2 = c_add(b, d), u = c_sub(b, d);
-    const float2 t3 = INV ? make_float2(-u.y, u.x) : make_float2(u.y, -u.x);  // u W_4
     a = c_add(t0, t2);
     c = c_sub(t0, t2);
-    b = c_add(t1, t3);
-    d = c_sub(t1, t3);
+    // t1 +- u W_4 (W_4 = -i, INV: +i): the swapped halves in scalar operations
+    if (INV) {
+        b = make_float2(t1.x - u.y, t1.y + u.x);
+        d = make_float2(t1.x + u.y, t1.y - u.x);
+    } else {
+        b = make_float2(t1.x + u.y, t1.y - u.x);
+        d = make_float2(t1.x - u.y, t1.y + u.x);
+    }
 }
 
 // In-register 16-point DFT, natural order in and out: x[k] <- sum_n x[n]
@@ -175,7 +214,7 @@ __device__ __forceinline__ void fft_warp(float2 (&v)[kR], uint32_t buf, uint32_t
             const float2 tw = w32mul<false>(v[k], k);
             const float2 own = h ? tw : v[k];
             const float2 oth = shfl_pair(own);
-            v[k] = make_float2(fmaf(sgn, own.x, oth.x), fmaf(sgn, own.y, oth.y));
+            v[k] = c_sfma(sgn, own, oth);
         }
     } else {
         // radix-2 step over k2 (k2 and k2 + 16 in the two lanes): the even lane
@@ -184,7 +223,7 @@ __device__ __forceinline__ void fft_warp(float2 (&v)[kR], uint32_t buf, uint32_t
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             const float2 oth = shfl_pair(v[k]);
-            const float2 s = make_float2(fmaf(sgn, v[k].x, oth.x), fmaf(sgn, v[k].y, oth.y));
+            const float2 s = c_sfma(sgn, v[k], oth);
             v[k] = h ? w32mul<true>(s, k) : s;
         }
         dft16<true>(v);  // register m: n2 = 2 m + h
