@@ -2033,9 +2033,11 @@ __global__ void __launch_bounds__(256) log_kernel(const LogJob *__restrict__ job
                                                   const int *__restrict__ blk_prefix, int njobs,
                                                   float dr)
 {
-    const int jb = find_job(blk_prefix, njobs, blockIdx.x);
+    // blocks in reverse: the envelopes written last (still in L2) are read first
+    const int blk = gridDim.x - 1 - blockIdx.x;
+    const int jb = find_job(blk_prefix, njobs, blk);
     const LogJob J = jobs[jb];
-    const size_t base = (size_t)(blockIdx.x - __ldg(blk_prefix + jb)) * kLogPerBlock;
+    const size_t base = (size_t)(blk - __ldg(blk_prefix + jb)) * kLogPerBlock;
     const float peak = __uint_as_float(__ldg(J.maxbits));
     // 20 log10(e / peak) = (20 log10 2) (log2 e - log2 peak), the logarithm on the
     // special-function unit (absolute error ~1e-6 of a unit of log2: ~1e-5 dB)
@@ -2052,10 +2054,11 @@ __global__ void __launch_bounds__(256) log_kernel(const LogJob *__restrict__ job
             e0 = __ldg(reinterpret_cast<const float4 *>(J.env + p0));
         if (ok1)
             e1 = __ldg(reinterpret_cast<const float4 *>(J.env + p1));
+        // streaming stores: the dB images do not displace envelopes still to be read
         if (ok0)
-            *reinterpret_cast<float4 *>(J.out + p0) = make_float4(db(e0.x), db(e0.y), db(e0.z), db(e0.w));
+            __stcs(reinterpret_cast<float4 *>(J.out + p0), make_float4(db(e0.x), db(e0.y), db(e0.z), db(e0.w)));
         if (ok1)
-            *reinterpret_cast<float4 *>(J.out + p1) = make_float4(db(e1.x), db(e1.y), db(e1.z), db(e1.w));
+            __stcs(reinterpret_cast<float4 *>(J.out + p1), make_float4(db(e1.x), db(e1.y), db(e1.z), db(e1.w)));
         return;
     }
     for (int t = threadIdx.x; t < kLogPerBlock; t += blockDim.x) {
