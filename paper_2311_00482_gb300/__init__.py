@@ -156,6 +156,11 @@ def _ptr(x):
     return int(x)
 
 
+def _nbytes(x):
+    """Bytes of a numpy array or torch tensor."""
+    return x.nbytes
+
+
 def _angles(angles):
     a = np.ascontiguousarray(np.atleast_1d(np.asarray(angles, dtype=np.float64)))
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -319,10 +324,9 @@ def bf_submit_many_into(h, rfs, n_samples, angles_rad, flags, outs):
     n = len(rfs)
     if len(outs) != n:
         raise ValueError("one destination per frame")
-    ptrs = (ctypes.c_void_p * n)(*[_ptr(r) for r in rfs])
-    optr = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
-    nbytes = min((o.nbytes if isinstance(o, np.ndarray) else o.numel() * o.element_size())
-                 for o in outs) if n else 0
+    ptrs = (ctypes.c_void_p * n)(*map(_ptr, rfs))
+    optr = (ctypes.c_void_p * n)(*map(_ptr, outs))
+    nbytes = min(map(_nbytes, outs)) if n else 0
     t = (ctypes.c_uint64 * n)()
     done = ctypes.c_int32()
     rc = load().bf_submit_many_into(h, n, ptrs, int(n_samples), ap, len(a), int(flags), optr,
@@ -341,9 +345,8 @@ def bf_poll_many(h, tickets, outs=None, timeout_us=-1) -> int:
     nbytes = 0
     optr = None
     if outs is not None:
-        optr = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
-        nbytes = min((o.nbytes if isinstance(o, np.ndarray) else o.numel() * o.element_size())
-                     for o in outs)
+        optr = (ctypes.c_void_p * n)(*map(_ptr, outs))
+        nbytes = min(map(_nbytes, outs))
     return _check(load().bf_poll_many(h, n, tk, optr, nbytes, int(timeout_us)),
                   allow=(BF_OK, BF_PENDING))
 

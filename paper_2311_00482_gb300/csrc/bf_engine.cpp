@@ -793,6 +793,7 @@ int Engine::poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const
     }
     using clk = std::chrono::steady_clock;
     const auto deadline = clk::now() + std::chrono::microseconds(timeout_us > 0 ? timeout_us : 0);
+    const Batch *finished = nullptr;  // the last batch seen complete (tickets share batches)
     for (auto &req : reqs) {  // launched and finished?
         {
             std::unique_lock<std::mutex> lk(mu_);
@@ -806,7 +807,7 @@ int Engine::poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const
                     return fail(BF_ETIMEDOUT, "a ticket was not launched within the timeout");
             }
         }
-        if (req->rc)
+        if (req->rc || req->batch.get() == finished)
             continue;
         const auto spin_until = clk::now() + std::chrono::microseconds(500);
         for (;;) {
@@ -823,6 +824,7 @@ int Engine::poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const
             else
                 std::this_thread::sleep_for(std::chrono::microseconds(20));
         }
+        finished = req->batch.get();
     }
     cudaSetDevice(device_);
     int rc = BF_OK;
@@ -832,13 +834,16 @@ int Engine::poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const
     // the rest through the slots' pinned staging
     int direct = 0;
     std::vector<int> staged_dest;  // results the batch left in pinned staging
+    const Batch *checked = nullptr;  // the last batch whose completion was confirmed
     for (int k = 0; k < n; ++k) {
         Request &r = *reqs[k];
         int rk = r.rc ? fail(r.rc, "%s", r.err.c_str()) : BF_OK;
-        if (!rk) {
+        if (!rk && r.batch.get() != checked) {
             cudaError_t q = cudaEventQuery(r.batch->res->done);
             if (q != cudaSuccess)
                 rk = cuda_fail(q, "batch execution");
+            else
+                checked = r.batch.get();
         }
         if (!rk) {
             const int v = *(volatile int *)r.batch->res->err_host;
