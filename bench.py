@@ -507,7 +507,10 @@ def run_iq(args):
     B = args.frames
     h = _handle(bf, acq)
     flags = bf.BF_IQDAS | bf.BF_BBDMAS | bf.BF_OUT_LOGDB
-    tune = bf.bf_autotune(h, acq.n_samples, acq.angles_rad, flags, frames=16)
+    if args.no_tune:
+        tune = {"rows": bf.bf_plan_info(h, acq.n_samples, acq.angles_rad, flags)["rows"]}
+    else:
+        tune = bf.bf_autotune(h, acq.n_samples, acq.angles_rad, flags, frames=16)
     rf_dev = [torch.from_numpy(rfs[k % len(rfs)]).cuda() for k in range(B)]
     out_dev = [torch.empty((2, acq.nx, acq.nz), dtype=torch.float32, device="cuda") for _ in range(B)]
     batch = bf.Batch([(h, rf_dev[k], acq.n_samples, acq.angles_rad, flags, out_dev[k])
