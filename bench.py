@@ -323,7 +323,9 @@ def run_ours(args):
     # collected, so one set of host results per step in flight plus one
     host_out = [[torch.empty((nm, acq.nx, acq.nz), dtype=torch.float32).pin_memory()
                  for _ in range(B)] for _ in range(E2E_DEPTH + 1)]
-    e2e_steps = max(2, min(args.steps, 10))
+    # steps of the end-to-end leg: enough that filling and draining the
+    # E2E_DEPTH steps in flight does not dominate (about 50 ms at 64 frames)
+    e2e_steps = 50
     lat = []
 
     def e2e_run(steps, record):
