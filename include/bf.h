@@ -363,9 +363,9 @@ BF_API int bf_plan_info(bf_handle *h, int32_t n_samples, const double *angles_ra
  * beamforming time in microseconds of every candidate (n_candidates
  * entries; -1 where a configuration does not fit).  Two-row tiles (16 rows,
  * up to four frames of one workload per job sharing every delay) serve DAS
- * and DMAS of RF records only; other work on a workload tuned to them keeps
- * the default tiles.  The environment variable BF_TILE_ROWS=2, 4 or 8
- * overrides any tuned choice. */
+ * and DMAS of RF records and IQ-DAS / BB-DMAS; other work on a workload
+ * tuned to them keeps the default tiles.  The environment variable
+ * BF_TILE_ROWS=2, 4 or 8 overrides any tuned choice. */
 BF_API int bf_autotune(bf_handle *h, int32_t n_samples, const double *angles_rad,
                        int32_t n_angles, uint32_t mode_and_flags, int32_t frames,
                        int32_t *rows_out, int32_t *stage_bytes_out, float *candidate_us,

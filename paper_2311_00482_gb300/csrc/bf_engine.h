@@ -233,8 +233,9 @@ namespace bfi {
 
 // Plan of a frame with these arguments (`flags`: its mode and precision bits).
 // cfg < 0: the configuration bf_autotune chose for this workload, else the
-// default; a two-row configuration serves DAS / DMAS of RF records only (an
-// explicit one is refused for other frames, a tuned one replaced by the default).
+// default; a two-row configuration serves DAS / DMAS of RF records and
+// IQ-DAS / BB-DMAS only (an explicit one is refused for other frames, a tuned
+// one replaced by the default).
 int handle_plan(bf_handle *h, int ns, const double *angles, int na, uint32_t flags, Plan **out,
                 int cfg = -1);
 int check_frame_args(bf_handle *h, int ns, const double *angles, int na, uint32_t flags);
@@ -248,7 +249,8 @@ int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *ang
                   uint32_t flags, float *out_dev, FrameScratch &s, FramePrep &fp, int cfg = -1,
                   int nf_cap = 1);
 // Frames (at most cap) of one plan that can share a beamforming job with a
-// frame of these flags (1: DAS / DMAS of RF records only share).
+// frame of these flags (1 unless the combiners are DAS / DMAS of RF records
+// or IQ-DAS / BB-DMAS; IQ frames with records above 4096 samples alone).
 int job_frames_cap(const Plan *p, uint32_t flags, int cap);
 void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl);
 int upload_maps(std::vector<FramePrep> &frames, cudaStream_t st, bool async);

@@ -31,7 +31,8 @@ inline int tile_rows(int rows_per_thread) { return kWarps * rows_per_thread; }
 // Tile configurations the autotuner chooses from: rows per thread (tile
 // height 8 * rows) and the target bytes of one pipeline stage's sample
 // windows (channels per stage).  Entry 0 is the default.  Two-row tiles serve
-// DAS / DMAS of RF records only, with up to four frames per job.
+// DAS / DMAS of RF records and IQ-DAS / BB-DMAS, with up to four frames per
+// job.
 struct TileConfig {
     int rows, stage_bytes;
 };
@@ -213,8 +214,8 @@ size_t demod_smem_bytes(int ns, bool pairs);
 // f-k migration launches (bf_kernels.cu), in order on `stream`.
 cudaError_t launch_fkmig(const FkJob &job, cudaStream_t stream);
 // nf: frames per job (1, 2 or 4, with 4 on two-row tiles only; the frames of
-// one job share the delays; DAS / DMAS variants of the RF precisions only when
-// nf > 1 or rows == 2).
+// one job share the delays; DAS / DMAS variants of the RF precisions, or the
+// IQ combiners, only when nf > 1 or rows == 2).
 cudaError_t launch_beamform(const BfJob *jobs_dev, const int *tile_prefix_dev, int njobs,
                             int total_tiles, size_t smem_bytes, int prec, int variant, int rows,
                             int nf, int *err_dev, cudaStream_t stream);

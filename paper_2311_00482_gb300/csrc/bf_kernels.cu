@@ -18,8 +18,9 @@
 //                    (DAS, signed-sqrt DMAS, coherence factor, pDAS), compounded
 //                    over angles (Eq. (1), Sec. II-B).  A job may carry 2 or 4
 //                    frames of one plan (their pairs interleaved by frame):
-//                    every delay serves all of them, and a storer warp writes
-//                    the staged tile images with bulk copies
+//                    every delay (and for IQ-DAS / BB-DMAS, Eq. (4), the
+//                    carrier phase) serves all of them, and a storer warp
+//                    writes the staged tile images with bulk copies
 //   envelope_kernel  per image column the analytic signal along depth via a
 //                    shared-memory radix-8 Stockham FFT (Bluestein for other
 //                    lengths), one-sided mask and optional [f0, 3 f0]

@@ -240,3 +240,35 @@ def test_iq_job_with_mixed_output_stages(torch, monkeypatch):
                     assert_close(got[m], ref[name], bf.BF_PREC_FP32, "%s %d" % (name, k))
     finally:
         bf.bf_destroy(h)
+
+
+def test_iq_records_too_long_for_frame_pairs_run_alone(torch, monkeypatch):
+    """8192-sample records: a frame pair's demodulation would need four 64 KB
+    transform buffers in one CTA, so such IQ frames take one-frame jobs even
+    on 16-row tiles; a batch of three still matches the oracle and equals the
+    frames beamformed alone."""
+    monkeypatch.setenv("BF_TILE_ROWS", "2")
+    acq = synth.SPECKLE_POINTS_128.with_(nx=24, nz=40, n_samples=8192, z0_m=20e-3, z1_m=25e-3,
+                                         angles_deg=(2.0,))
+    rfs = scaled_frames(acq, 3, synth.BASE_SEED + 960)
+    flags = bf.BF_IQDAS | bf.BF_BBDMAS
+    h = make_handle(acq)
+    try:
+        assert bf.bf_plan_info(h, acq.n_samples, acq.angles_rad, flags)["rows"] == 2
+        rf_d = [torch.from_numpy(r).cuda() for r in rfs]
+        outs = [torch.full((2, acq.nx, acq.nz), float("nan"), device="cuda") for _ in rfs]
+        batch = bf.Batch([(h, rf_d[k], acq.n_samples, acq.angles_rad, flags, outs[k])
+                          for k in range(3)])
+        try:
+            batch.launch()
+            batch.status()
+        finally:
+            batch.close()
+        for k in range(3):
+            got = outs[k].cpu().numpy().astype(np.float64)
+            np.testing.assert_array_equal(got, run_gpu(torch, acq, rfs[k], flags, h=h))
+            ref = iq_ref(acq, rfs[k])
+            assert_close(got[0], ref["iqdas"], bf.BF_PREC_FP32, "iqdas %d" % k)
+            assert_close(got[1], ref["bbdmas"], bf.BF_PREC_FP32, "bbdmas %d" % k)
+    finally:
+        bf.bf_destroy(h)
