@@ -321,8 +321,10 @@ def run_ours(args):
     host_rf = [torch.from_numpy(rfs[k % len(rfs)]).pin_memory() for k in range(B)]
     # E2E_DEPTH steps in flight: step k + E2E_DEPTH is submitted before step k is
     # collected, so one set of host results per step in flight plus one
-    host_out = [[torch.empty((nm, acq.nx, acq.nz), dtype=torch.float32).pin_memory()
-                 for _ in range(B)] for _ in range(E2E_DEPTH + 1)]
+    # (each set one pinned buffer: the frames' images contiguous, so that a
+    # batch's results leave in one transfer)
+    host_out = [list(torch.empty((B, nm, acq.nx, acq.nz), dtype=torch.float32).pin_memory())
+                for _ in range(E2E_DEPTH + 1)]
     # steps of the end-to-end leg: enough that filling and draining the
     # E2E_DEPTH steps in flight does not dominate (about 50 ms at 64 frames)
     e2e_steps = 50
@@ -341,7 +343,8 @@ def run_ours(args):
             if k < steps:
                 t_sub = time.perf_counter()
                 inflight.append((bf.bf_submit_many_into(h, host_rf, acq.n_samples, acq.angles_rad,
-                                                        flags, host_out[k % (E2E_DEPTH + 1)]),
+                                                        flags | bf.BF_DEST_ONE_BUFFER,
+                                                        host_out[k % (E2E_DEPTH + 1)]),
                                  t_sub))
             if len(inflight) > E2E_DEPTH or (k >= steps and inflight):
                 tickets, t_sub0 = inflight.pop(0)

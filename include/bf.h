@@ -89,6 +89,9 @@ enum { BF_OUT_RF = 0, BF_OUT_ENV = 1 << 8, BF_OUT_LOGDB = 2 << 8, BF_OUT_MASK = 
 enum { BF_IQDAS = 1 << 12, BF_BBDMAS = 1 << 13, BF_IQ_MASK = 3 << 12 };
 /* bf_fkmig only: Stolt's mapping instead of the exact plane-wave one (bit 16). */
 enum { BF_FK_STOLT = 1 << 16 };
+/* bf_submit_many_into only: the destinations lie in one allocation (bit 17),
+ * so that destinations back to back leave in one transfer. */
+enum { BF_DEST_ONE_BUFFER = 1 << 17 };
 
 enum {
     BF_OK = 0,
@@ -239,8 +242,12 @@ BF_API int bf_submit_many(bf_handle *h, int32_t n, const int16_t *const *rf, int
  * memory through the engine's page-locked staging, copied on by the poll.
  * Each destination must stay valid and untouched until its ticket is polled:
  * bf_poll / bf_poll_many then only wait (their out / outs arguments are
- * ignored for these tickets) and release.  Errors as bf_submit_many, plus
- * BF_EINVAL for a null or too small destination. */
+ * ignored for these tickets) and release.  With BF_DEST_ONE_BUFFER in
+ * mode_and_flags the caller states that every outs[k] lies in one allocation
+ * (views of one buffer): the results of frames whose destinations follow one
+ * another in memory (outs[k + 1] == outs[k] + bf_output_bytes / 4) then leave
+ * their batch in one transfer.  Errors as bf_submit_many, plus BF_EINVAL for
+ * a null or too small destination. */
 BF_API int bf_submit_many_into(bf_handle *h, int32_t n, const int16_t *const *rf,
                                int32_t n_samples, const double *angles_rad, int32_t n_angles,
                                uint32_t mode_and_flags, float *const *outs, size_t out_bytes,

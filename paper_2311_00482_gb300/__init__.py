@@ -23,6 +23,7 @@ from . import build as _build
 BF_DAS, BF_DMAS, BF_CF, BF_PDAS, BF_MODE_MASK = 1, 2, 4, 8, 15
 BF_IQDAS, BF_BBDMAS, BF_IQ_MASK = 1 << 12, 1 << 13, 3 << 12
 BF_FK_STOLT = 1 << 16
+BF_DEST_ONE_BUFFER = 1 << 17
 BF_PREC_FP32, BF_PREC_FP16, BF_PREC_BF16, BF_PREC_MASK = 0, 1 << 4, 2 << 4, 3 << 4
 BF_OUT_RF, BF_OUT_ENV, BF_OUT_LOGDB, BF_OUT_MASK = 0, 1 << 8, 2 << 8, 3 << 8
 BF_OK, BF_PENDING = 0, 1

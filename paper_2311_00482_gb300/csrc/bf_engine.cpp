@@ -20,6 +20,7 @@
 // allocates nothing once the engine is warm.
 #include <algorithm>
 #include <atomic>
+#include <cstdint>
 #include <chrono>
 #include <condition_variable>
 #include <cstdlib>
@@ -202,6 +203,9 @@ struct Slot {
 // Device job lists, status word and events of one launched batch.
 struct BatchRes {
     DeviceLaunch dl;
+    // results the batch delivers itself (direct routes), in request order: host
+    // destinations that are contiguous leave in one transfer
+    DevMem arena;
     cudaEvent_t start = nullptr, done = nullptr;
     int *err_host = nullptr;  // pinned copy of the status word, written after the last kernel
     bool clean = true;        // false: the launch failed part-way, do not reuse
@@ -272,6 +276,9 @@ struct Request {
     // staging, which the poll copies on); null otherwise
     float *dest = nullptr;
     bool dest_staged = false;
+    // nonzero: the destinations of this request's bf_submit_many_into call lie in
+    // one allocation (BF_DEST_ONE_BUFFER), so neighbours may share a transfer
+    uint64_t dest_group = 0;
     std::shared_ptr<Batch> batch;
     int state = 0;  // 0 queued, 1 launched, 2 failed to launch
     int rc = BF_OK;
@@ -316,7 +323,10 @@ public:
     // dest (optional): where the batch delivers the result (see Request::dest).
     int submit(bf_handle *h, const int16_t *rf, int ns, const double *angles, int na,
                uint32_t flags, uint64_t *ticket, bool wait_copy = true,
-               std::vector<Deferred> *defer = nullptr, float *dest = nullptr);
+               std::vector<Deferred> *defer = nullptr, float *dest = nullptr,
+               uint64_t dest_group = 0);
+    // a fresh id for the destinations of one bf_submit_many_into call
+    uint64_t next_dest_group() { return next_group_.fetch_add(1) + 1; }
     int flush(std::vector<Deferred> &defer);
     int poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes, int64_t timeout_us);
     int poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const *outs, size_t out_bytes,
@@ -381,6 +391,7 @@ private:
     int holding_ = 0;  // submit_many calls in progress
     cudaEvent_t epoch_ = nullptr;
     uint64_t next_ticket_ = 1;
+    std::atomic<uint64_t> next_group_{0};
     int next_batch_ = 0;
     cudaStream_t streams_[kStreams]{};
     cudaStream_t copy_ = nullptr, d2h_ = nullptr;
@@ -403,7 +414,7 @@ std::unique_ptr<Slot> Engine::take_slot()
 
 int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles, int na,
                    uint32_t flags, uint64_t *ticket, bool wait_copy, std::vector<Deferred> *defer,
-                   float *dest)
+                   float *dest, uint64_t dest_group)
 {
     int rc = check_frame_args(h, ns, angles, na, flags);
     if (rc)
@@ -417,6 +428,7 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
     req->out_bytes = out_bytes;
     req->dest = dest;
     req->dest_staged = dest && route_of(dest, true) != CopyRoute::kDirect;
+    req->dest_group = dest ? dest_group : 0;
     {
         std::lock_guard<std::mutex> lk(mu_);
         if (live_ >= max_live_)
@@ -603,9 +615,33 @@ void Engine::launch(std::vector<std::shared_ptr<Request>> &reqs)
         frames.push_back(r->fp);
         cudaStreamWaitEvent(st, r->slot->h2d, 0);
     }
+    int rc = R.init();
+    // results that leave with the batch by DMA: written into the batch's arena
+    // (256-byte aligned, in request order) instead of the slots
+    std::vector<size_t> aoff(reqs.size(), SIZE_MAX);
+    size_t abytes = 0;
+    for (size_t i = 0; i < reqs.size(); ++i) {
+        const Request &q = *reqs[i];
+        if (!q.dest || q.dest_staged)
+            continue;
+        aoff[i] = abytes;
+        abytes += (q.out_bytes + 255) & ~(size_t)255;
+    }
+    if (!rc && abytes)
+        rc = R.arena.ensure(abytes);
+    for (size_t i = 0; i < reqs.size() && !rc; ++i) {
+        if (aoff[i] == SIZE_MAX)
+            continue;
+        FramePrep &f = frames[i];
+        float *to = (float *)((char *)R.arena.p + aoff[i]);
+        if (f.y == f.out)
+            f.y = to;
+        if (f.env == f.out)
+            f.env = to;
+        f.out = to;
+    }
     HostLaunch hl;
     build_launch(frames, hl);
-    int rc = R.init();
     if (!rc)
         rc = upload_maps(frames, st, true);
     for (size_t i = 0; i < reqs.size(); ++i)
@@ -619,15 +655,43 @@ void Engine::launch(std::vector<std::shared_ptr<Request>> &reqs)
     if (!rc)
         rc = enqueue(frames, hl, R.dl, st);
     // results with a destination leave with the batch (a copy engine moves them
-    // while the next batch's kernels run)
+    // while the next batch's kernels run): from the arena, one transfer per run
+    // of destinations contiguous on both sides; staged routes from the slot
+    // into its pinned staging
+    const char *run_src = nullptr;
+    char *run_dst = nullptr;
+    size_t run_bytes = 0;
+    uint64_t run_group = 0;
+    auto flush_run = [&]() {
+        if (run_bytes && !rc &&
+            cudaMemcpyAsync(run_dst, run_src, run_bytes, cudaMemcpyDefault, st) != cudaSuccess)
+            rc = fail(BF_ECUDA, "cudaMemcpyAsync (results to their destinations)");
+        run_bytes = 0;
+    };
     for (size_t i = 0; i < reqs.size() && !rc; ++i) {
         Request &q = *reqs[i];
         if (!q.dest)
             continue;
-        void *to = q.dest_staged ? q.slot->pin_out.p : (void *)q.dest;
-        if (cudaMemcpyAsync(to, q.slot->out.p, q.out_bytes, cudaMemcpyDefault, st) != cudaSuccess)
-            rc = fail(BF_ECUDA, "cudaMemcpyAsync (result to its destination)");
+        if (q.dest_staged) {
+            if (cudaMemcpyAsync(q.slot->pin_out.p, q.slot->out.p, q.out_bytes, cudaMemcpyDefault,
+                                st) != cudaSuccess)
+                rc = fail(BF_ECUDA, "cudaMemcpyAsync (result to its staging)");
+            continue;
+        }
+        const char *src = (const char *)R.arena.p + aoff[i];
+        char *dst = (char *)q.dest;
+        if (run_bytes && q.dest_group && q.dest_group == run_group &&
+            src == run_src + run_bytes && dst == run_dst + run_bytes) {
+            run_bytes += q.out_bytes;
+            continue;
+        }
+        flush_run();
+        run_src = src;
+        run_dst = dst;
+        run_bytes = q.out_bytes;
+        run_group = q.dest_group;
     }
+    flush_run();
     // the status word travels back with the batch: polls read it without a sync
     if (!rc && cudaMemcpyAsync(R.err_host, R.dl.err.p, sizeof(int), cudaMemcpyDeviceToHost, st) !=
                    cudaSuccess)
@@ -990,7 +1054,7 @@ BF_API int bf_poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes, 
 static int submit_many(bf_handle *h, int32_t n, const int16_t *const *rf, int32_t n_samples,
                        const double *angles_rad, int32_t n_angles, uint32_t flags,
                        float *const *outs, size_t out_bytes, uint64_t *tickets_out,
-                       int32_t *n_submitted)
+                       int32_t *n_submitted, bool one_buffer = false)
 {
     if (!h || !rf || !tickets_out || n < 0)
         return fail(BF_EINVAL, "null argument");
@@ -1013,6 +1077,7 @@ static int submit_many(bf_handle *h, int32_t n, const int16_t *const *rf, int32_
         ~Hold() { e->hold(false); }
     };
     int rc = BF_OK, k = 0;
+    const uint64_t group = outs && one_buffer ? eng->next_dest_group() : 0;
     {
         Hold hold(eng);  // released once every frame is admitted (copies may still run)
         std::vector<Engine::Deferred> defer;  // device and pinned sources: DMA per frame
@@ -1022,7 +1087,7 @@ static int submit_many(bf_handle *h, int32_t n, const int16_t *const *rf, int32_
                 break;
             }
             rc = eng->submit(h, rf[k], n_samples, angles_rad, n_angles, flags, tickets_out + k,
-                             false, &defer, outs ? outs[k] : nullptr);
+                             false, &defer, outs ? outs[k] : nullptr, group);
             if (rc)
                 break;
         }
@@ -1051,8 +1116,10 @@ BF_API int bf_submit_many_into(bf_handle *h, int32_t n, const int16_t *const *rf
 {
     if (!outs)
         return fail(BF_EINVAL, "null destinations");
-    return submit_many(h, n, rf, n_samples, angles_rad, n_angles, mode_and_flags, outs, out_bytes,
-                       tickets_out, n_submitted);
+    const bool one_buffer = (mode_and_flags & BF_DEST_ONE_BUFFER) != 0;
+    return submit_many(h, n, rf, n_samples, angles_rad, n_angles,
+                       mode_and_flags & ~(uint32_t)BF_DEST_ONE_BUFFER, outs, out_bytes, tickets_out,
+                       n_submitted, one_buffer);
 }
 
 BF_API int bf_poll_many(bf_handle *h, int32_t n, const uint64_t *tickets, float *const *outs,
