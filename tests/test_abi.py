@@ -34,6 +34,26 @@ def test_header_declares_the_entry_points():
     assert set(names) == set(bf.EXPORTED)
 
 
+def header_constants():
+    """BF_* enumerators of include/bf.h with their values (plain integers and
+    n << k forms)."""
+    text = open(HEADER).read()
+    consts = {}
+    for body in re.findall(r"enum\s*\{([^}]*)\}", text):
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        for name, expr in re.findall(r"\b(BF_\w+)\s*=\s*([-\w\s<|]+?)\s*(?:,|$)", body):
+            consts[name] = int(eval(expr, {}, dict(consts)))
+    return consts
+
+
+def test_binding_constants_match_the_header():
+    consts = header_constants()
+    assert {"BF_DAS", "BF_OUT_LOGDB", "BF_IQDAS", "BF_FK_STOLT", "BF_DEST_ONE_BUFFER",
+            "BF_EINVAL"} <= set(consts)
+    for name, value in consts.items():
+        assert getattr(bf, name) == value, name
+
+
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_symbols():
         assert hasattr(lib, name), name
