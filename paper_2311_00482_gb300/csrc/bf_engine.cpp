@@ -265,10 +265,25 @@ struct Batch {
 
 }  // namespace
 
+// One event for the RF copies bf_submit_many queued on one transfer stream:
+// every request among them waits on it (one record and one wait per stream
+// instead of one per frame).  Destroyed with the last request that holds it.
+struct CopyEvent {
+    cudaEvent_t e = nullptr;
+    ~CopyEvent()
+    {
+        if (e)
+            cudaEventDestroy(e);
+    }
+};
+
 struct Request {
     uint64_t ticket = 0;
     bf_handle *h = nullptr;
     std::unique_ptr<Slot> slot;
+    // the RF copy's completion: the shared event of bf_submit_many's copies on
+    // the request's stream, or (null) the slot's own event
+    std::shared_ptr<CopyEvent> copied;
     FramePrep fp;
     size_t out_bytes = 0;
     // destination given at submission (bf_submit_many_into): the batch itself
@@ -324,7 +339,7 @@ public:
     int submit(bf_handle *h, const int16_t *rf, int ns, const double *angles, int na,
                uint32_t flags, uint64_t *ticket, bool wait_copy = true,
                std::vector<Deferred> *defer = nullptr, float *dest = nullptr,
-               uint64_t dest_group = 0);
+               uint64_t dest_group = 0, const CopyRoute *dest_route = nullptr);
     // a fresh id for the destinations of one bf_submit_many_into call
     uint64_t next_dest_group() { return next_group_.fetch_add(1) + 1; }
     int flush(std::vector<Deferred> &defer);
@@ -377,6 +392,7 @@ private:
     void loop();
     void launch(std::vector<std::shared_ptr<Request>> &reqs);
     std::unique_ptr<Slot> take_slot();
+    void put_free(std::unique_ptr<Slot> s);  // under mu_
 
     int device_;
     std::mutex mu_;
@@ -384,6 +400,7 @@ private:
     std::deque<std::shared_ptr<Request>> pending_;
     std::deque<std::shared_ptr<Batch>> inflight_;
     std::vector<std::unique_ptr<Slot>> free_;
+    std::vector<size_t> free_bytes_;  // device bytes of free_[i]
     size_t used_ = 0, budget_ = 0;
     int live_ = 0;
     int max_batch_ = 64, max_inflight_ = 3, max_live_ = 512;
@@ -404,17 +421,27 @@ std::unique_ptr<Slot> Engine::take_slot()
 {
     if (free_.empty())
         return std::make_unique<Slot>();
-    auto it = std::max_element(free_.begin(), free_.end(), [](const auto &a, const auto &b) {
-        return a->device_bytes() < b->device_bytes();
-    });
-    std::unique_ptr<Slot> s = std::move(*it);
-    free_.erase(it);
+    // the largest free slot (the least growth); sizes kept beside the list so
+    // that the choice reads one contiguous array
+    const size_t i = (size_t)(std::max_element(free_bytes_.begin(), free_bytes_.end()) -
+                              free_bytes_.begin());
+    std::unique_ptr<Slot> s = std::move(free_[i]);
+    free_[i] = std::move(free_.back());
+    free_.pop_back();
+    free_bytes_[i] = free_bytes_.back();
+    free_bytes_.pop_back();
     return s;
+}
+
+void Engine::put_free(std::unique_ptr<Slot> s)
+{
+    free_bytes_.push_back(s->device_bytes());
+    free_.push_back(std::move(s));
 }
 
 int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles, int na,
                    uint32_t flags, uint64_t *ticket, bool wait_copy, std::vector<Deferred> *defer,
-                   float *dest, uint64_t dest_group)
+                   float *dest, uint64_t dest_group, const CopyRoute *dest_route)
 {
     int rc = check_frame_args(h, ns, angles, na, flags);
     if (rc)
@@ -427,7 +454,9 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
     req->h = h;
     req->out_bytes = out_bytes;
     req->dest = dest;
-    req->dest_staged = dest && route_of(dest, true) != CopyRoute::kDirect;
+    // (dest_route: the route of the call's one destination buffer, found once)
+    req->dest_staged =
+        dest && (dest_route ? *dest_route : route_of(dest, true)) != CopyRoute::kDirect;
     req->dest_group = dest ? dest_group : 0;
     {
         std::lock_guard<std::mutex> lk(mu_);
@@ -452,7 +481,7 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
         std::lock_guard<std::mutex> lk(mu_);
         used_ -= before;
         used_ += s.device_bytes();
-        free_.push_back(std::move(req->slot));
+        put_free(std::move(req->slot));
         live_ -= 1;
         return code;
     };
@@ -462,7 +491,7 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
         std::lock_guard<std::mutex> lk(mu_);
         const size_t grow = need > before ? need - before : 0;
         if (grow && used_ + grow > budget_) {
-            free_.push_back(std::move(req->slot));
+            put_free(std::move(req->slot));
             live_ -= 1;
             return fail(BF_EAGAIN, "device memory budget reached (%zu of %zu bytes in use)", used_,
                         budget_);
@@ -471,7 +500,7 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
             size_t fr = 0, tot = 0;
             cudaSetDevice(device_);
             if (cudaMemGetInfo(&fr, &tot) != cudaSuccess || fr < grow + ((size_t)256 << 20)) {
-                free_.push_back(std::move(req->slot));
+                put_free(std::move(req->slot));
                 live_ -= 1;
                 return fail(BF_EAGAIN, "not enough free device memory for a request (%zu needed)",
                             grow);
@@ -496,7 +525,7 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
         used_ -= grow;
         used_ -= before;
         used_ += s.device_bytes();
-        free_.push_back(std::move(req->slot));
+        put_free(std::move(req->slot));
         live_ -= 1;
         return rc;
     }
@@ -545,7 +574,7 @@ int Engine::submit(bf_handle *h, const int16_t *rf, int ns, const double *angles
         used_ -= before;
         used_ += s.device_bytes();
         if (e != cudaSuccess) {
-            free_.push_back(std::move(req->slot));
+            put_free(std::move(req->slot));
             live_ -= 1;
             return inject ? fail(BF_ECUDA, "injected RF copy failure (BF_FAULT=copy)")
                           : cuda_fail(e, "copying the request's RF");
@@ -568,15 +597,21 @@ int Engine::flush(std::vector<Deferred> &defer)
         return BF_OK;
     cudaSetDevice(device_);
     cudaError_t e = cudaSuccess;
-    // one DMA per frame, spread over the transfer streams; each slot's copy
-    // event follows its own copy
+    // one DMA per frame, spread over the transfer streams; one event per stream
+    // after its copies, shared by the requests copied there
+    const int nst = (int)std::min<size_t>(defer.size(), kXferStreams);
+    std::shared_ptr<CopyEvent> ev[kXferStreams];
+    for (int j = 0; j < nst && e == cudaSuccess; ++j) {
+        ev[j] = std::make_shared<CopyEvent>();
+        e = cudaEventCreateWithFlags(&ev[j]->e, cudaEventDisableTiming);
+    }
     for (size_t i = 0; i < defer.size() && e == cudaSuccess; ++i) {
         Deferred &d = defer[i];
-        cudaStream_t st = xin_[i % kXferStreams];
-        e = cudaMemcpyAsync(d.req->slot->rf.p, d.src, d.bytes, cudaMemcpyDefault, st);
-        if (e == cudaSuccess)
-            e = cudaEventRecord(d.req->slot->h2d, st);
+        e = cudaMemcpyAsync(d.req->slot->rf.p, d.src, d.bytes, cudaMemcpyDefault, xin_[i % nst]);
+        d.req->copied = ev[i % nst];
     }
+    for (int j = 0; j < nst && e == cudaSuccess; ++j)
+        e = cudaEventRecord(ev[j]->e, xin_[j]);
     std::string msg;
     int rc = BF_OK;
     if (e != cudaSuccess) {
@@ -611,9 +646,14 @@ void Engine::launch(std::vector<std::shared_ptr<Request>> &reqs)
     cudaStream_t st = streams_[b->id % kStreams];
     std::vector<FramePrep> frames;
     frames.reserve(reqs.size());
+    std::vector<cudaEvent_t> waited;  // each copy event once (many requests share one)
     for (auto &r : reqs) {
         frames.push_back(r->fp);
-        cudaStreamWaitEvent(st, r->slot->h2d, 0);
+        const cudaEvent_t ev = r->copied ? r->copied->e : r->slot->h2d;
+        if (std::find(waited.begin(), waited.end(), ev) == waited.end()) {
+            cudaStreamWaitEvent(st, ev, 0);
+            waited.push_back(ev);
+        }
     }
     int rc = R.init();
     // results that leave with the batch by DMA: written into the batch's arena
@@ -830,7 +870,7 @@ int Engine::poll(bf_handle *h, uint64_t ticket, float *out, size_t out_bytes, in
     }
     {
         std::lock_guard<std::mutex> lk(mu_);
-        free_.push_back(std::move(req->slot));
+        put_free(std::move(req->slot));
         live_ -= 1;
     }
     return rc;
@@ -955,7 +995,7 @@ int Engine::poll_many(bf_handle *h, int n, const uint64_t *tickets, float *const
     {
         std::lock_guard<std::mutex> lk(mu_);
         for (auto &req : reqs) {
-            free_.push_back(std::move(req->slot));
+            put_free(std::move(req->slot));
             live_ -= 1;
         }
     }
@@ -1078,6 +1118,10 @@ static int submit_many(bf_handle *h, int32_t n, const int16_t *const *rf, int32_
     };
     int rc = BF_OK, k = 0;
     const uint64_t group = outs && one_buffer ? eng->next_dest_group() : 0;
+    // one allocation holds every destination: one route for all of them
+    CopyRoute one_route = CopyRoute::kStaged;
+    if (group)
+        one_route = route_of(outs[0], true);
     {
         Hold hold(eng);  // released once every frame is admitted (copies may still run)
         std::vector<Engine::Deferred> defer;  // device and pinned sources: DMA per frame
@@ -1087,7 +1131,8 @@ static int submit_many(bf_handle *h, int32_t n, const int16_t *const *rf, int32_
                 break;
             }
             rc = eng->submit(h, rf[k], n_samples, angles_rad, n_angles, flags, tickets_out + k,
-                             false, &defer, outs ? outs[k] : nullptr, group);
+                             false, &defer, outs ? outs[k] : nullptr, group,
+                             group ? &one_route : nullptr);
             if (rc)
                 break;
         }
