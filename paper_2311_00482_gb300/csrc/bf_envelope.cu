@@ -70,6 +70,40 @@ __device__ __forceinline__ float2 c_sub(float2 a, float2 b)
     return c;
 }
 
+// (a.x^2 + b.x^2, a.y^2 + b.y^2): per half b^2 rounded, then one FMA.
+__device__ __forceinline__ float2 c_sqsum(float2 a, float2 b)
+{
+    unsigned long long ra, rb, rc;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(rc) : "l"(rb));
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(rc) : "l"(ra), "l"(rc));
+    float2 c;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(c.x), "=f"(c.y) : "l"(rc));
+    return c;
+}
+
+// a * s, s a scalar (both halves).
+__device__ __forceinline__ float2 c_scale(float2 a, float s)
+{
+    unsigned long long ra, rs, rc;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %1};" : "=l"(rs) : "f"(s));
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(rc) : "l"(ra), "l"(rs));
+    float2 c;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(c.x), "=f"(c.y) : "l"(rc));
+    return c;
+}
+
+// Square root on the special-function unit (relative error about one unit in
+// the last place, far inside the envelope's tolerance).
+__device__ __forceinline__ float sqrt_fast(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // s * a + b with s a scalar (both halves), as one paired FMA.
 __device__ __forceinline__ float2 c_sfma(float s, float2 a, float2 b)
 {
@@ -284,6 +318,8 @@ __global__ void __launch_bounds__(32 * kEnvWarps, 2)
 
     int cur = -1;
     float lmax = 0.f;
+    int mask_job = -1;     // the job bp_mask belongs to
+    unsigned bp_mask = 0u;  // bit k: spectrum register k of this lane is in the band
     unsigned *cur_max = nullptr;
     const float inv = 1.f / (float)kN;
     for (int g = blockIdx.x * kEnvWarps + warp; g < total_pairs; g += gridDim.x * kEnvWarps) {
@@ -326,16 +362,23 @@ __global__ void __launch_bounds__(32 * kEnvWarps, 2)
             fft_warp<true>(v, buf, twa, lane);
 #pragma unroll
             for (int r = 0; r < kR; ++r) {
-                const float2 y = lds2(hold_at(r));
-                const float hx = v[r].x * inv, hy = v[r].y * inv;
-                v[r] = make_float2(sqrtf(fmaf(y.x, y.x, hx * hx)), sqrtf(fmaf(y.y, y.y, hy * hy)));
+                const float2 q = c_sqsum(lds2(hold_at(r)), c_scale(v[r], inv));  // y^2 + (H y)^2
+                v[r] = make_float2(sqrt_fast(q.x), sqrt_fast(q.y));
             }
         } else {
-            const int lo = J.kb_lo, hi = J.kb_hi;
+            if (jb != mask_job) {  // this lane's bins inside the band, once per image
+                const int lo = J.kb_lo, hi = J.kb_hi;
+                bp_mask = 0u;
+#pragma unroll
+                for (int k = 0; k < kR; ++k) {
+                    const int fa = h ? 256 - k1 - 16 * k : k1 + 16 * k;  // |f|
+                    bp_mask |= (fa >= lo && fa <= hi) ? (1u << k) : 0u;
+                }
+                mask_job = jb;
+            }
 #pragma unroll
             for (int k = 0; k < kR; ++k) {
-                const int fa = h ? 256 - k1 - 16 * k : k1 + 16 * k;  // |f|
-                const float bp = (fa >= lo && fa <= hi) ? 1.f : 0.f;
+                const float bp = ((bp_mask >> k) & 1u) ? 1.f : 0.f;
                 const float sg = (k == 0 && k1 == 0) ? 0.f : sg_lane;
                 v[k] = make_float2(v[k].x * bp, v[k].y * bp);                 // B Z
                 sts2(hold_at(k), make_float2(v[k].y * sg, -v[k].x * sg));  // -i sgn(f) B Z
@@ -350,9 +393,8 @@ __global__ void __launch_bounds__(32 * kEnvWarps, 2)
             fft_warp<true>(v, buf, twa, lane);  // their Hilbert transforms
 #pragma unroll
             for (int r = 0; r < kR; ++r) {
-                const float2 b = lds2(hold_at(r));
-                v[r] = make_float2(sqrtf(fmaf(b.x, b.x, v[r].x * v[r].x)) * inv,
-                                   sqrtf(fmaf(b.y, b.y, v[r].y * v[r].y)) * inv);
+                const float2 q = c_sqsum(lds2(hold_at(r)), v[r]);
+                v[r] = c_scale(make_float2(sqrt_fast(q.x), sqrt_fast(q.y)), inv);
             }
         }
         float *__restrict__ oa = J.env + (size_t)ca * kN;

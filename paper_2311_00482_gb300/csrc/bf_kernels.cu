@@ -2028,7 +2028,7 @@ __global__ void __launch_bounds__(256) fk_depth_kernel(const FkJob J)
 
 // ------------------------------------------------------------------ log --
 
-constexpr int kLogPerBlock = 2048;
+constexpr int kLogPerBlock = 4096;
 
 __global__ void __launch_bounds__(256) log_kernel(const LogJob *__restrict__ jobs,
                                                   const int *__restrict__ blk_prefix, int njobs,
@@ -2047,19 +2047,23 @@ __global__ void __launch_bounds__(256) log_kernel(const LogJob *__restrict__ job
         return (e > 0.f && peak > 0.f) ? fminf(fmaxf(6.0205999132796239f * (__log2f(e) - lp), -dr), 0.f)
                                        : -dr;
     };
-    if (J.vec4) {  // eight pixels per thread as two 16-byte loads issued together
-        const size_t p0 = base + (size_t)threadIdx.x * 4, p1 = p0 + (size_t)blockDim.x * 4;
-        const bool ok0 = p0 < (size_t)J.n, ok1 = p1 < (size_t)J.n;
-        float4 e0 = make_float4(0.f, 0.f, 0.f, 0.f), e1 = e0;
-        if (ok0)
-            e0 = __ldg(reinterpret_cast<const float4 *>(J.env + p0));
-        if (ok1)
-            e1 = __ldg(reinterpret_cast<const float4 *>(J.env + p1));
-        // streaming stores: the dB images do not displace envelopes still to be read
-        if (ok0)
-            __stcs(reinterpret_cast<float4 *>(J.out + p0), make_float4(db(e0.x), db(e0.y), db(e0.z), db(e0.w)));
-        if (ok1)
-            __stcs(reinterpret_cast<float4 *>(J.out + p1), make_float4(db(e1.x), db(e1.y), db(e1.z), db(e1.w)));
+    if (J.vec4) {  // sixteen pixels per thread as four 16-byte loads issued together
+        float4 e[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const size_t pu = base + (size_t)threadIdx.x * 4 + (size_t)u * blockDim.x * 4;
+            ok[u] = pu < (size_t)J.n;
+            e[u] = ok[u] ? __ldcs(reinterpret_cast<const float4 *>(J.env + pu))
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const size_t pu = base + (size_t)threadIdx.x * 4 + (size_t)u * blockDim.x * 4;
+            if (ok[u])
+                __stcs(reinterpret_cast<float4 *>(J.out + pu),
+                       make_float4(db(e[u].x), db(e[u].y), db(e[u].z), db(e[u].w)));
+        }
         return;
     }
     for (int t = threadIdx.x; t < kLogPerBlock; t += blockDim.x) {
