@@ -83,18 +83,6 @@ __device__ __forceinline__ float2 c_sqsum(float2 a, float2 b)
     return c;
 }
 
-// a * s, s a scalar (both halves).
-__device__ __forceinline__ float2 c_scale(float2 a, float s)
-{
-    unsigned long long ra, rs, rc;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
-    asm("mov.b64 %0, {%1, %1};" : "=l"(rs) : "f"(s));
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(rc) : "l"(ra), "l"(rs));
-    float2 c;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(c.x), "=f"(c.y) : "l"(rc));
-    return c;
-}
-
 // Square root on the special-function unit (relative error about one unit in
 // the last place, far inside the envelope's tolerance).
 __device__ __forceinline__ float sqrt_fast(float x)
@@ -354,15 +342,16 @@ __global__ void __launch_bounds__(32 * kEnvWarps, 2)
         }
         fft_warp<false>(v, buf, twa, lane);
         if (!band) {
+            // the inverse transform's 1 / N (a power of two: exact) with the mask
 #pragma unroll
             for (int k = 0; k < kR; ++k) {
-                const float sg = (k == 0 && k1 == 0) ? 0.f : sg_lane;
-                v[k] = make_float2(v[k].y * sg, -v[k].x * sg);  // -i sgn(f) Z
+                const float sg = (k == 0 && k1 == 0) ? 0.f : sg_lane * inv;
+                v[k] = make_float2(v[k].y * sg, -v[k].x * sg);  // -i sgn(f) Z / N
             }
             fft_warp<true>(v, buf, twa, lane);
 #pragma unroll
             for (int r = 0; r < kR; ++r) {
-                const float2 q = c_sqsum(lds2(hold_at(r)), c_scale(v[r], inv));  // y^2 + (H y)^2
+                const float2 q = c_sqsum(lds2(hold_at(r)), v[r]);  // y^2 + (H y)^2
                 v[r] = make_float2(sqrt_fast(q.x), sqrt_fast(q.y));
             }
         } else {
@@ -377,8 +366,8 @@ __global__ void __launch_bounds__(32 * kEnvWarps, 2)
                 mask_job = jb;
             }
 #pragma unroll
-            for (int k = 0; k < kR; ++k) {
-                const float bp = ((bp_mask >> k) & 1u) ? 1.f : 0.f;
+            for (int k = 0; k < kR; ++k) {  // the 1 / N of the inverses with the mask
+                const float bp = ((bp_mask >> k) & 1u) ? inv : 0.f;
                 const float sg = (k == 0 && k1 == 0) ? 0.f : sg_lane;
                 v[k] = make_float2(v[k].x * bp, v[k].y * bp);                 // B Z
                 sts2(hold_at(k), make_float2(v[k].y * sg, -v[k].x * sg));  // -i sgn(f) B Z
@@ -394,7 +383,7 @@ __global__ void __launch_bounds__(32 * kEnvWarps, 2)
 #pragma unroll
             for (int r = 0; r < kR; ++r) {
                 const float2 q = c_sqsum(lds2(hold_at(r)), v[r]);
-                v[r] = c_scale(make_float2(sqrt_fast(q.x), sqrt_fast(q.y)), inv);
+                v[r] = make_float2(sqrt_fast(q.x), sqrt_fast(q.y));
             }
         }
         float *__restrict__ oa = J.env + (size_t)ca * kN;
