@@ -386,10 +386,9 @@ def test_submit_many_and_poll_many(torch):
 
 
 def test_submit_many_and_poll_many_batched_copies(torch):
-    """Seventy frames from pinned host records into pinned host images: the
-    records and images move in batched copy kernels of at most 64 frames, an
-    image whose destination is not 16-byte aligned by plain copy; every result
-    equals its frame beamformed alone."""
+    """Seventy frames from pinned host records into pinned host images (more
+    frames than one batch takes), one image into a destination that is not
+    16-byte aligned; every result equals its frame beamformed alone."""
     acq = synth.SPECKLE_POINTS_128.with_(nx=40, nz=64)
     flags = bf.BF_DAS | bf.BF_DMAS
     rfs = [synth.speckle_points_frame(acq, seed=synth.BASE_SEED + 330 + k)[0] for k in range(4)]
