@@ -6,6 +6,8 @@ Envelopes use the same bounds; log-compressed images are compared in dB with
 a max-abs bound of 0.05 dB, which is what a 2e-6-of-peak envelope error
 becomes at the -70 dB floor (8.7 dB per unit relative error at 3.2e-4 of peak).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -549,3 +551,34 @@ def test_submit_many_into_delivers_to_every_destination_kind(torch):
         assert ei.value.code == bf.BF_EINVAL
     finally:
         bf.bf_destroy(h)
+
+
+@pytest.mark.parametrize("stage", [bf.BF_OUT_RF, bf.BF_OUT_ENV, bf.BF_OUT_LOGDB])
+def test_one_buffer_delivery_for_every_output_stage(torch, stage):
+    """bf_submit_many_into with BF_DEST_ONE_BUFFER: the batch's kernels write the
+    images (beamformed, envelope or dB) into its result arena and the views of
+    one pinned buffer receive them in one transfer; each equals the frame
+    beamformed alone, on 16-row tiles (four-frame jobs) as on the default tiles."""
+    acq = synth.SPECKLE_POINTS_128.with_(nx=48, nz=96)
+    flags = bf.BF_DAS | bf.BF_DMAS | stage
+    rfs = [synth.speckle_points_frame(acq, seed=synth.BASE_SEED + 380 + k)[0] for k in range(5)]
+    for rows in ("2", None):
+        if rows:
+            os.environ["BF_TILE_ROWS"] = rows
+        h = make_handle(acq)
+        try:
+            solo = [run_gpu(torch, acq, rf, flags, h=h) for rf in rfs]
+            srcs = [torch.from_numpy(r).pin_memory() for r in rfs]
+            buf = torch.full((5, 2, acq.nx, acq.nz), float("nan")).pin_memory()
+            tickets = bf.bf_submit_many_into(h, srcs, acq.n_samples, acq.angles_rad,
+                                             flags | bf.BF_DEST_ONE_BUFFER, list(buf))
+            assert bf.bf_poll_many(h, tickets, None, timeout_us=30_000_000) == bf.BF_OK
+            for k in range(5):
+                # four-frame jobs round the DMAS sums differently from single frames
+                # (a few 1e-6 relative: 4e-4 dB near the -70 dB floor); a frame in
+                # the wrong place would be off by whole decibels
+                atol = 0.01 if stage == bf.BF_OUT_LOGDB else 2e-6 * np.max(np.abs(solo[k]))
+                np.testing.assert_allclose(buf[k].numpy(), solo[k], rtol=0, atol=atol + 1e-30)
+        finally:
+            bf.bf_destroy(h)
+            os.environ.pop("BF_TILE_ROWS", None)
