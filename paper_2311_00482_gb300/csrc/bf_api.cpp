@@ -209,8 +209,8 @@ static int env_tables(int nz, std::shared_ptr<EnvTablesDev> &out)
 // Tile configuration of a workload: what bf_autotune measured fastest for it,
 // else entry 0 (4 rows per thread, 32-row tiles, three CTAs per SM, measured
 // faster than 8 rows on every grid tried); BF_TILE_ROWS=8 forces entry 3,
-// BF_TILE_ROWS=2 entry 4 (DAS / DMAS of RF records, IQ-DAS / BB-DMAS; others
-// keep entry 0).
+// BF_TILE_ROWS=2 entry 6 (16-row tiles of up to 22 channels per stage; DAS /
+// DMAS of RF records, IQ-DAS / BB-DMAS; others keep entry 0).
 static int choose_cfg(const bf_handle *h, const PlanKey &key)
 {
     if (const char *e = std::getenv("BF_TILE_ROWS")) {
@@ -219,7 +219,7 @@ static int choose_cfg(const bf_handle *h, const PlanKey &key)
         if (std::atoi(e) == 4)
             return 0;
         if (std::atoi(e) == 2)
-            return 4;
+            return 6;
     }
     auto it = h->tuned.find(key);
     return it == h->tuned.end() ? 0 : it->second;

@@ -18,7 +18,7 @@ constexpr int kPadL = 2;
 constexpr int kTileCols = 32;
 constexpr int kWarps = 8;
 constexpr int kThreads = 32 * kWarps;
-constexpr int kMaxGroup = 16;         // channels staged per pipeline stage (upper bound)
+constexpr int kMaxGroup = 24;         // channels staged per pipeline stage (upper bound)
 constexpr int kMaxStages = 3;         // pipeline stages in shared memory (at most)
 constexpr int kMaxBox = 256;          // TMA box extent limit per dimension
 constexpr int kMaxSmemPerCta = 227 << 10;  // dynamic shared memory one CTA may use
@@ -37,11 +37,12 @@ struct TileConfig {
     int rows, stage_bytes;
 };
 constexpr TileConfig kTileConfigs[] = {{4, 24 << 10}, {4, 16 << 10}, {4, 32 << 10}, {8, 24 << 10},
-                                       {2, 14 << 10}, {2, 12 << 10}};
-// Pipeline stages of a beamforming CTA: two deep stages (up to 16 channels of
-// four frames) for two-row tiles, three otherwise (measured fastest for each).
+                                       {2, 14 << 10}, {2, 12 << 10}, {2, 17 << 10}};
+// Pipeline stages of a beamforming CTA: two deep stages (up to 22 channels of
+// four frames, the most that keep two CTAs per SM) for two-row tiles, three
+// otherwise (measured fastest for each).
 __host__ __device__ constexpr int stages_for_rows(int rows) { return rows == 2 ? 2 : 3; }
-constexpr int kNumTileConfigs = 6;
+constexpr int kNumTileConfigs = 7;
 // Frames of one plan that one beamforming job may carry (sharing every delay).
 constexpr int kMaxFramesPerJob = 4;
 

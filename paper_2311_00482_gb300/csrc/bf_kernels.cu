@@ -457,7 +457,7 @@ struct SmemHeader {
     // storer -> consumers (the staging area is free again)
     uint64_t epi_full, epi_empty;
 };
-constexpr int kHeaderBytes = 4096;
+constexpr int kHeaderBytes = 4608;
 static_assert(sizeof(SmemHeader) <= kHeaderBytes, "header");
 
 // Sample pairs read from shared memory through 32-bit shared-window addresses.

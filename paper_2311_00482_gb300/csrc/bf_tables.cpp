@@ -195,7 +195,10 @@ void angle_tables(const GeomHost &g, const GeometryHost &geo, int ns,
     out.rows = rows_per_thread;
     out.align = align;
     int grp = stage_bytes / (out.wmax * pair_bytes(prec) + kTileCols * 12);
-    out.group = std::max(1, std::min(kMaxGroup, std::min(grp, g.ne)));
+    // at most 16 channels per stage on 32- and 64-row tiles (three stages: more
+    // leaves one CTA per SM), up to kMaxGroup on 16-row tiles (two stages)
+    const int cap = rows_per_thread == 2 ? kMaxGroup : 16;
+    out.group = std::max(1, std::min(cap, std::min(grp, g.ne)));
 }
 
 void bandpass_bins(int nz, double z0, double z1, double c, double f0, int &lo, int &hi)
