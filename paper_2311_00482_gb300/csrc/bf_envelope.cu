@@ -18,7 +18,11 @@
 //     IDFT(-i sgn(k) Z) = H{y_a} + i H{y_b}; env = |y + i H{y}|;
 //   band-pass: IDFT(B Z) and IDFT(-i sgn(k) B Z) give the band-passed columns
 //     and their Hilbert transforms; env = |y_B + i H{y_B}|.
-// Each image's maximum goes to its maxbits word (float bits, env >= 0).
+// The inverse's 1/N (a power of two, exact) rides on the mask.  Complex
+// additions, the lane-pair radix-2 step and the magnitudes' squares run as
+// paired FP32 instructions; the magnitudes' square roots on the
+// special-function unit.  Each image's maximum goes to its maxbits word
+// (float bits, env >= 0).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
