@@ -420,16 +420,37 @@ __global__ void __launch_bounds__(256) demod_kernel(const DemodJob *__restrict__
     for (int k = threadIdx.x; k < m; k += blockDim.x)
         tw[k] = __ldg(J.tw + k);
     const float inv = 1.f / (float)m;
-    const float2 *A = analytic_scaled(J.rf + (size_t)row * m, m, lgm, X, Y, tw);
     if (J.nf == 1) {
+        const float2 *A = analytic_scaled(J.rf + (size_t)row * m, m, lgm, X, Y, tw);
         float4 *__restrict__ out = J.pairs + (size_t)row * J.nsp;
         for (int j = threadIdx.x; j < J.nsp; j += blockDim.x)
             out[j] = demod_pair(A, j, m, J.rot, inv);
         return;
     }
-    // frame pair: the second frame's analytic signal in the two free buffers,
-    // then per pair index the pair's eight floats in two 16-byte stores
-    const float2 *B = analytic_scaled(J.rf2 + (size_t)row * m, m, lgm, A == X ? Y : X, Z, tw);
+    // frame pair: both records in one transform, z = u_a + i u_b.  Their
+    // spectra follow from Z's Hermitian parts, U_a[k] = (Z[k] + conj Z[-k]) / 2
+    // and U_b[k] = (Z[k] - conj Z[-k]) / 2i; each gets the one-sided mask and
+    // its own inverse transform (three transforms for two records).
+    {
+        const int16_t *__restrict__ ua = J.rf + (size_t)row * m;
+        const int16_t *__restrict__ ub = J.rf2 + (size_t)row * m;
+        for (int k = threadIdx.x; k < m; k += blockDim.x)
+            X[k] = make_float2((float)__ldg(ua + k), (float)__ldg(ub + k));
+    }
+    __syncthreads();
+    float2 *S = fft_r8(X, Y, m, lgm, 1, tw, false);
+    float2 *P = S == X ? Y : X;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        const float h = (k == 0 || 2 * k == m) ? 1.f : (2 * k < m ? 2.f : 0.f);
+        const float2 zk = S[k], zm = S[(m - k) & (m - 1)];
+        const float hh = 0.5f * h;
+        P[k] = make_float2((zk.x + zm.x) * hh, (zk.y - zm.y) * hh);
+        Z[k] = make_float2((zk.y + zm.y) * hh, (zm.x - zk.x) * hh);
+    }
+    __syncthreads();
+    const float2 *A = fft_r8(P, S, m, lgm, 1, tw, true);  // m * analytic signal of u_a
+    const float2 *B = fft_r8(Z, A == P ? S : P, m, lgm, 1, tw, true);  // and of u_b
+    // per pair index the pair's eight floats in two 16-byte stores
     float4 *__restrict__ out = J.pairs + (size_t)row * J.nsp * J.nf + J.fi / 2 * 2;
     for (int j = threadIdx.x; j < J.nsp; j += blockDim.x) {
         const float4 a = demod_pair(A, j, m, J.rot, inv), b = demod_pair(B, j, m, J.rot, inv);

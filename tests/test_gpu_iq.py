@@ -134,6 +134,19 @@ def assert_db_close(got, mag, what):
                                                                      float(err.max()))
 
 
+def assert_matches_single(got, single, is_db, what):
+    """A frame of a multi-frame job against the same frame beamformed alone.
+    The beamforming arithmetic per frame is the single-frame kernel's, but a
+    frame pair is demodulated in one complex transform (two real records),
+    which rounds differently from one transform per record: magnitudes within
+    2e-6 of the image's peak, dB images within 0.01 dB (a frame in the wrong
+    place would be off by whole decibels)."""
+    for m in range(got.shape[0]):
+        atol = 0.01 if is_db else 2e-6 * float(np.max(np.abs(single[m])))
+        np.testing.assert_allclose(got[m], single[m], rtol=0, atol=atol + 1e-30,
+                                   err_msg="%s image %d" % (what, m))
+
+
 def scaled_frames(acq, n, seed0):
     """n distinct records, frame k at (k + 2) / (n + 1) of its synthesized amplitude,
     so that the frames' image maxima (and dB images) differ."""
@@ -151,9 +164,9 @@ def scaled_frames(acq, n, seed0):
 @pytest.mark.parametrize("rows,n,nz", [("2", 7, 92), ("2", 7, 90), ("2", 7, 91), ("4", 5, 92)])
 def test_iq_frames_share_delay_and_carrier_phase(torch, monkeypatch, rows, n, nz):
     """Multi-frame IQ jobs (Sec. II-B-1, Eq. (4)): every frame's IQ-DAS and
-    BB-DMAS images match the oracle, equal the frame's single-frame result on
-    the same tiles bit for bit (each frame's arithmetic is the single-frame
-    kernel's), and the log stage normalises each frame by its own maximum."""
+    BB-DMAS images match the oracle and the frame's single-frame result on
+    the same tiles, and the log stage normalises each frame by its own
+    maximum."""
     monkeypatch.setenv("BF_TILE_ROWS", rows)
     acq = synth.SPECKLE_POINTS_128.with_(nx=70, nz=nz, angles_deg=(-4.0, 4.0))
     rfs = scaled_frames(acq, n, synth.BASE_SEED + 900)
@@ -175,7 +188,8 @@ def test_iq_frames_share_delay_and_carrier_phase(torch, monkeypatch, rows, n, nz
             for k in range(n):
                 ref = iq_ref(acq, rfs[k])
                 single = run_gpu(torch, acq, rfs[k], flags | stage, h=h)
-                np.testing.assert_array_equal(got[k], single, "frame %d stage %d" % (k, stage))
+                assert_matches_single(got[k], single, stage == bf.BF_OUT_LOGDB,
+                                      "frame %d stage %d" % (k, stage))
                 for m, name in enumerate(("iqdas", "bbdmas")):
                     if stage == bf.BF_OUT_RF:
                         assert_close(got[k][m], ref[name], bf.BF_PREC_FP32, "%s %d" % (name, k))
@@ -231,7 +245,8 @@ def test_iq_job_with_mixed_output_stages(torch, monkeypatch):
             batch.close()
         for k in range(4):
             got = outs[k].cpu().numpy().astype(np.float64)
-            np.testing.assert_array_equal(got, run_gpu(torch, acq, rfs[k], base | stages[k], h=h))
+            assert_matches_single(got, run_gpu(torch, acq, rfs[k], base | stages[k], h=h),
+                                  stages[k] == bf.BF_OUT_LOGDB, "frame %d" % k)
             ref = iq_ref(acq, rfs[k])
             for m, name in enumerate(("iqdas", "bbdmas")):
                 if stages[k] == bf.BF_OUT_LOGDB:
