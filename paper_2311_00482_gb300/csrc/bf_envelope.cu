@@ -314,7 +314,10 @@ __global__ void __launch_bounds__(32 * kEnvWarps, 2)
     unsigned bp_mask = 0u;  // bit k: spectrum register k of this lane is in the band
     unsigned *cur_max = nullptr;
     const float inv = 1.f / (float)kN;
-    for (int g = blockIdx.x * kEnvWarps + warp; g < total_pairs; g += gridDim.x * kEnvWarps) {
+    // Column pairs in reverse launch order: the beamformer writes the last
+    // images of a batch last, so those are still in L2 when this kernel starts.
+    for (int g0 = blockIdx.x * kEnvWarps + warp; g0 < total_pairs; g0 += gridDim.x * kEnvWarps) {
+        const int g = total_pairs - 1 - g0;
         const int jb = find_pair_job(pair_prefix, njobs, g);
         const EnvJob &J = jobs[jb];
         if (jb != cur) {  // flush the previous image's maximum
@@ -336,7 +339,9 @@ __global__ void __launch_bounds__(32 * kEnvWarps, 2)
 #pragma unroll
         for (int r = 0; r < kR; ++r) {
             const int n = 32 * r + lane;
-            v[r] = make_float2(__ldg(ya + n), has_b ? __ldg(yb + n) : 0.f);
+            // read once: streaming loads, evicted first, so the envelopes this
+            // kernel writes stay in L2 for the log stage
+            v[r] = make_float2(__ldcs(ya + n), has_b ? __ldcs(yb + n) : 0.f);
         }
         const bool band = J.band != 0;
         if (!band) {

@@ -1721,7 +1721,11 @@ __global__ void __launch_bounds__(256) envelope_kernel(const EnvJob *__restrict_
 {
     extern __shared__ __align__(16) float2 sbuf[];
     __shared__ float red[32];
-    const int jb = find_job(blk_prefix, njobs, blockIdx.x);
+    // blocks in reverse: the beamformer writes a batch's last images last, so
+    // those are still in L2 when this kernel starts (and the log stage, in
+    // launch order, then reads the envelopes written last first)
+    const int blk = gridDim.x - 1 - blockIdx.x;
+    const int jb = find_job(blk_prefix, njobs, blk);
     const EnvJob J = jobs[jb];
     const int nz = J.nz, m = J.fft_m;
     const int lgm = 31 - __clz(m);
@@ -1729,7 +1733,7 @@ __global__ void __launch_bounds__(256) envelope_kernel(const EnvJob *__restrict_
 
     if (!J.bluestein) {
         const int C = J.cols_per_block >> 1;  // complex columns (pairs of image columns)
-        const int c0 = (blockIdx.x - __ldg(blk_prefix + jb)) * J.cols_per_block;
+        const int c0 = (blk - __ldg(blk_prefix + jb)) * J.cols_per_block;
         float2 *Zb = sbuf, *Pb = sbuf + (size_t)C * m, *Qb = sbuf + (size_t)2 * C * m;
         float2 *tw = sbuf + (size_t)3 * C * m;
         float2 *ptw = tw + m;  // per-pass twiddles of the radix-8 passes
@@ -1859,7 +1863,7 @@ __global__ void __launch_bounds__(256) envelope_kernel(const EnvJob *__restrict_
         }
     } else {
         // one column per block through Bluestein's chirp transforms
-        const int c0 = blockIdx.x - __ldg(blk_prefix + jb);
+        const int c0 = blk - __ldg(blk_prefix + jb);
         float2 *A = sbuf, *B = sbuf + m, *tw = sbuf + (size_t)3 * m;
         for (int k = threadIdx.x; k < m; k += blockDim.x)
             tw[k] = __ldg(J.tw + k);
@@ -2055,8 +2059,9 @@ __global__ void __launch_bounds__(256) log_kernel(const LogJob *__restrict__ job
                                                   const int *__restrict__ blk_prefix, int njobs,
                                                   float dr)
 {
-    // blocks in reverse: the envelopes written last (still in L2) are read first
-    const int blk = gridDim.x - 1 - blockIdx.x;
+    // blocks in launch order: the warp envelope kernel walks a batch's images
+    // in reverse, so the envelopes it wrote last (still in L2) are read first
+    const int blk = blockIdx.x;
     const int jb = find_job(blk_prefix, njobs, blk);
     const LogJob J = jobs[jb];
     const size_t base = (size_t)(blk - __ldg(blk_prefix + jb)) * kLogPerBlock;
