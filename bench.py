@@ -77,8 +77,8 @@ def dist_info():
 # of the 512 x 512 workload at the benchmark's own 64 frames per launch
 # (other frame counts are scaled by the frames).  Valid only for the kernel
 # source the capture was taken on: any other source reports null.
-TRAFFIC_CAPTURE = {"sources_sha256": "d244328c86f8dc69506bf6c0575094ccd6dbe125fc1b56d6e078988e89a38573",
-                   "frames": 64, "bytes": 32057344 + 79566336}
+TRAFFIC_CAPTURE = {"sources_sha256": "3469e468dddf85f511065af756bb54029671f197ae3644ce8d0b985a80c0b7f6",
+                   "frames": 64, "bytes": 32055808 + 79521280}
 
 
 def beamform_traffic(frames):

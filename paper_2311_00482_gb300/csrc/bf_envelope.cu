@@ -286,6 +286,9 @@ __global__ void __launch_bounds__(32 * kEnvWarps, 2)
                          int njobs, int total_pairs)
 {
     extern __shared__ __align__(16) float2 esm[];
+    // the log stage's blocks may be scheduled as this grid's CTAs finish (they
+    // wait for the whole grid before reading its results)
+    asm volatile("griddepcontrol.launch_dependents;");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     {
         // [16][kPitch]: W_N^(k1 n2) from the job's table exp(-2 pi i k / N), k < N

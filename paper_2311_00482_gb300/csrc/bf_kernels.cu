@@ -1725,6 +1725,9 @@ __global__ void __launch_bounds__(256) envelope_kernel(const EnvJob *__restrict_
     // those are still in L2 when this kernel starts (and the log stage, in
     // launch order, then reads the envelopes written last first)
     const int blk = gridDim.x - 1 - blockIdx.x;
+    // the log stage's blocks may be scheduled as this grid's CTAs finish (they
+    // wait for the whole grid before reading its results)
+    asm volatile("griddepcontrol.launch_dependents;");
     const int jb = find_job(blk_prefix, njobs, blk);
     const EnvJob J = jobs[jb];
     const int nz = J.nz, m = J.fft_m;
@@ -2059,13 +2062,17 @@ __global__ void __launch_bounds__(256) log_kernel(const LogJob *__restrict__ job
                                                   const int *__restrict__ blk_prefix, int njobs,
                                                   float dr)
 {
-    // blocks in launch order: the warp envelope kernel walks a batch's images
-    // in reverse, so the envelopes it wrote last (still in L2) are read first
+    // blocks in launch order: the envelope kernels walk a batch's images in
+    // reverse, so the envelopes written last (still in L2) are read first
     const int blk = blockIdx.x;
     const int jb = find_job(blk_prefix, njobs, blk);
     const LogJob J = jobs[jb];
     const size_t base = (size_t)(blk - __ldg(blk_prefix + jb)) * kLogPerBlock;
-    const float peak = __uint_as_float(__ldg(J.maxbits));
+    // Launched as a programmatic dependent of the envelope kernel: this block
+    // may start while that grid's last CTAs still run, and waits here until
+    // the grid has completed and its envelopes and maxima are visible.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const float peak = __uint_as_float(__ldcg(J.maxbits));
     // 20 log10(e / peak) = (20 log10 2) (log2 e - log2 peak), the logarithm on the
     // special-function unit (absolute error ~1e-6 of a unit of log2: ~1e-5 dB)
     const float lp = peak > 0.f ? __log2f(peak) : 0.f;
@@ -2318,8 +2325,20 @@ cudaError_t launch_log(const LogJob *jobs_dev, const int *blk_prefix_dev, int nj
 {
     if (njobs <= 0 || total_blocks <= 0)
         return cudaSuccess;
-    log_kernel<<<total_blocks, 256, 0, stream>>>(jobs_dev, blk_prefix_dev, njobs, dynamic_range_db);
-    return cudaGetLastError();
+    // programmatic stream serialization: the blocks may be scheduled before the
+    // envelope kernel ends (the kernel's griddepcontrol.wait orders the reads),
+    // which hides this launch behind that kernel's last CTAs
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)total_blocks);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, log_kernel, jobs_dev, blk_prefix_dev, njobs, dynamic_range_db);
 }
 
 int log_blocks(long long pixels) { return (int)((pixels + kLogPerBlock - 1) / kLogPerBlock); }
