@@ -861,11 +861,14 @@ int upload_maps(std::vector<FramePrep> &frames, cudaStream_t st, bool async)
 // frame maxima, beamforming (one launch per precision / combiner variant),
 // envelope, log compression.
 int enqueue(const std::vector<FramePrep> &frames, const HostLaunch &hl, DeviceLaunch &dl,
-            cudaStream_t st, cudaEvent_t *marks)
+            cudaStream_t st, cudaEvent_t *marks, const MarkBranch *branch)
 {
     cudaError_t e;
     // Inside a stream capture the marks must be external event records (they
     // become graph nodes that record at replay time); outside, plain records.
+    // An event record between two kernels of a graph costs about 2 us and
+    // keeps the next kernel from being launched ahead, so in a capture with a
+    // branch the marks hang off a side stream instead.
     unsigned mark_flags = cudaEventRecordDefault;
     if (marks) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -874,10 +877,24 @@ int enqueue(const std::vector<FramePrep> &frames, const HostLaunch &hl, DeviceLa
             return cuda_fail(e, "cudaStreamIsCapturing");
         if (cs == cudaStreamCaptureStatusActive)
             mark_flags = cudaEventRecordExternal;
-        e = cudaEventRecordWithFlags(marks[0], st, mark_flags);
-        if (e != cudaSuccess)
-            return cuda_fail(e, "cudaEventRecord (mark)");
+        else
+            branch = nullptr;
     }
+    auto mark = [&](int k) -> cudaError_t {
+        if (!marks)
+            return cudaSuccess;
+        if (!branch)
+            return cudaEventRecordWithFlags(marks[k], st, mark_flags);
+        cudaError_t r = cudaEventRecord(branch->fork[k], st);
+        if (r == cudaSuccess)
+            r = cudaStreamWaitEvent(branch->side, branch->fork[k], 0);
+        if (r == cudaSuccess)
+            r = cudaEventRecordWithFlags(marks[k], branch->side, mark_flags);
+        return r;
+    };
+    e = mark(0);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaEventRecord (mark)");
     for (const HostLaunch::IGroup &g : hl.igroups) {
         e = launch_ingest((const IngestJob *)dl.ingest.p + g.first,
                           (const int *)dl.ingest_prefix.p + g.prefix_first, g.count, g.rows, g.prec,
@@ -892,8 +909,9 @@ int enqueue(const std::vector<FramePrep> &frames, const HostLaunch &hl, DeviceLa
             return cuda_fail(e, "demodulation launch");
     }
     // (the ingest / demodulation launches above zeroed each frame's image maxima)
-    if (marks)
-        cudaEventRecordWithFlags(marks[1], st, mark_flags);
+    e = mark(1);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaEventRecord (mark)");
     for (const HostLaunch::Group &g : hl.groups) {
         e = launch_beamform((const BfJob *)dl.jobs.p + g.first,
                             (const int *)dl.tile_prefix.p + g.prefix_first, g.count, g.tiles, g.smem,
@@ -901,8 +919,9 @@ int enqueue(const std::vector<FramePrep> &frames, const HostLaunch &hl, DeviceLa
         if (e != cudaSuccess)
             return cuda_fail(e, "beamform launch");
     }
-    if (marks)
-        cudaEventRecordWithFlags(marks[2], st, mark_flags);
+    e = mark(2);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaEventRecord (mark)");
     if (!hl.env.empty()) {
         e = launch_envelope((const EnvJob *)dl.env.p, (const int *)dl.env_prefix.p, (int)hl.env.size(),
                             hl.env_blocks, hl.env_smem, st);
@@ -921,8 +940,14 @@ int enqueue(const std::vector<FramePrep> &frames, const HostLaunch &hl, DeviceLa
         if (e != cudaSuccess)
             return cuda_fail(e, "log launch");
     }
-    if (marks)
-        cudaEventRecordWithFlags(marks[3], st, mark_flags);
+    e = mark(3);
+    if (e == cudaSuccess && marks && branch) {  // the side branch back into st
+        e = cudaEventRecord(branch->join, branch->side);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(st, branch->join, 0);
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaEventRecord (mark)");
     return BF_OK;
 }
 
@@ -1586,10 +1611,18 @@ BF_API int bf_batch_create(const bf_frame *frames, int32_t n, bf_batch **out)
         return rc;
     cudaMemset(b->dl.err.p, 0, sizeof(int));
     // Capture the batch's launches once; bf_batch_launch replays the graph.
+    // The stage marks sit on a side branch of the graph (MarkBranch).
     cudaStream_t cap;
     cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
     if (e != cudaSuccess)
         return cuda_fail(e, "cudaStreamCreate");
+    MarkBranch br;
+    e = cudaStreamCreateWithFlags(&br.side, cudaStreamNonBlocking);
+    for (auto &f : br.fork)
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&f, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&br.join, cudaEventDisableTiming);
     for (auto &m : b->marks)
         if (e == cudaSuccess)
             e = cudaEventCreate(&m);
@@ -1599,7 +1632,7 @@ BF_API int bf_batch_create(const bf_frame *frames, int32_t n, bf_batch **out)
     if (e == cudaSuccess)
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        rc = enqueue(b->frames, b->hl, b->dl, cap, b->marks);
+        rc = enqueue(b->frames, b->hl, b->dl, cap, b->marks, &br);
         cudaGraph_t g = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         if (!rc && e2 == cudaSuccess) {
@@ -1615,6 +1648,13 @@ BF_API int bf_batch_create(const bf_frame *frames, int32_t n, bf_batch **out)
         rc = cuda_fail(e, "cudaStreamBeginCapture");
     }
     cudaStreamDestroy(cap);
+    for (auto &f : br.fork)
+        if (f)
+            cudaEventDestroy(f);
+    if (br.join)
+        cudaEventDestroy(br.join);
+    if (br.side)
+        cudaStreamDestroy(br.side);
     if (rc)
         return rc;
     *out = b.release();

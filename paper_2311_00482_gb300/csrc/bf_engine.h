@@ -254,10 +254,22 @@ int prepare_frame(bf_handle *h, const int16_t *rf_dev, int ns, const double *ang
 int job_frames_cap(const Plan *p, uint32_t flags, int cap);
 void build_launch(const std::vector<FramePrep> &frames, HostLaunch &hl);
 int upload_maps(std::vector<FramePrep> &frames, cudaStream_t st, bool async);
+// Stage marks of a captured graph on a side branch: mark k is recorded on the
+// side stream after it joins the capture behind stage k (fork[k] recorded on
+// the capture stream), so each mark node depends on the work it closes and no
+// kernel depends on a mark: the kernels keep direct edges.  Mark 0 is a root
+// beside the first launch.  join brings the side branch back into the
+// capture's origin stream at the end.
+struct MarkBranch {
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t join = nullptr;
+};
 // marks (optional, 4 events): recorded before the ingest, before and after the
-// beamforming launches, and after the last launch.
+// beamforming launches, and after the last launch; in line on st, or (branch,
+// inside a capture of st) on the branch's side stream.
 int enqueue(const std::vector<FramePrep> &frames, const HostLaunch &hl, DeviceLaunch &dl,
-            cudaStream_t st, cudaEvent_t *marks = nullptr);
+            cudaStream_t st, cudaEvent_t *marks = nullptr, const MarkBranch *branch = nullptr);
 int read_device_error(DeviceLaunch &dl, cudaStream_t st);
 bool is_device_pointer(const void *p);
 void engine_forget(bf_handle *h);
