@@ -324,8 +324,10 @@ BF_API int bf_batch_launch(bf_batch *b, void *cuda_stream);
 BF_API int bf_batch_status(bf_batch *b, void *cuda_stream);
 /* Paper: no counterpart (per-stage timing; the paper times whole
  * reconstructions, Sec. III-B).
- * Device time of the last completed replay, from events captured in the graph:
- * ms3[0] ingest (+ resets), ms3[1] beamforming launches, ms3[2] envelope + log.
+ * Device time of the last completed replay, from events captured in the graph
+ * on a side branch (each event node follows the stage it closes; no kernel
+ * waits on one): ms3[0] ingest (+ resets), ms3[1] beamforming launches,
+ * ms3[2] envelope + log.
  * *kernel_launches (optional) receives the number of kernels one replay runs. */
 BF_API int bf_batch_timing(bf_batch *b, float *ms3, int32_t *kernel_launches);
 /* Paper: no counterpart.  Free a batch (its graph, tables and scratch); the
