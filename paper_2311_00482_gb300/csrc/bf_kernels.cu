@@ -304,13 +304,17 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestJob *__restrict
     if (row == 0 && chunk == 0 && threadIdx.x < 4) {  // before any later kernel takes a maximum
         if (J.maxbits)
             J.maxbits[threadIdx.x] = 0u;
-        for (int f = 1; f < J.nf; ++f)
-            if (J.maxbits_more[f - 1])
-                J.maxbits_more[f - 1][threadIdx.x] = 0u;
+        for (int f = 1; f < J.nf; ++f) {
+            unsigned *m = jobs[jb].maxbits_more[f - 1];
+            if (m)
+                m[threadIdx.x] = 0u;
+        }
     }
     const int nf = J.nf;  // 1, 2 or 4
     const int g = chunk * blockDim.x + threadIdx.x;
-    auto record = [&](int f) { return f == 0 ? J.rf : J.rf_more[f - 1]; };
+    // the other frames' pointers come from the job in global memory: a runtime
+    // index into the local copy J would put it on the stack
+    auto record = [&](int f) { return f == 0 ? J.rf : jobs[jb].rf_more[f - 1]; };
     auto vec_ok = [&](const int16_t *rf) {
         return (J.ns & 7) == 0 && (reinterpret_cast<unsigned long long>(rf) & 15) == 0;
     };
